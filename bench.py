@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Open-GRAPE gradient-evaluation benchmark on GB300.
+
+One step = one full gradient evaluation of the d=120 transmon-resonator
+reset problem (3-level transmon x N=40 resonator, N_t = 2000 slices, n_RK = 4
+RK4 substeps, 3 initial states, 3 controls, 3 jump operators): forward RK4
+propagation, cost, adjoint propagation and per-slice gradient traces, all in
+libgrape.so kernels.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own copy of
+the problem (replicas, weak scaling) and the time is the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GRAPE grad evals/s (fwd+adjoint), % HBM roofline; served p50/p99 latency"
+UNIT = "grad_evals/s"
+FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 nominal (recipe table)
+CPU_SAMPLE_SLICES = 200          # oracle sample: 200 of the 2000 slices
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend=backend)
+    return rank, world, dist
+
+
+def workload():
+    import workloads
+    return workloads.transmon_resonator_d120()
+
+
+def algorithmic_counts(w, nb, nt, ndo):
+    """Algorithmic FP64 flops and HBM bytes of one gradient evaluation.
+
+    Lindblad action per entry and RK stage: 16 flops per Hamiltonian band
+    (two complex multiply-adds), 4 per jump term (real coefficient times a
+    complex entry, added) and 8 for the stage combinations.  Trace per
+    stage pair: one complex multiply-add per entry and distinct control-band
+    offset.  Bytes: every stage input is written once by the forward and the
+    adjoint sweep and read once by the trace kernel (16 B per entry)."""
+    d2 = w.d * w.d
+    entries = 4 * w.n_slices * w.n_rk * w.n_states * d2
+    f_prop = (16 * nb + 4 * nt + 8) * entries
+    f_trace = 8 * ndo * entries
+    bytes_prop = 16 * entries
+    return {"flops_forward": f_prop, "flops_adjoint": f_prop, "flops_trace": f_trace,
+            "bytes_forward": bytes_prop, "bytes_adjoint": bytes_prop,
+            "bytes_trace": 2 * bytes_prop, "entries": entries}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def profiled_traffic(kernel_src_sha):
+    """DRAM bytes per launch of the forward propagation kernel from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "prop_kernel_transmon_resonator_d120.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"kernel source sha256:\s*([0-9a-f]{12,64})", text)
+    m_tr = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_tr or not kernel_src_sha.startswith(m_sha.group(1)):
+        return None
+    return float(m_tr.group(1))
+
+
+def cpu_baseline(threads=None):
+    """The plain-C FP64 oracle on a bounded sample of the workload."""
+    import workloads
+    from oracle import sparse
+    w = workloads.transmon_resonator_d120(n_slices=CPU_SAMPLE_SLICES)
+    nthreads = threads or w.n_states
+    _, _, _, secs = sparse.run_workload(w, mode=sparse.MODE_EXACT, threads=nthreads)
+    frac = CPU_SAMPLE_SLICES / 2000.0
+    return {"value": frac / secs, "unit": UNIT, "cores": min(nthreads, w.n_states),
+            "kind": "oracle",
+            "sample": f"d=120 problem with {CPU_SAMPLE_SLICES} of 2000 slices (same d, states, "
+                      f"controls, RK substeps), {secs:.2f} s, scaled by {frac:g} grad evals; "
+                      f"OpenMP over the {w.n_states} initial states"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import workloads
+    from oracle import sparse
+    sparse.build()
+    w = workloads.transmon_resonator_d120(n_slices=40)
+    frac = 40 / 2000.0
+    for _ in range(args.warmup):
+        sparse.run_workload(w, threads=w.n_states)
+    times = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        times.append(sparse.run_workload(w, threads=w.n_states)[3])
+    total = time.perf_counter() - t_all
+    value = frac * args.steps / total
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "transmon_resonator_d120", "d": 120, "n_slices": 2000,
+                   "n_rk": 4, "n_states": 3, "n_controls": 3, "n_jumps": 3,
+                   "grad_mode": "exact"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": w.n_states, "kind": "oracle",
+                         "sample": "each step: the d=120 problem with 40 of 2000 slices, "
+                                   "scaled by 0.02 grad evals"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, dist = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+    from paper_1609_03170_gb300 import GrapeProblem, _lib
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w = workload()
+    P = GrapeProblem.from_workload(w)
+    stream = torch.cuda.Stream()
+    u_dev = torch.from_numpy(w.u).cuda()
+    F_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    G_dev = torch.empty((w.n_slices, w.n_controls), dtype=torch.float64, device="cuda")
+
+    def step_device():
+        _lib.grape_gradient(P.handle, u_dev.data_ptr(), F_dev.data_ptr(), G_dev.data_ptr(),
+                            stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step_device()
+    stream.synchronize()
+    launches_per_step = P.gradient_launches()
+
+    # ---- device-resident timing (value) ------------------------------------
+    P.set_profiling(True)
+    P.phase_times()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step_device()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    phases = P.phase_times()
+    P.set_profiling(False)
+
+    # ---- end to end through the public API with pinned host buffers ------
+    u_host = torch.empty((w.n_slices, w.n_controls), dtype=torch.float64, pin_memory=True)
+    u_host.copy_(torch.from_numpy(w.u))
+    F_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
+    G_host = torch.empty((w.n_slices, w.n_controls), dtype=torch.float64, pin_memory=True)
+    _lib.grape_gradient(P.handle, u_host.data_ptr(), F_host.data_ptr(), G_host.data_ptr(),
+                        stream.cuda_stream)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _lib.grape_gradient(P.handle, u_host.data_ptr(), F_host.data_ptr(), G_host.data_ptr(),
+                            stream.cuda_stream)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+
+    if dist:
+        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    from paper_1609_03170_gb300 import problem as _problem
+    bm = _problem.band_model(w.phys)
+    # bands of A = H_eff (union of H0, controls and c^+c offsets) and jump terms
+    offs = set(int(o) for o in bm.H0.offsets)
+    for h in bm.Hc:
+        offs |= set(int(o) for o in h.offsets)
+    for c in bm.jumps:
+        for o1 in c.offsets:
+            for o2 in c.offsets:
+                offs.add(int(o2) - int(o1))
+    nt = sum(len(c.offsets) ** 2 for c in bm.jumps)
+    ndo = len(set(int(o) for h in bm.Hc for o in h.offsets))
+    counts = algorithmic_counts(w, len(offs), nt, ndo)
+
+    fwd_ms, fwd_n = phases["forward"]
+    adj_ms, adj_n = phases["adjoint"]
+    tr_ms, tr_n = phases["trace"]
+    dom = "forward" if fwd_ms >= adj_ms else "adjoint"
+    dom_ms = (fwd_ms / max(fwd_n, 1)) if dom == "forward" else (adj_ms / max(adj_n, 1))
+    achieved = counts["flops_" + dom] / (dom_ms * 1e-3) / 1e12
+    src = open(os.path.join(ROOT, "paper_1609_03170_gb300", "csrc", "grape_kernels.cu"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()
+    traffic = profiled_traffic(sha)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    step_bytes = counts["bytes_forward"] + counts["bytes_adjoint"] + counts["bytes_trace"]
+    value = world * 1000.0 / ms
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "transmon_resonator_d120", "d": w.d, "n_slices": w.n_slices,
+                   "n_rk": w.n_rk, "n_states": w.n_states, "n_controls": w.n_controls,
+                   "n_jumps": len(bm.jumps), "grad_mode": "exact",
+                   "cluster": P.geometry()[0], "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2: %.1f GB of stage storage written and read per step"
+                         % (step_bytes / 1e9)},
+        "roofline": {"bound": "alu", "kernel": f"prop_kernel ({dom})", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": traffic,
+                     "flops_per_launch": counts["flops_" + dom],
+                     "ms_per_launch": dom_ms,
+                     "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300 unit counts and clock)"},
+        "hbm": {"bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
+                "peak_gbs": hbm_peak, "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+        "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+        "e2e": {"value": world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(u_host.numel() * 8),
+                "d2h_bytes_per_step": int(F_host.numel() * 8 + G_host.numel() * 8)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,139 @@
+/*
+ * grape.h - C ABI of the GB300 open-GRAPE gradient library (libgrape.so).
+ *
+ * Open GRAPE without matrix exponentials (Boutin et al., arXiv:1609.03170):
+ * the density matrix rho (d x d, complex128) is propagated under the Lindblad
+ * master equation (Eq. master, Eq. disspation)
+ *     d rho/dt = -i[H(t), rho] + sum_m gamma_m (c_m rho c_m^+ - {c_m^+ c_m, rho}/2),
+ *     H(t) = H_0 + sum_k u_k(j) H_k on slice j             (Eq. Hamiltonian)
+ * over N piecewise-constant control slices of length dt = T/N, each slice
+ * integrated with n_RK classic RK4 substeps (Sec. 3, Eq. rkmaster).  The
+ * performance index is Phi = sum_s Re Tr(sigma_s rho_s(T)) (Eq. phi, Eq. Phi0)
+ * and its gradient dPhi/du_k(j) comes from a backward (adjoint) propagation
+ * under the dual Lindbladian followed by per-slice trace products
+ * (Sec. 2.2 Eq. lambda, Eq. dphidu; Sec. 3).
+ *
+ * Conventions
+ *  - complex numbers are interleaved (re, im) doubles;
+ *  - d x d matrices are row-major; rho0/sigma hold n_states (or 1) of them;
+ *  - controls u are slice-major: u[j * n_controls + k];
+ *  - pointers passed to grape_forward / grape_gradient may be host or device
+ *    memory (told apart with cudaPointerGetAttributes); device pointers must
+ *    be on the problem's device and are only borrowed;
+ *  - every call returns a grape_status; on failure grape_last_error() gives a
+ *    thread-local message.  No call aborts, traps or waits without a bound.
+ */
+#ifndef GRAPE_H_
+#define GRAPE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GRAPE_OK = 0,
+    GRAPE_EINVAL = 1,      /* invalid argument or descriptor */
+    GRAPE_ENOMEM = 2,      /* device or host allocation failed */
+    GRAPE_ECUDA = 3,       /* a CUDA runtime call failed */
+    GRAPE_ETIMEOUT = 4,    /* a bounded wait ran out */
+    GRAPE_EBUSY = 5,       /* resource (slot, memory budget) not available now */
+    GRAPE_ENOTREADY = 6,   /* result not ready yet (grape_poll) */
+    GRAPE_EINTERNAL = 7
+} grape_status;
+
+typedef enum {
+    GRAPE_GRAD_EXACT = 0,        /* exact derivative of the discrete RK4 map */
+    GRAPE_GRAD_FIRST_ORDER = 1   /* the paper's Eq. (dphidu), first order in dt */
+} grape_grad_mode;
+
+/* A banded (DIA) operator: band b holds the entries Op[i][i + offsets[b]],
+ * values[b * d + i] (complex), for i in [0, d); entries whose column falls
+ * outside [0, d) are ignored. */
+typedef struct {
+    int32_t n_diag;
+    const int32_t *offsets;   /* [n_diag] */
+    const double *values;     /* [n_diag][d] complex interleaved */
+} grape_band_op;
+
+/* Problem descriptor.  grape_problem_create copies every array it points to. */
+typedef struct {
+    int32_t d;                  /* Hilbert-space dimension */
+    int32_t n_controls;         /* R, number of control Hamiltonians */
+    int32_t n_jumps;            /* number of dissipators c_m */
+    int32_t n_states;           /* initial states propagated (n_s of Eq. RK) */
+    int32_t n_slices;           /* N, piecewise-constant control slices */
+    int32_t n_rk;               /* RK4 substeps per slice */
+    double T;                   /* total duration */
+    grape_band_op H0;           /* drift Hamiltonian (Hermitian) */
+    const grape_band_op *Hc;    /* [n_controls] control Hamiltonians (Hermitian) */
+    const grape_band_op *jumps; /* [n_jumps] jump operators c_m */
+    const double *rates;        /* [n_jumps] gamma_m >= 0 */
+    const double *rho0;         /* [n_states][d][d] complex, Hermitian */
+    const double *sigma;        /* [n_states or 1][d][d] complex target/observable */
+    int32_t sigma_broadcast;    /* 1: one sigma for all states */
+    int32_t grad_mode;          /* grape_grad_mode */
+    int32_t ckpt_stride;        /* reserved, 0 */
+} grape_problem_desc;
+
+typedef struct grape_problem *grape_problem_t;
+
+/* Builds the device tables of a problem on the current CUDA device.
+ * Operators enter as band lists (Eq. Hamiltonian, Eq. disspation); the
+ * non-Hermitian part -i/2 sum gamma_m c_m^+ c_m is formed here.  sigma enters
+ * the cost only through its Hermitian part (rho(T) is Hermitian), so it is
+ * stored Hermitianised.  Errors: GRAPE_EINVAL (sizes, band offsets beyond
+ * +-(d-1), non-Hermitian rho0 or control, negative rates), GRAPE_ENOMEM. */
+grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_t *out);
+
+/* Frees everything the problem allocated.  NULL is accepted. */
+grape_status grape_problem_destroy(grape_problem_t problem);
+
+/* Forward propagation (Sec. 3, Eq. rkmaster) and the cost (Eq. phi).
+ * u: [n_slices][n_controls] doubles, host or device.
+ * F: one double (host or device) receiving Phi.
+ * rhoT: NULL or [n_states][d][d] complex (host or device) receiving rho_s(T).
+ * stream: a cudaStream_t (NULL = legacy default stream).  The call returns
+ * once the results are in host memory when F is a host pointer; with device
+ * outputs it only enqueues the work on the stream. */
+grape_status grape_forward(grape_problem_t problem, const double *u, double *F,
+                           double *rhoT, void *stream);
+
+/* Phi and its gradient dPhi/du_k(j) (Sec. 2.2 Eq. dphidu; Sec. 3), in the
+ * problem's grad_mode.  grad: [n_slices][n_controls] doubles, host or
+ * device.  Same pointer and stream rules as grape_forward. */
+grape_status grape_gradient(grape_problem_t problem, const double *u, double *F,
+                            double *grad, void *stream);
+
+/* Device memory the problem holds, in bytes (tables plus stage storage). */
+grape_status grape_problem_memory(grape_problem_t problem, size_t *bytes);
+
+/* Launch geometry chosen for the propagation kernels (cluster size, threads
+ * per block, elements per thread).  For tests and benchmarks. */
+grape_status grape_problem_geometry(grape_problem_t problem, int32_t *cluster,
+                                    int32_t *threads, int32_t *elems_per_thread);
+
+/* Per-launch timing with CUDA events recorded on the caller's stream around
+ * every kernel the library launches (off by default).  grape_phase_times
+ * waits for the recorded events, returns the summed milliseconds and launch
+ * counts since the previous call per phase - [0] forward propagation,
+ * [1] cost, [2] adjoint propagation, [3] gradient traces - and clears them. */
+grape_status grape_set_profiling(grape_problem_t problem, int32_t on);
+grape_status grape_phase_times(grape_problem_t problem, double ms[4], int32_t launches[4]);
+
+/* Kernel launches one grape_gradient call makes (for launch accounting). */
+int32_t grape_gradient_launches(grape_problem_t problem);
+
+/* Thread-local message of the last failed call on this thread. */
+const char *grape_last_error(void);
+
+/* Library version string. */
+const char *grape_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAPE_H_ */

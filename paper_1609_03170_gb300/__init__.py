@@ -1,0 +1,16 @@
+"""GB300-native open GRAPE without matrix exponentials (arXiv:1609.03170).
+
+The hot path - RK4 propagation of the density matrix under the Lindblad
+equation, the adjoint propagation under the dual Lindbladian and the
+per-slice gradient traces - runs as hand-written sm_103a CUDA kernels behind
+the C ABI of ``include/grape.h`` (``libgrape.so``).  This package holds the
+build script, the ctypes binding and the problem front end.
+"""
+from . import _lib
+from ._lib import (GRAPE_GRAD_EXACT, GRAPE_GRAD_FIRST_ORDER, GrapeError, grape_forward,
+                   grape_gradient, grape_problem_create, grape_problem_destroy)
+from .problem import BandModel, BandOp, GrapeProblem, band_model
+
+__all__ = ["GRAPE_GRAD_EXACT", "GRAPE_GRAD_FIRST_ORDER", "GrapeError", "GrapeProblem",
+           "BandModel", "BandOp", "band_model", "grape_forward", "grape_gradient",
+           "grape_problem_create", "grape_problem_destroy"]

@@ -1,0 +1,151 @@
+"""ctypes binding of libgrape.so: the C ABI of include/grape.h, same names.
+
+Argument marshalling only; every step of the propagation and of the gradient
+runs in the library's CUDA kernels.  Loading fails loudly when the library is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int32, c_double, c_void_p, c_size_t = ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+P = ctypes.POINTER
+
+GRAPE_OK, GRAPE_EINVAL, GRAPE_ENOMEM, GRAPE_ECUDA, GRAPE_ETIMEOUT, GRAPE_EBUSY, \
+    GRAPE_ENOTREADY, GRAPE_EINTERNAL = range(8)
+GRAPE_GRAD_EXACT, GRAPE_GRAD_FIRST_ORDER = 0, 1
+
+STATUS_NAMES = {0: "GRAPE_OK", 1: "GRAPE_EINVAL", 2: "GRAPE_ENOMEM", 3: "GRAPE_ECUDA",
+                4: "GRAPE_ETIMEOUT", 5: "GRAPE_EBUSY", 6: "GRAPE_ENOTREADY", 7: "GRAPE_EINTERNAL"}
+
+
+class grape_band_op(ctypes.Structure):
+    _fields_ = [("n_diag", c_int32), ("offsets", P(c_int32)), ("values", P(c_double))]
+
+
+class grape_problem_desc(ctypes.Structure):
+    _fields_ = [("d", c_int32), ("n_controls", c_int32), ("n_jumps", c_int32),
+                ("n_states", c_int32), ("n_slices", c_int32), ("n_rk", c_int32),
+                ("T", c_double),
+                ("H0", grape_band_op), ("Hc", P(grape_band_op)), ("jumps", P(grape_band_op)),
+                ("rates", P(c_double)), ("rho0", P(c_double)), ("sigma", P(c_double)),
+                ("sigma_broadcast", c_int32), ("grad_mode", c_int32), ("ckpt_stride", c_int32)]
+
+
+class GrapeError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+EXPORTS = ["grape_problem_create", "grape_problem_destroy", "grape_forward", "grape_gradient",
+           "grape_problem_memory", "grape_problem_geometry", "grape_set_profiling",
+           "grape_phase_times", "grape_gradient_launches", "grape_last_error", "grape_version"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgrape.so (building it with nvcc when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libgrape.so not found at {path}; run paper_1609_03170_gb300.build")
+    lib = ctypes.CDLL(path)
+    lib.grape_problem_create.argtypes = [P(grape_problem_desc), P(c_void_p)]
+    lib.grape_problem_create.restype = c_int32
+    lib.grape_problem_destroy.argtypes = [c_void_p]
+    lib.grape_problem_destroy.restype = c_int32
+    lib.grape_forward.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.grape_forward.restype = c_int32
+    lib.grape_gradient.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.grape_gradient.restype = c_int32
+    lib.grape_problem_memory.argtypes = [c_void_p, P(c_size_t)]
+    lib.grape_problem_memory.restype = c_int32
+    lib.grape_problem_geometry.argtypes = [c_void_p, P(c_int32), P(c_int32), P(c_int32)]
+    lib.grape_problem_geometry.restype = c_int32
+    lib.grape_set_profiling.argtypes = [c_void_p, c_int32]
+    lib.grape_set_profiling.restype = c_int32
+    lib.grape_phase_times.argtypes = [c_void_p, P(c_double), P(c_int32)]
+    lib.grape_phase_times.restype = c_int32
+    lib.grape_gradient_launches.argtypes = [c_void_p]
+    lib.grape_gradient_launches.restype = c_int32
+    lib.grape_last_error.argtypes = []
+    lib.grape_last_error.restype = ctypes.c_char_p
+    lib.grape_version.argtypes = []
+    lib.grape_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def check(status: int, where: str):
+    if status != GRAPE_OK:
+        msg = load().grape_last_error().decode(errors="replace")
+        raise GrapeError(status, where, msg)
+
+
+def grape_problem_create(desc: grape_problem_desc) -> c_void_p:
+    h = c_void_p()
+    check(load().grape_problem_create(ctypes.byref(desc), ctypes.byref(h)), "grape_problem_create")
+    return h
+
+
+def grape_problem_destroy(h) -> None:
+    check(load().grape_problem_destroy(h), "grape_problem_destroy")
+
+
+def grape_forward(h, u_ptr: int, F_ptr: int, rhoT_ptr: int, stream_ptr: int) -> None:
+    check(load().grape_forward(h, u_ptr or None, F_ptr or None, rhoT_ptr or None,
+                               stream_ptr or None), "grape_forward")
+
+
+def grape_gradient(h, u_ptr: int, F_ptr: int, grad_ptr: int, stream_ptr: int) -> None:
+    check(load().grape_gradient(h, u_ptr or None, F_ptr or None, grad_ptr or None,
+                                stream_ptr or None), "grape_gradient")
+
+
+def grape_problem_memory(h) -> int:
+    n = c_size_t()
+    check(load().grape_problem_memory(h, ctypes.byref(n)), "grape_problem_memory")
+    return int(n.value)
+
+
+def grape_problem_geometry(h):
+    c, t, e = c_int32(), c_int32(), c_int32()
+    check(load().grape_problem_geometry(h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(e)),
+          "grape_problem_geometry")
+    return int(c.value), int(t.value), int(e.value)
+
+
+def grape_set_profiling(h, on: bool) -> None:
+    check(load().grape_set_profiling(h, 1 if on else 0), "grape_set_profiling")
+
+
+PHASES = ("forward", "cost", "adjoint", "trace")
+
+
+def grape_phase_times(h):
+    """{phase: (milliseconds, launches)} since the previous call."""
+    ms = (c_double * 4)()
+    n = (c_int32 * 4)()
+    check(load().grape_phase_times(h, ms, n), "grape_phase_times")
+    return {PHASES[i]: (float(ms[i]), int(n[i])) for i in range(4)}
+
+
+def grape_gradient_launches(h) -> int:
+    return int(load().grape_gradient_launches(h))
+
+
+def grape_version() -> str:
+    return load().grape_version().decode()

@@ -1,0 +1,802 @@
+// grape_api.cu - C ABI of libgrape.so (declared in include/grape.h).
+//
+// Host-side work: validation of the problem descriptor, band (DIA) algebra
+// that turns H_0, H_k and the jump operators into the two kernel tables
+// (forward Lindbladian, Eq. master/disspation, and its dual), the launch
+// geometry, the segment plan of the gradient (stage storage or checkpoints
+// plus recomputation) and the launch sequence of grape_forward and
+// grape_gradient.  All arithmetic of the propagation and of the gradient
+// runs in the kernels of grape_kernels.cu.
+#include "grape.h"
+#include "grape_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+namespace {
+
+using cplx = std::complex<double>;
+using Bands = std::map<int, std::vector<cplx>>;   // offset o -> Op[i][i+o], i in [0, d)
+
+thread_local std::string g_last_error;
+
+grape_status fail(grape_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+#define GRAPE_CUDA_TRY(expr)                                                              \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(GRAPE_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool valid_entry(int i, int o, int d) { return i + o >= 0 && i + o < d; }
+
+grape_status read_bands(const grape_band_op &op, int d, const char *name, Bands *out) {
+    Bands B;
+    if (op.n_diag < 0 || (op.n_diag > 0 && (!op.offsets || !op.values)))
+        return fail(GRAPE_EINVAL, std::string(name) + ": bad band list");
+    for (int b = 0; b < op.n_diag; ++b) {
+        const int o = op.offsets[b];
+        if (o <= -d || o >= d) return fail(GRAPE_EINVAL, std::string(name) + ": band offset out of range");
+        auto &v = B[o];
+        v.resize(d);
+        for (int i = 0; i < d; ++i) {
+            if (!valid_entry(i, o, d)) continue;   // entries outside the matrix are ignored
+            const double re = op.values[2 * ((size_t)b * d + i)];
+            const double im = op.values[2 * ((size_t)b * d + i) + 1];
+            if (!std::isfinite(re) || !std::isfinite(im))
+                return fail(GRAPE_EINVAL, std::string(name) + ": non-finite value");
+            v[i] += cplx(re, im);
+        }
+    }
+    *out = B;
+    return GRAPE_OK;
+}
+
+void add_into(Bands &dst, const Bands &src, cplx s, int d) {
+    for (const auto &kv : src) {
+        auto &v = dst[kv.first];
+        v.resize(d);
+        for (int i = 0; i < d; ++i) v[i] += s * kv.second[i];
+    }
+}
+
+Bands adjoint(const Bands &A, int d) {
+    Bands R;
+    for (const auto &kv : A) {
+        const int o = kv.first;
+        auto &w = R[-o];
+        w.resize(d);
+        for (int i = 0; i < d; ++i)
+            if (i - o >= 0 && i - o < d) w[i] = std::conj(kv.second[i - o]);   // A^+[i][i-o] = conj(A[i-o][i])
+    }
+    return R;
+}
+
+Bands product(const Bands &A, const Bands &B, int d) {
+    Bands R;
+    for (const auto &a : A)
+        for (const auto &b : B) {
+            const int o = a.first + b.first;
+            if (o <= -d || o >= d) continue;
+            auto &w = R[o];
+            w.resize(d);
+            for (int i = 0; i < d; ++i) {
+                const int m = i + a.first;
+                if (m < 0 || m >= d || !valid_entry(m, b.first, d)) continue;
+                w[i] += a.second[i] * b.second[m];
+            }
+        }
+    return R;
+}
+
+Bands scaled(const Bands &A, cplx s, int d) {
+    Bands R;
+    add_into(R, A, s, d);
+    return R;
+}
+
+void prune(Bands &A) {
+    for (auto it = A.begin(); it != A.end();) {
+        bool zero = true;
+        for (const cplx &c : it->second)
+            if (c != cplx(0.0, 0.0)) { zero = false; break; }
+        it = zero ? A.erase(it) : std::next(it);
+    }
+}
+
+double max_abs(const Bands &A) {
+    double m = 0.0;
+    for (const auto &kv : A)
+        for (const cplx &c : kv.second) m = std::max(m, std::abs(c));
+    return m;
+}
+
+bool hermitian(const Bands &A, int d) {
+    Bands D = A;
+    add_into(D, adjoint(A, d), -1.0, d);
+    return max_abs(D) <= 1e-12 * std::max(1.0, max_abs(A));
+}
+
+struct HostDir {
+    std::vector<int> off;        // nb
+    std::vector<cplx> A0, Ak;    // [nb][d], [R][nb][d]
+    std::vector<int> oL, oR;     // nt
+    std::vector<cplx> vL, vR;    // [nt][d]
+};
+
+HostDir make_dir(const Bands &A0, const std::vector<Bands> &Ak,
+                 const std::vector<Bands> &jumps, int d) {
+    HostDir h;
+    std::map<int, int> idx;
+    for (const auto &kv : A0) idx[kv.first] = 0;
+    for (const auto &B : Ak)
+        for (const auto &kv : B) idx[kv.first] = 0;
+    for (auto &kv : idx) {
+        kv.second = (int)h.off.size();
+        h.off.push_back(kv.first);
+    }
+    const int nb = (int)h.off.size(), R = (int)Ak.size();
+    h.A0.assign((size_t)nb * d, cplx());
+    h.Ak.assign((size_t)R * nb * d, cplx());
+    for (const auto &kv : A0)
+        for (int i = 0; i < d; ++i) h.A0[(size_t)idx[kv.first] * d + i] = kv.second[i];
+    for (int k = 0; k < R; ++k)
+        for (const auto &kv : Ak[k])
+            for (int i = 0; i < d; ++i)
+                h.Ak[((size_t)k * nb + idx[kv.first]) * d + i] = kv.second[i];
+    for (const auto &c : jumps)
+        for (const auto &a : c)
+            for (const auto &b : c) {
+                h.oL.push_back(a.first);
+                h.oR.push_back(b.first);
+                h.vL.insert(h.vL.end(), a.second.begin(), a.second.end());
+                h.vR.insert(h.vR.end(), b.second.begin(), b.second.end());
+            }
+    return h;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int pow2ceil(long long x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev_);
+        if (prev_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != prev_) cudaSetDevice(prev_);
+    }
+
+  private:
+    int prev_ = 0;
+};
+
+}  // namespace
+
+struct grape_problem {
+    int device = 0;
+    int d = 0, R = 0, J = 0, ns = 0, n_slices = 0, n_rk = 0, mode = 0;
+    double T = 0.0;
+    size_t d2 = 0;
+    int ncl = 1, threads = 256, ept = 1, chunk = 0, halo = 0, win = 0, reach = 0;
+    size_t smem = 0;
+    int ckpt_stride = 0;
+    int seg = 0, nseg = 0;           // gradient segment plan (0 until first gradient)
+    PropTables tab[2];               // [0] forward, [1] dual
+    TraceArgs trace{};
+    double2 *d_rho0 = nullptr, *d_sigma = nullptr, *d_x = nullptr, *d_mu = nullptr;
+    double2 *d_Y = nullptr, *d_K = nullptr, *d_ckpt = nullptr;
+    double *d_u = nullptr, *d_F = nullptr, *d_G = nullptr;
+    size_t bytes = 0;
+    bool profiling = false;
+    struct Mark { int phase; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> event_pool;
+    cudaEvent_t take_event() {
+        cudaEvent_t e = nullptr;
+        if (!event_pool.empty()) {
+            e = event_pool.back();
+            event_pool.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+        }
+        return e;
+    }
+    std::vector<void *> allocs;
+    void *alloc(size_t n) {
+        void *p = nullptr;
+        if (n == 0) n = 16;
+        if (cudaMalloc(&p, n) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        allocs.push_back(p);
+        bytes += n;
+        return p;
+    }
+    ~grape_problem() {
+        for (auto &m : marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+        for (auto e : event_pool) cudaEventDestroy(e);
+        for (void *p : allocs) cudaFree(p);
+    }
+};
+
+namespace {
+
+template <typename T>
+grape_status upload(grape_problem *P, const std::vector<T> &h, T **out) {
+    *out = static_cast<T *>(P->alloc(h.size() * sizeof(T)));
+    if (!*out) return fail(GRAPE_ENOMEM, "cudaMalloc failed for a problem table");
+    if (!h.empty())
+        GRAPE_CUDA_TRY(cudaMemcpy(*out, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return GRAPE_OK;
+}
+
+grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
+    const int d = P->d;
+    if ((int)h.off.size() > GRAPE_MAXB)
+        return fail(GRAPE_EINVAL, "too many distinct Hamiltonian bands (max 12)");
+    if ((int)h.oL.size() > GRAPE_MAXT)
+        return fail(GRAPE_EINVAL, "too many jump band pairs (max 12)");
+    std::memset(t, 0, sizeof(*t));
+    t->nb = (int)h.off.size();
+    t->nt = (int)h.oL.size();
+    for (int b = 0; b < t->nb; ++b) {
+        t->off[b] = h.off[b];
+        t->off_row[b] = h.off[b] * d;
+    }
+    for (int q = 0; q < t->nt; ++q) t->jflat[q] = h.oL[q] * d + h.oR[q];
+    auto cvt = [](const std::vector<cplx> &v) {
+        std::vector<double2> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
+        return o;
+    };
+    double2 *p;
+    grape_status s;
+    if ((s = upload(P, cvt(h.A0), &p)) != GRAPE_OK) return s;
+    t->A0 = p;
+    if ((s = upload(P, cvt(h.Ak), &p)) != GRAPE_OK) return s;
+    t->Ak = p;
+    if ((s = upload(P, cvt(h.vL), &p)) != GRAPE_OK) return s;
+    t->vL = p;
+    if ((s = upload(P, cvt(h.vR), &p)) != GRAPE_OK) return s;
+    t->vR = p;
+    return GRAPE_OK;
+}
+
+grape_status choose_geometry(grape_problem *P, int omax) {
+    int max_smem = 0;
+    GRAPE_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+    const long long d2 = (long long)P->d2;
+    P->halo = omax * (P->d + 1);
+    const int nb = std::max(P->tab[0].nb, P->tab[1].nb), nt = std::max(P->tab[0].nt, P->tab[1].nt);
+    int ncl = std::min(16, pow2ceil((d2 + 1023) / 1024));
+    if (const char *env = std::getenv("GRAPE_CLUSTER")) {
+        const int v = std::atoi(env);
+        if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) ncl = v;
+    }
+    for (;;) {
+        const int chunk = (int)((d2 + ncl - 1) / ncl);
+        const int win = chunk + 2 * P->halo;
+        const size_t smem = ((size_t)2 * win + 2 * (size_t)nb * P->d + 2 * (size_t)nt * P->d) * sizeof(double2);
+        const int threads = 256;   // the kernel is compiled for 256-thread blocks
+        const int ept = pow2ceil((chunk + threads - 1) / threads);
+        bool ok = smem <= (size_t)max_smem && ept <= 16;
+        if (ok) {
+            // the attribute is an upper bound shared by all problems: use the device maximum
+            cudaError_t e = grape_prepare_prop(ept, (size_t)max_smem, ncl);
+            int clusters = 0;
+            if (e == cudaSuccess)
+                e = grape_max_active_clusters(threads, ept, smem, ncl, ncl * P->ns, &clusters);
+            if (e != cudaSuccess) cudaGetLastError();
+            ok = (e == cudaSuccess && clusters >= 1);
+            if (ok) {
+                P->ncl = ncl;
+                P->chunk = chunk;
+                P->win = win;
+                P->smem = smem;
+                P->threads = threads;
+                P->ept = ept;
+                P->reach = (ncl > 1) ? (P->halo + chunk - 1) / chunk : 0;
+                return GRAPE_OK;
+            }
+            if (ncl > 1 && smem <= (size_t)max_smem) {   // cluster too wide to schedule: narrow it
+                ncl /= 2;
+                if (ncl >= 1) continue;
+            }
+        }
+        if (ncl >= 16) break;
+        ncl *= 2;
+    }
+    return fail(GRAPE_EINVAL, "problem too large for the cluster propagation kernel "
+                              "(state window does not fit in shared memory)");
+}
+
+void rk_coefficients(double h, bool adjoint, PropArgs *a) {
+    if (!adjoint) {
+        const double g[4] = {1.0, 1.0, 1.0, 1.0};
+        const double w[4] = {h / 6, h / 3, h / 3, h / 6};
+        const double b[4] = {0.0, h / 2, h / 2, h};
+        for (int s = 0; s < 4; ++s) { a->g[s] = g[s]; a->a[s] = w[s]; a->b[s] = b[s]; a->store_map[s] = s; }
+    } else {
+        // reverse mode of one RK4 substep: kb4 = h/6 mu, kb3 = h/3 mu + h yb4,
+        // kb2 = h/3 mu + h/2 yb3, kb1 = h/6 mu + h/2 yb2; mu_prev = mu + sum yb
+        const double g[4] = {h / 6, h / 3, h / 3, h / 6};
+        const double b[4] = {0.0, h, h / 2, h / 2};
+        for (int s = 0; s < 4; ++s) { a->g[s] = g[s]; a->a[s] = 1.0; a->b[s] = b[s]; a->store_map[s] = 3 - s; }
+    }
+}
+
+PropArgs base_args(const grape_problem *P, int dir, const double *u) {
+    PropArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.tab = P->tab[dir];
+    a.d = P->d;
+    a.R = P->R;
+    a.n_states = P->ns;
+    a.ncl = P->ncl;
+    a.chunk = P->chunk;
+    a.halo = P->halo;
+    a.win = P->win;
+    a.reach = P->reach;
+    a.u = u;
+    a.n_rk = P->n_rk;
+    a.bound_step = 1;
+    rk_coefficients(P->T / P->n_slices / P->n_rk, dir == 1, &a);
+    return a;
+}
+
+size_t seg_bytes(const grape_problem *P, long long seg) {
+    const size_t mat = P->d2 * sizeof(double2) * P->ns;
+    const size_t per = (P->mode == GRAPE_GRAD_EXACT) ? (size_t)seg * P->n_rk * 4 * mat
+                                                    : (size_t)(seg + 1) * mat;
+    size_t total = 2 * per;
+    if (seg < P->n_slices) total += (size_t)((P->n_slices + seg - 1) / seg + 1) * mat;
+    return total;
+}
+
+grape_status plan_gradient(grape_problem *P) {
+    if (P->nseg > 0) return GRAPE_OK;
+    size_t free_b = 0, total_b = 0;
+    GRAPE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    double frac = 0.6;
+    if (const char *env = std::getenv("GRAPE_MEM_FRACTION")) {
+        const double v = std::atof(env);
+        if (v > 0.0 && v <= 0.95) frac = v;
+    }
+    const size_t budget = (size_t)(frac * (double)free_b);
+    long long seg;
+    if (P->ckpt_stride > 0) {
+        seg = std::min<long long>(P->ckpt_stride, P->n_slices);
+    } else {
+        seg = P->n_slices;
+        while (seg > 1 && seg_bytes(P, seg) > budget) seg = (seg + 1) / 2;
+    }
+    if (seg_bytes(P, seg) > budget && P->ckpt_stride <= 0)
+        return fail(GRAPE_ENOMEM, "gradient storage does not fit in device memory");
+    const size_t mat = P->d2 * sizeof(double2) * P->ns;
+    const size_t per = (P->mode == GRAPE_GRAD_EXACT) ? (size_t)seg * P->n_rk * 4 * mat
+                                                    : (size_t)(seg + 1) * mat;
+    P->d_Y = static_cast<double2 *>(P->alloc(per));
+    P->d_K = static_cast<double2 *>(P->alloc(per));
+    if (!P->d_Y || !P->d_K) return fail(GRAPE_ENOMEM, "cudaMalloc failed for gradient storage");
+    const int nseg = (int)((P->n_slices + seg - 1) / seg);
+    if (nseg > 1) {
+        P->d_ckpt = static_cast<double2 *>(P->alloc((size_t)(nseg + 1) * mat));
+        if (!P->d_ckpt) return fail(GRAPE_ENOMEM, "cudaMalloc failed for checkpoints");
+    }
+    P->seg = (int)seg;
+    P->nseg = nseg;
+    return GRAPE_OK;
+}
+
+enum { PH_FORWARD = 0, PH_COST = 1, PH_ADJOINT = 2, PH_TRACE = 3 };
+
+// Runs one launch, bracketed by CUDA events on its stream when profiling.
+template <typename F>
+grape_status timed(grape_problem *P, int phase, cudaStream_t s, F &&launch) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (P->profiling) {
+        a = P->take_event();
+        b = P->take_event();
+        if (a) cudaEventRecord(a, s);
+    }
+    const cudaError_t e = launch();
+    if (P->profiling && a && b) {
+        cudaEventRecord(b, s);
+        P->marks.push_back({phase, a, b});
+    }
+    if (e != cudaSuccess) return fail(GRAPE_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return GRAPE_OK;
+}
+
+grape_status launch_prop(grape_problem *P, const PropArgs &a, cudaStream_t s) {
+    return timed(P, a.reverse ? PH_ADJOINT : PH_FORWARD, s,
+                 [&] { return grape_launch_prop(a, P->threads, P->ept, P->smem, s); });
+}
+
+grape_status stage_inputs(grape_problem *P, const double *u, const double **u_dev,
+                          cudaStream_t s) {
+    const size_t ub = (size_t)P->n_slices * P->R * sizeof(double);
+    if (P->R == 0) { *u_dev = P->d_u; return GRAPE_OK; }
+    if (!u) return fail(GRAPE_EINVAL, "u is NULL");
+    if (is_device_ptr(u)) {
+        *u_dev = u;
+    } else {
+        GRAPE_CUDA_TRY(cudaMemcpyAsync(P->d_u, u, ub, cudaMemcpyHostToDevice, s));
+        *u_dev = P->d_u;
+    }
+    return GRAPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *grape_last_error(void) { return g_last_error.c_str(); }
+
+const char *grape_version(void) { return "grape-gb300 0.1 (sm_103a, fp64)"; }
+
+grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_t *out) {
+    if (!desc || !out) return fail(GRAPE_EINVAL, "NULL descriptor or output");
+    *out = nullptr;
+    const int d = desc->d;
+    if (d < 1 || d > 4096) return fail(GRAPE_EINVAL, "d must be in [1, 4096]");
+    if (desc->n_controls < 0 || desc->n_controls > GRAPE_MAXR)
+        return fail(GRAPE_EINVAL, "n_controls must be in [0, 8]");
+    if (desc->n_jumps < 0 || desc->n_states < 1 || desc->n_slices < 1 || desc->n_rk < 1)
+        return fail(GRAPE_EINVAL, "n_jumps >= 0, n_states >= 1, n_slices >= 1, n_rk >= 1 required");
+    if (!(desc->T > 0.0) || !std::isfinite(desc->T)) return fail(GRAPE_EINVAL, "T must be positive");
+    if (desc->grad_mode != GRAPE_GRAD_EXACT && desc->grad_mode != GRAPE_GRAD_FIRST_ORDER)
+        return fail(GRAPE_EINVAL, "unknown grad_mode");
+    if (desc->ckpt_stride < 0) return fail(GRAPE_EINVAL, "ckpt_stride must be >= 0");
+    if (!desc->rho0 || !desc->sigma) return fail(GRAPE_EINVAL, "rho0 and sigma are required");
+    if (desc->n_controls > 0 && !desc->Hc) return fail(GRAPE_EINVAL, "Hc is NULL");
+    if (desc->n_jumps > 0 && (!desc->jumps || !desc->rates)) return fail(GRAPE_EINVAL, "jumps/rates NULL");
+
+    grape_status st;
+    Bands H0;
+    if ((st = read_bands(desc->H0, d, "H0", &H0)) != GRAPE_OK) return st;
+    if (!hermitian(H0, d)) return fail(GRAPE_EINVAL, "H0 is not Hermitian");
+    std::vector<Bands> Hc(desc->n_controls);
+    for (int k = 0; k < desc->n_controls; ++k) {
+        if ((st = read_bands(desc->Hc[k], d, "Hc", &Hc[k])) != GRAPE_OK) return st;
+        if (!hermitian(Hc[k], d)) return fail(GRAPE_EINVAL, "a control Hamiltonian is not Hermitian");
+        prune(Hc[k]);
+    }
+    std::vector<Bands> C(desc->n_jumps);
+    for (int m = 0; m < desc->n_jumps; ++m) {
+        const double g = desc->rates[m];
+        if (!(g >= 0.0) || !std::isfinite(g)) return fail(GRAPE_EINVAL, "rates must be finite and >= 0");
+        if ((st = read_bands(desc->jumps[m], d, "jump", &C[m])) != GRAPE_OK) return st;
+        prune(C[m]);
+    }
+
+    // Forward: A = H_eff = H0 - i/2 sum gamma c^+ c (+ sum u_k H_k), terms from sqrt(gamma) c.
+    Bands A0 = H0;
+    std::vector<Bands> Jf, Ja;
+    for (int m = 0; m < desc->n_jumps; ++m) {
+        const double g = desc->rates[m];
+        if (g == 0.0 || C[m].empty()) continue;
+        add_into(A0, product(adjoint(C[m], d), C[m], d), cplx(0.0, -0.5 * g), d);
+        Jf.push_back(scaled(C[m], std::sqrt(g), d));
+        Ja.push_back(scaled(adjoint(C[m], d), std::sqrt(g), d));
+    }
+    prune(A0);
+    // Dual: A' = -H_eff^+, A'_k = -H_k^+, terms from sqrt(gamma) c^+.
+    Bands A0d = scaled(adjoint(A0, d), -1.0, d);
+    std::vector<Bands> Hcd(Hc.size());
+    for (size_t k = 0; k < Hc.size(); ++k) Hcd[k] = scaled(adjoint(Hc[k], d), -1.0, d);
+    for (auto &c : Jf) prune(c);
+    for (auto &c : Ja) prune(c);
+    const HostDir hf = make_dir(A0, Hc, Jf, d);
+    const HostDir ha = make_dir(A0d, Hcd, Ja, d);
+
+    // initial states (Hermitian) and the Hermitian part of sigma
+    const size_t d2 = (size_t)d * d;
+    std::vector<double2> rho0(d2 * desc->n_states), sig(d2 * desc->n_states);
+    for (int s = 0; s < desc->n_states; ++s) {
+        const double *r = desc->rho0 + 2 * d2 * s;
+        double mx = 0.0, asym = 0.0;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                const cplx a(r[2 * (i * d + j)], r[2 * (i * d + j) + 1]);
+                const cplx b(r[2 * (j * d + i)], r[2 * (j * d + i) + 1]);
+                if (!std::isfinite(a.real()) || !std::isfinite(a.imag()))
+                    return fail(GRAPE_EINVAL, "rho0 has non-finite entries");
+                mx = std::max(mx, std::abs(a));
+                asym = std::max(asym, std::abs(a - std::conj(b)));
+                rho0[s * d2 + i * d + j] = make_double2(a.real(), a.imag());
+            }
+        if (asym > 1e-12 * std::max(mx, 1e-300)) return fail(GRAPE_EINVAL, "rho0 is not Hermitian");
+        const double *g = desc->sigma + (desc->sigma_broadcast ? 0 : 2 * d2 * s);
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                const cplx a(g[2 * (i * d + j)], g[2 * (i * d + j) + 1]);
+                const cplx b(g[2 * (j * d + i)], g[2 * (j * d + i) + 1]);
+                if (!std::isfinite(a.real()) || !std::isfinite(a.imag()))
+                    return fail(GRAPE_EINVAL, "sigma has non-finite entries");
+                const cplx hpart = 0.5 * (a + std::conj(b));
+                sig[s * d2 + i * d + j] = make_double2(hpart.real(), hpart.imag());
+            }
+    }
+
+    // control bands for the trace kernel
+    TraceArgs tr;
+    std::memset(&tr, 0, sizeof(tr));
+    std::vector<double2> cbv;
+    {
+        std::map<int, int> doidx;
+        for (int k = 0; k < desc->n_controls; ++k)
+            for (const auto &kv : Hc[k]) {
+                if (tr.ncb >= GRAPE_MAXCB) return fail(GRAPE_EINVAL, "too many control bands (max 8)");
+                auto it = doidx.find(kv.first);
+                if (it == doidx.end()) {
+                    if ((int)doidx.size() >= GRAPE_MAXDO) return fail(GRAPE_EINVAL, "too many control band offsets");
+                    const int id = (int)doidx.size();
+                    doidx[kv.first] = id;
+                    tr.do_off[id] = kv.first;
+                    it = doidx.find(kv.first);
+                }
+                tr.cb_k[tr.ncb] = k;
+                tr.cb_do[tr.ncb] = it->second;
+                for (int i = 0; i < d; ++i) cbv.push_back(make_double2(kv.second[i].real(), kv.second[i].imag()));
+                tr.ncb++;
+            }
+        tr.ndo = (int)doidx.size();
+        tr.d = d;
+        tr.R = desc->n_controls;
+    }
+
+    grape_problem *P = new grape_problem();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return fail(GRAPE_ECUDA, "no CUDA device");
+    }
+    P->device = dev;
+    P->d = d;
+    P->d2 = d2;
+    P->R = desc->n_controls;
+    P->J = desc->n_jumps;
+    P->ns = desc->n_states;
+    P->n_slices = desc->n_slices;
+    P->n_rk = desc->n_rk;
+    P->T = desc->T;
+    P->mode = desc->grad_mode;
+    P->ckpt_stride = desc->ckpt_stride;
+    auto bail = [&](grape_status s) { delete P; return s; };
+    if ((st = upload_dir(P, hf, &P->tab[0])) != GRAPE_OK) return bail(st);
+    if ((st = upload_dir(P, ha, &P->tab[1])) != GRAPE_OK) return bail(st);
+    int omax = 0;
+    for (int dir = 0; dir < 2; ++dir) {
+        const HostDir &h = dir ? ha : hf;
+        for (int o : h.off) omax = std::max(omax, std::abs(o));
+        for (size_t q = 0; q < h.oL.size(); ++q)
+            omax = std::max(omax, std::max(std::abs(h.oL[q]), std::abs(h.oR[q])));
+    }
+    if ((st = choose_geometry(P, omax)) != GRAPE_OK) return bail(st);
+    if ((st = upload(P, rho0, &P->d_rho0)) != GRAPE_OK) return bail(st);
+    if ((st = upload(P, sig, &P->d_sigma)) != GRAPE_OK) return bail(st);
+    double2 *cb = nullptr;
+    if ((st = upload(P, cbv, &cb)) != GRAPE_OK) return bail(st);
+    tr.cb_val = cb;
+    P->trace = tr;
+    P->d_x = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
+    P->d_mu = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
+    P->d_u = static_cast<double *>(P->alloc((size_t)P->n_slices * std::max(P->R, 1) * sizeof(double)));
+    P->d_F = static_cast<double *>(P->alloc(sizeof(double)));
+    P->d_G = static_cast<double *>(P->alloc((size_t)P->n_slices * std::max(P->R, 1) * sizeof(double)));
+    if (!P->d_x || !P->d_mu || !P->d_u || !P->d_F || !P->d_G) return bail(fail(GRAPE_ENOMEM, "cudaMalloc failed"));
+    *out = P;
+    return GRAPE_OK;
+}
+
+grape_status grape_problem_destroy(grape_problem_t P) {
+    if (!P) return GRAPE_OK;
+    DeviceGuard g(P->device);
+    delete P;
+    return GRAPE_OK;
+}
+
+grape_status grape_problem_memory(grape_problem_t P, size_t *bytes) {
+    if (!P || !bytes) return fail(GRAPE_EINVAL, "NULL argument");
+    *bytes = P->bytes;
+    return GRAPE_OK;
+}
+
+grape_status grape_problem_geometry(grape_problem_t P, int32_t *cluster, int32_t *threads,
+                                    int32_t *ept) {
+    if (!P) return fail(GRAPE_EINVAL, "NULL problem");
+    if (cluster) *cluster = P->ncl;
+    if (threads) *threads = P->threads;
+    if (ept) *ept = P->ept;
+    return GRAPE_OK;
+}
+
+grape_status grape_set_profiling(grape_problem_t P, int32_t on) {
+    if (!P) return fail(GRAPE_EINVAL, "NULL problem");
+    P->profiling = (on != 0);
+    return GRAPE_OK;
+}
+
+grape_status grape_phase_times(grape_problem_t P, double ms[4], int32_t launches[4]) {
+    if (!P || !ms || !launches) return fail(GRAPE_EINVAL, "NULL argument");
+    DeviceGuard g(P->device);
+    for (int i = 0; i < 4; ++i) { ms[i] = 0.0; launches[i] = 0; }
+    grape_status st = GRAPE_OK;
+    for (auto &m : P->marks) {
+        float t = 0.0f;
+        cudaError_t e = cudaEventSynchronize(m.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, m.a, m.b);
+        if (e != cudaSuccess && st == GRAPE_OK)
+            st = fail(GRAPE_ECUDA, std::string("event timing: ") + cudaGetErrorString(e));
+        ms[m.phase] += t;
+        launches[m.phase] += 1;
+        P->event_pool.push_back(m.a);
+        P->event_pool.push_back(m.b);
+    }
+    P->marks.clear();
+    return st;
+}
+
+int32_t grape_gradient_launches(grape_problem_t P) {
+    if (!P) return -1;
+    if (P->nseg <= 1) return 4;
+    return 2 + 3 * P->nseg;
+}
+
+grape_status grape_forward(grape_problem_t P, const double *u, double *F, double *rhoT,
+                           void *stream) {
+    if (!P || !F) return fail(GRAPE_EINVAL, "NULL problem or F");
+    DeviceGuard g(P->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double *ud;
+    grape_status st;
+    if ((st = stage_inputs(P, u, &ud, s)) != GRAPE_OK) return st;
+    PropArgs a = base_args(P, 0, ud);
+    a.sub_begin = 0;
+    a.sub_end = (long long)P->n_slices * P->n_rk;
+    a.x_in = P->d_rho0;
+    a.x_out = P->d_x;
+    if ((st = launch_prop(P, a, s)) != GRAPE_OK) return st;
+    const bool f_dev = is_device_ptr(F);
+    if ((st = timed(P, PH_COST, s, [&] {
+             return grape_launch_cost(P->d_x, P->d_sigma, P->ns, (int)P->d2, f_dev ? F : P->d_F, s);
+         })) != GRAPE_OK)
+        return st;
+    bool sync = false;
+    if (rhoT) {
+        const size_t nb = P->d2 * P->ns * sizeof(double2);
+        const bool r_dev = is_device_ptr(rhoT);
+        GRAPE_CUDA_TRY(cudaMemcpyAsync(rhoT, P->d_x, nb,
+                                       r_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        sync |= !r_dev;
+    }
+    if (!f_dev) {
+        GRAPE_CUDA_TRY(cudaMemcpyAsync(F, P->d_F, sizeof(double), cudaMemcpyDeviceToHost, s));
+        sync = true;
+    }
+    if (sync) GRAPE_CUDA_TRY(cudaStreamSynchronize(s));
+    return GRAPE_OK;
+}
+
+grape_status grape_gradient(grape_problem_t P, const double *u, double *F, double *grad,
+                            void *stream) {
+    if (!P || !F || (!grad && P->R > 0)) return fail(GRAPE_EINVAL, "NULL problem, F or grad");
+    DeviceGuard g(P->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    grape_status st;
+    if ((st = plan_gradient(P)) != GRAPE_OK) return st;
+    const double *ud;
+    if ((st = stage_inputs(P, u, &ud, s)) != GRAPE_OK) return st;
+    const bool f_dev = is_device_ptr(F);
+    const bool g_dev = grad && is_device_ptr(grad);
+    double *Gout = g_dev ? grad : P->d_G;
+    const bool exact = (P->mode == GRAPE_GRAD_EXACT);
+    const long long nsub = (long long)P->n_slices * P->n_rk;
+    const double dt = P->T / P->n_slices;
+    const size_t mat = P->d2 * P->ns;
+
+    // forward sweep: stage storage directly (one segment) or checkpoints
+    PropArgs f = base_args(P, 0, ud);
+    f.sub_begin = 0;
+    f.sub_end = nsub;
+    f.x_in = P->d_rho0;
+    f.x_out = P->d_x;
+    if (P->nseg == 1) {
+        if (exact) f.stage_store = P->d_Y;
+        else { f.bound_store = P->d_Y; f.bound_step = P->n_rk; }
+    } else {
+        f.bound_store = P->d_ckpt;
+        f.bound_step = (long long)P->seg * P->n_rk;
+    }
+    if ((st = launch_prop(P, f, s)) != GRAPE_OK) return st;
+    if ((st = timed(P, PH_COST, s, [&] {
+             return grape_launch_cost(P->d_x, P->d_sigma, P->ns, (int)P->d2, f_dev ? F : P->d_F, s);
+         })) != GRAPE_OK)
+        return st;
+    GRAPE_CUDA_TRY(cudaMemcpyAsync(P->d_mu, P->d_sigma, mat * sizeof(double2),
+                                   cudaMemcpyDeviceToDevice, s));
+    for (int gi = P->nseg - 1; gi >= 0; --gi) {
+        const long long j0 = (long long)gi * P->seg;
+        const long long j1 = std::min<long long>(P->n_slices, j0 + P->seg);
+        if (P->nseg > 1) {   // recompute the segment's forward stage inputs from its checkpoint
+            PropArgs r = base_args(P, 0, ud);
+            r.sub_begin = j0 * P->n_rk;
+            r.sub_end = j1 * P->n_rk;
+            r.x_in = P->d_ckpt + (size_t)gi * mat;
+            r.x_out = P->d_x;
+            if (exact) r.stage_store = P->d_Y;
+            else { r.bound_store = P->d_Y; r.bound_step = P->n_rk; }
+            if ((st = launch_prop(P, r, s)) != GRAPE_OK) return st;
+        }
+        PropArgs b = base_args(P, 1, ud);
+        b.sub_begin = j0 * P->n_rk;
+        b.sub_end = j1 * P->n_rk;
+        b.reverse = 1;
+        b.x_in = P->d_mu;
+        b.x_out = P->d_mu;
+        if (exact) b.stage_store = P->d_K;
+        else { b.bound_store = P->d_K; b.bound_step = P->n_rk; }
+        if ((st = launch_prop(P, b, s)) != GRAPE_OK) return st;
+        TraceArgs t = P->trace;
+        t.n_rows = (int)(j1 - j0);
+        t.G = Gout + (size_t)j0 * P->R;
+        if (exact) {
+            t.K = P->d_K;
+            t.Y = P->d_Y;
+            t.npairs = (long long)P->n_rk * 4 * P->ns;
+            t.weight = 1.0;
+        } else {
+            t.K = P->d_K + mat;   // lambda_{j+1}, rho_{j+1} pair with row j
+            t.Y = P->d_Y + mat;
+            t.npairs = P->ns;
+            t.weight = dt;
+        }
+        if (P->R > 0 && (st = timed(P, PH_TRACE, s, [&] { return grape_launch_trace(t, s); })) != GRAPE_OK)
+            return st;
+    }
+    bool sync = false;
+    if (!f_dev) {
+        GRAPE_CUDA_TRY(cudaMemcpyAsync(F, P->d_F, sizeof(double), cudaMemcpyDeviceToHost, s));
+        sync = true;
+    }
+    if (grad && !g_dev && P->R > 0) {
+        GRAPE_CUDA_TRY(cudaMemcpyAsync(grad, P->d_G, (size_t)P->n_slices * P->R * sizeof(double),
+                                       cudaMemcpyDeviceToHost, s));
+        sync = true;
+    }
+    if (sync) GRAPE_CUDA_TRY(cudaStreamSynchronize(s));
+    return GRAPE_OK;
+}
+
+}  // extern "C"

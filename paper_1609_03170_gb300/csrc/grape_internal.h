@@ -1,0 +1,82 @@
+// grape_internal.h - kernel argument blocks shared by grape_kernels.cu and
+// grape_api.cu.  Not part of the public ABI (include/grape.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define GRAPE_MAXB 12    // bands of the (effective) Hamiltonian part A
+#define GRAPE_MAXT 12    // jump sandwich terms vL[i] conj(vR[j]) X[i+oL][j+oR]
+#define GRAPE_MAXR 8     // control Hamiltonians
+#define GRAPE_MAXCB 8    // (control, band) pairs seen by the trace kernel
+#define GRAPE_MAXDO 8    // distinct band offsets among the control bands
+
+// One direction of the Lindblad action in the common form
+//   W = -i (A X - X A^+) + sum_t vL_t[i] conj(vR_t[j]) X[i + oL_t][j + oR_t]
+// Forward (Eq. master):   A = H_eff = H_0 - i/2 sum gamma c^+ c + sum_k u_k H_k,
+//                         terms from sqrt(gamma) c_m (all band pairs).
+// Dual (adjoint):         A = -H_eff^+, terms from sqrt(gamma) c_m^+.
+// A(u) = A0 + sum_k u_k Ak is rebuilt in shared memory once per slice.
+struct PropTables {
+    int nb, nt;
+    int off[GRAPE_MAXB];        // band offsets o_b: A_b[i] = A[i][i + o_b]
+    int off_row[GRAPE_MAXB];    // o_b * d (flat shift of row i -> i + o_b)
+    int jflat[GRAPE_MAXT];      // oL_t * d + oR_t
+    const double2 *A0;          // [nb][d]
+    const double2 *Ak;          // [R][nb][d]
+    const double2 *vL;          // [nt][d]
+    const double2 *vR;          // [nt][d]
+};
+
+// One RK4 sweep over substeps [sub_begin, sub_end) of one segment.  The
+// per-substep recurrence for a base value x (rho forward, mu adjoint) is
+//   z_0 = g0 x;  for s = 0..3:  w_s = Op(z_s);  acc += a_s w_s;
+//                               z_{s+1} = g_{s+1} x + b_{s+1} w_s
+//   x <- acc (acc starts at x)
+// which is classic RK4 forward (g = 1, a = h(1/6,1/3,1/3,1/6),
+// b = h(-,1/2,1/2,1)) and its exact reverse-mode adjoint backward
+// (g = h(1/6,1/3,1/3,1/6), a = 1, b = h(-,1,1/2,1/2)).
+struct PropArgs {
+    PropTables tab;
+    int d, R, n_states;
+    int ncl, chunk, halo, win, reach;   // cluster split of the d*d matrix
+    const double *u;                    // [n_slices][R]
+    int n_rk;
+    long long sub_begin, sub_end;       // substep range
+    int reverse;
+    double g[4], a[4], b[4];
+    int store_map[4];                   // stage s -> slot of the stage store
+    const double2 *x_in;                // [n_states][d*d]
+    double2 *x_out;                     // [n_states][d*d] (may alias x_in)
+    double2 *stage_store;               // [(n - sub_begin)][4][n_states][d*d] or null
+    double2 *bound_store;               // [slot][n_states][d*d] or null
+    long long bound_step;               // substeps between bound stores
+};
+
+// Trace products of the gradient (Eq. dphidu), per output row j:
+//   G[j][k] = weight * sum_q (-2) Im sum_b sum_m Hk_b[m] P_{o_b}[m],
+//   P_o[m]  = sum_l K_q[m + o][l] conj(Y_q[m][l]),
+// i.e. -2 Im Tr(K Y H_k) = Re Tr(K (-i)[H_k, Y]) for Hermitian K and Y.
+struct TraceArgs {
+    int d, R;
+    int ncb, ndo;
+    int cb_k[GRAPE_MAXCB];      // control of band entry c
+    int cb_do[GRAPE_MAXCB];     // distinct-offset index of band entry c
+    int do_off[GRAPE_MAXDO];    // distinct offsets
+    const double2 *cb_val;      // [ncb][d]  Hk_b[m]
+    const double2 *K;           // adjoint-side matrices
+    const double2 *Y;           // forward-side matrices
+    long long npairs;           // matrices per output row
+    int n_rows;
+    double weight;
+    double *G;                  // [n_rows][R]
+};
+
+cudaError_t grape_launch_prop(const PropArgs &p, int threads, int ept, size_t smem,
+                              cudaStream_t stream);
+cudaError_t grape_prepare_prop(int ept, size_t smem, int ncl);
+cudaError_t grape_max_active_clusters(int threads, int ept, size_t smem, int ncl,
+                                      int n_blocks, int *clusters);
+cudaError_t grape_launch_trace(const TraceArgs &p, cudaStream_t stream);
+cudaError_t grape_launch_cost(const double2 *rho, const double2 *sigma, int n_states,
+                              int d2, double *F, cudaStream_t stream);

@@ -1,0 +1,204 @@
+"""Open-GRAPE problems as banded operators, and the Python front end of the C ABI.
+
+``band_model(phys)`` writes the dispersive transmon-resonator model (Eq.
+Hdrive with sigma_z replaced by a per-level shift, Eq. kerr, Eq. ME, the
+two-quadrature drive of Sec. 4.2) directly as DIA bands in the basis
+i = n*Q + q: the resonator operators a, a^dag sit on offsets +-Q, the
+transmon ladder b, b^dag on +-1 and every number operator on the diagonal.
+
+``GrapeProblem`` owns one ``grape_problem_t`` and marshals arguments for
+``grape_forward`` / ``grape_gradient``: numpy inputs are passed as host
+pointers, CUDA torch tensors as device pointers (outputs then stay on the
+device).  All computation happens in libgrape.so.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _lib
+
+
+@dataclasses.dataclass
+class BandOp:
+    """Op[i][i + offsets[b]] = values[b, i]."""
+    offsets: np.ndarray     # int32 [n_diag]
+    values: np.ndarray      # complex128 [n_diag, d]
+
+    @staticmethod
+    def make(d: int, bands: Sequence[Tuple[int, np.ndarray]]) -> "BandOp":
+        bands = [(o, v) for o, v in bands if -d < o < d]     # bands outside the matrix are empty
+        offs = np.array([o for o, _ in bands], dtype=np.int32)
+        vals = np.zeros((len(bands), d), dtype=np.complex128)
+        for b, (_, v) in enumerate(bands):
+            vals[b] = v
+        return BandOp(offs, vals)
+
+
+@dataclasses.dataclass
+class BandModel:
+    d: int
+    H0: BandOp
+    Hc: List[BandOp]
+    jumps: List[BandOp]
+    rates: np.ndarray
+
+
+def band_model(phys) -> BandModel:
+    Q, N = phys.Q, phys.N
+    d = Q * N
+    i = np.arange(d)
+    n = i // Q
+    q = i % Q
+    up_res = np.where(n + 1 < N, np.sqrt(n + 1.0), 0.0)      # a[i][i+Q]
+    dn_res = np.sqrt(n.astype(float))                         # a^dag[i][i-Q]
+    up_qub = np.where(q + 1 < Q, np.sqrt(q + 1.0), 0.0)      # b[i][i+1]
+    dn_qub = np.sqrt(q.astype(float))                         # b^dag[i][i-1]
+
+    chi = np.asarray(phys.chi, dtype=float)[q]
+    diag = chi * n + phys.delta * n + phys.kerr * n.astype(float) ** 2
+    if phys.qubit_energy:
+        diag = diag + np.asarray(phys.qubit_energy, dtype=float)[q]
+    H0 = BandOp.make(d, [(0, diag.astype(np.complex128))])
+
+    kinds = {
+        "res_x": [(Q, up_res + 0j), (-Q, dn_res + 0j)],
+        "res_y": [(Q, -1j * up_res), (-Q, 1j * dn_res)],
+        "qub_x": [(1, up_qub + 0j), (-1, dn_qub + 0j)],
+        "qub_y": [(1, -1j * up_qub), (-1, 1j * dn_qub)],
+    }
+    Hc = [BandOp.make(d, kinds[k]) for k in phys.controls]
+
+    jumps, rates = [BandOp.make(d, [(Q, up_res + 0j)])], [phys.kappa]
+    if phys.gamma1:
+        jumps.append(BandOp.make(d, [(1, up_qub + 0j)])); rates.append(phys.gamma1)
+    if phys.gamma_phi:
+        jumps.append(BandOp.make(d, [(0, q.astype(np.complex128))])); rates.append(phys.gamma_phi)
+    return BandModel(d=d, H0=H0, Hc=Hc, jumps=jumps, rates=np.array(rates, dtype=np.float64))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _is_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class GrapeProblem:
+    """One open-GRAPE gradient problem resident on the current CUDA device."""
+
+    def __init__(self, model: BandModel, rho0: np.ndarray, sigma: np.ndarray, T: float,
+                 n_slices: int, n_rk: int, grad_mode: int = _lib.GRAPE_GRAD_EXACT,
+                 ckpt_stride: int = 0):
+        _lib.load()
+        d = model.d
+        rho0 = np.ascontiguousarray(rho0, dtype=np.complex128)
+        sigma = np.ascontiguousarray(sigma, dtype=np.complex128)
+        if rho0.ndim == 2:
+            rho0 = rho0[None]
+        self.d, self.n_states = d, rho0.shape[0]
+        self.n_slices, self.n_rk, self.T = int(n_slices), int(n_rk), float(T)
+        self.R = len(model.Hc)
+        keep = []
+
+        def band(op: BandOp) -> _lib.grape_band_op:
+            offs = np.ascontiguousarray(op.offsets, dtype=np.int32)
+            vals = np.ascontiguousarray(op.values, dtype=np.complex128).view(np.float64)
+            keep.extend([offs, vals])
+            return _lib.grape_band_op(len(offs), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      _dptr(vals))
+
+        Hc = (_lib.grape_band_op * max(1, self.R))(*[band(h) for h in model.Hc])
+        J = len(model.jumps)
+        jumps = (_lib.grape_band_op * max(1, J))(*[band(c) for c in model.jumps])
+        rates = np.ascontiguousarray(model.rates, dtype=np.float64)
+        rho_f = rho0.view(np.float64)
+        sig_f = sigma.view(np.float64)
+        desc = _lib.grape_problem_desc(
+            d, self.R, J, self.n_states, self.n_slices, self.n_rk, self.T,
+            band(model.H0), Hc, jumps, _dptr(rates), _dptr(rho_f), _dptr(sig_f),
+            1 if sigma.ndim == 2 else 0, int(grad_mode), int(ckpt_stride))
+        self._h = _lib.grape_problem_create(desc)
+        del keep
+
+    @classmethod
+    def from_workload(cls, w, grad_mode: int = _lib.GRAPE_GRAD_EXACT, ckpt_stride: int = 0):
+        return cls(band_model(w.phys), w.rho0, w.sigma, w.T, w.n_slices, w.n_rk,
+                   grad_mode=grad_mode, ckpt_stride=ckpt_stride)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.grape_problem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- queries ----------------------------------------------------------
+    @property
+    def handle(self):
+        return self._h
+
+    def memory_bytes(self) -> int:
+        return _lib.grape_problem_memory(self._h)
+
+    def geometry(self):
+        return _lib.grape_problem_geometry(self._h)
+
+    def gradient_launches(self) -> int:
+        return _lib.grape_gradient_launches(self._h)
+
+    def set_profiling(self, on: bool = True) -> None:
+        _lib.grape_set_profiling(self._h, on)
+
+    def phase_times(self):
+        return _lib.grape_phase_times(self._h)
+
+    # -- compute ----------------------------------------------------------
+    def forward(self, u, stream=None, want_rho=True):
+        """Phi and rho(T).  numpy u -> numpy results; CUDA tensor u -> CUDA tensors."""
+        if _is_cuda(u):
+            import torch
+            F = torch.empty(1, dtype=torch.float64, device=u.device)
+            rho = (torch.empty((self.n_states, self.d, self.d), dtype=torch.complex128,
+                               device=u.device) if want_rho else None)
+            _lib.grape_forward(self._h, u.data_ptr(), F.data_ptr(),
+                               rho.data_ptr() if rho is not None else 0, _stream_ptr(stream))
+            return F, rho
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        F = np.zeros(1)
+        rho = np.zeros((self.n_states, self.d, self.d), dtype=np.complex128) if want_rho else None
+        _lib.grape_forward(self._h, u.ctypes.data, F.ctypes.data,
+                           rho.ctypes.data if rho is not None else 0, _stream_ptr(stream))
+        return float(F[0]), rho
+
+    def gradient(self, u, stream=None, out=None):
+        """Phi and dPhi/du (n_slices x R)."""
+        if _is_cuda(u):
+            import torch
+            F = torch.empty(1, dtype=torch.float64, device=u.device)
+            G = out if out is not None else torch.empty((self.n_slices, self.R),
+                                                        dtype=torch.float64, device=u.device)
+            _lib.grape_gradient(self._h, u.data_ptr(), F.data_ptr(), G.data_ptr(),
+                                _stream_ptr(stream))
+            return F, G
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        F = np.zeros(1)
+        G = np.zeros((self.n_slices, self.R))
+        _lib.grape_gradient(self._h, u.ctypes.data, F.ctypes.data, G.ctypes.data,
+                            _stream_ptr(stream))
+        return float(F[0]), G
