@@ -123,6 +123,29 @@ grape_status grape_problem_geometry(grape_problem_t problem, int32_t *cluster,
 grape_status grape_set_profiling(grape_problem_t problem, int32_t on);
 grape_status grape_phase_times(grape_problem_t problem, double ms[4], int32_t launches[4]);
 
+/* grape_gradient without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need a gradient - code whose allocator owns all of
+ * the device memory, host callbacks where cudaMalloc may not be called, or
+ * latency-bound loops that must not wait on the allocator.  The problem is
+ * created beforehand with grape_problem_create; the stage storage, the
+ * propagated states and any checkpoints come from one file-scope device
+ * array of 64 MiB that every GPU loading libgrape.so holds until the process
+ * exits.  u, F and grad must be device pointers on the problem's device
+ * (GRAPE_EINVAL otherwise); a problem whose scratch exceeds 64 MiB even with
+ * one-slice checkpoint segments is rejected with GRAPE_EINVAL and a message
+ * giving the bytes it needs.  The call makes no cudaMalloc/cudaFree and no
+ * host allocation of its own; it only enqueues work on `stream`.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (nothing in it needs to start at zero: every buffer is
+ * written before it is read), so calls whose GPU work overlaps - on two
+ * streams, or from two threads - race and give wrong results: serialise them.
+ * Results equal those of grape_gradient. */
+grape_status grape_gradient_static(grape_problem_t problem, const double *u, double *F,
+                                   double *grad, void *stream);
+
 /* Kernel launches one grape_gradient call makes (for launch accounting). */
 int32_t grape_gradient_launches(grape_problem_t problem);
 

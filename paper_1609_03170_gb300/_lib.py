@@ -45,7 +45,8 @@ _lib = None
 
 EXPORTS = ["grape_problem_create", "grape_problem_destroy", "grape_forward", "grape_gradient",
            "grape_problem_memory", "grape_problem_geometry", "grape_set_profiling",
-           "grape_phase_times", "grape_gradient_launches", "grape_last_error", "grape_version"]
+           "grape_phase_times", "grape_gradient_launches", "grape_gradient_static",
+           "grape_last_error", "grape_version"]
 
 
 def library_path() -> str:
@@ -71,6 +72,8 @@ def load(build_if_missing: bool = True):
     lib.grape_forward.restype = c_int32
     lib.grape_gradient.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.grape_gradient.restype = c_int32
+    lib.grape_gradient_static.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.grape_gradient_static.restype = c_int32
     lib.grape_problem_memory.argtypes = [c_void_p, P(c_size_t)]
     lib.grape_problem_memory.restype = c_int32
     lib.grape_problem_geometry.argtypes = [c_void_p, P(c_int32), P(c_int32), P(c_int32)]
@@ -113,6 +116,13 @@ def grape_forward(h, u_ptr: int, F_ptr: int, rhoT_ptr: int, stream_ptr: int) -> 
 def grape_gradient(h, u_ptr: int, F_ptr: int, grad_ptr: int, stream_ptr: int) -> None:
     check(load().grape_gradient(h, u_ptr or None, F_ptr or None, grad_ptr or None,
                                 stream_ptr or None), "grape_gradient")
+
+
+def grape_gradient_static(h, u_ptr: int, F_ptr: int, grad_ptr: int, stream_ptr: int) -> None:
+    """grape_gradient with every scratch buffer in the library's static device
+    array (no device allocation); u, F and grad must be device pointers."""
+    check(load().grape_gradient_static(h, u_ptr or None, F_ptr or None, grad_ptr or None,
+                                       stream_ptr or None), "grape_gradient_static")
 
 
 def grape_problem_memory(h) -> int:

@@ -800,3 +800,136 @@ grape_status grape_gradient(grape_problem_t P, const double *u, double *F, doubl
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// grape_gradient_static: the gradient without any device allocation.
+//
+// For callers that cannot allocate device memory at the time they need a
+// gradient - code running under a custom or pool allocator that owns all of
+// the device memory, callbacks and host functions where cudaMalloc may not be
+// called, or real-time loops that must not block on the allocator.  The
+// problem tables are created beforehand by grape_problem_create; every buffer
+// the gradient needs beyond its inputs and outputs (RK stage storage of the
+// forward and adjoint sweeps, checkpoints, the propagated state) comes from
+// the file-scope array below instead of cudaMalloc.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;   // 64 MiB per device
+constexpr int kMaxDevices = 64;
+
+// Device memory held by every GPU that loads this library, until exit.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch per device, looked up once per device.
+// In host code the symbol name is only a host-side stand-in, never a device
+// address, so it must go through cudaGetSymbolAddress.
+void *g_static_ptr[kMaxDevices] = {};
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" {
+
+grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F, double *grad,
+                                   void *stream) {
+    if (!P || !u || !F || (!grad && P->R > 0)) return fail(GRAPE_EINVAL, "NULL problem, u, F or grad");
+    if (P->device < 0 || P->device >= kMaxDevices) return fail(GRAPE_EINVAL, "device index too large");
+    DeviceGuard g(P->device);
+    if (!is_device_ptr(u) || !is_device_ptr(F) || (P->R > 0 && !is_device_ptr(grad)))
+        return fail(GRAPE_EINVAL, "grape_gradient_static takes device pointers for u, F and grad");
+    if (!g_static_ptr[P->device]) {   // once per device, with that device current
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(GRAPE_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") +
+                                         cudaGetErrorString(e));
+        g_static_ptr[P->device] = ptr;
+    }
+    unsigned char *base = static_cast<unsigned char *>(g_static_ptr[P->device]);
+
+    // scratch plan: propagated state, adjoint state, stage storage of one
+    // segment (forward and adjoint) and, with several segments, checkpoints
+    const bool exact = (P->mode == GRAPE_GRAD_EXACT);
+    const size_t mat = align256(P->d2 * P->ns * sizeof(double2));
+    auto per_seg = [&](long long sg) {
+        return align256(exact ? (size_t)sg * P->n_rk * 4 * P->d2 * P->ns * sizeof(double2)
+                              : (size_t)(sg + 1) * P->d2 * P->ns * sizeof(double2));
+    };
+    auto need = [&](long long sg) {
+        const long long ns = (P->n_slices + sg - 1) / sg;
+        return 2 * mat + 2 * per_seg(sg) + (ns > 1 ? (size_t)(ns + 1) * mat : 0);
+    };
+    long long seg = P->n_slices;
+    while (seg > 1 && need(seg) > kStaticScratchBytes) seg = (seg + 1) / 2;
+    if (need(seg) > kStaticScratchBytes)
+        return fail(GRAPE_EINVAL, "problem needs " + std::to_string(need(seg)) +
+                                      " bytes of scratch; the static scratch holds " +
+                                      std::to_string(kStaticScratchBytes));
+    const int nseg = (int)((P->n_slices + seg - 1) / seg);
+    double2 *x = reinterpret_cast<double2 *>(base);
+    double2 *mu = reinterpret_cast<double2 *>(base + mat);
+    double2 *Y = reinterpret_cast<double2 *>(base + 2 * mat);
+    double2 *K = reinterpret_cast<double2 *>(base + 2 * mat + per_seg(seg));
+    double2 *ckpt = reinterpret_cast<double2 *>(base + 2 * mat + 2 * per_seg(seg));
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long nsub = (long long)P->n_slices * P->n_rk;
+    const size_t m = P->d2 * P->ns;
+    PropArgs f = base_args(P, 0, u);
+    f.sub_begin = 0;
+    f.sub_end = nsub;
+    f.x_in = P->d_rho0;
+    f.x_out = x;
+    if (nseg == 1) {
+        if (exact) f.stage_store = Y;
+        else { f.bound_store = Y; f.bound_step = P->n_rk; }
+    } else {
+        f.bound_store = ckpt;
+        f.bound_step = seg * P->n_rk;
+    }
+    GRAPE_CUDA_TRY(grape_launch_prop(f, P->threads, P->ept, P->smem, s));
+    GRAPE_CUDA_TRY(grape_launch_cost(x, P->d_sigma, P->ns, (int)P->d2, F, s));
+    GRAPE_CUDA_TRY(cudaMemcpyAsync(mu, P->d_sigma, m * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    for (int gi = nseg - 1; gi >= 0; --gi) {
+        const long long j0 = (long long)gi * seg;
+        const long long j1 = std::min<long long>(P->n_slices, j0 + seg);
+        if (nseg > 1) {
+            PropArgs r = base_args(P, 0, u);
+            r.sub_begin = j0 * P->n_rk;
+            r.sub_end = j1 * P->n_rk;
+            r.x_in = ckpt + (size_t)gi * m;   // the kernel writes checkpoints back to back
+            r.x_out = x;
+            if (exact) r.stage_store = Y;
+            else { r.bound_store = Y; r.bound_step = P->n_rk; }
+            GRAPE_CUDA_TRY(grape_launch_prop(r, P->threads, P->ept, P->smem, s));
+        }
+        PropArgs b = base_args(P, 1, u);
+        b.sub_begin = j0 * P->n_rk;
+        b.sub_end = j1 * P->n_rk;
+        b.reverse = 1;
+        b.x_in = mu;
+        b.x_out = mu;
+        if (exact) b.stage_store = K;
+        else { b.bound_store = K; b.bound_step = P->n_rk; }
+        GRAPE_CUDA_TRY(grape_launch_prop(b, P->threads, P->ept, P->smem, s));
+        TraceArgs t = P->trace;
+        t.n_rows = (int)(j1 - j0);
+        t.G = grad + (size_t)j0 * P->R;
+        if (exact) {
+            t.K = K;
+            t.Y = Y;
+            t.npairs = (long long)P->n_rk * 4 * P->ns;
+            t.weight = 1.0;
+        } else {
+            t.K = K + m;
+            t.Y = Y + m;
+            t.npairs = P->ns;
+            t.weight = P->T / P->n_slices;
+        }
+        if (P->R > 0) GRAPE_CUDA_TRY(grape_launch_trace(t, s));
+    }
+    return GRAPE_OK;
+}
+
+}  // extern "C"
