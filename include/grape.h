@@ -45,6 +45,13 @@ typedef enum {
 } grape_status;
 
 typedef enum {
+    GRAPE_PREC_DF64 = 0,   /* double-float: pairs of FP32 numbers, ~48-bit significands,
+                              on the FP32 pipes (default; GB300 issues FP32 ~67x faster
+                              than FP64) */
+    GRAPE_PREC_FP64 = 1    /* native FP64 */
+} grape_precision;
+
+typedef enum {
     GRAPE_GRAD_EXACT = 0,        /* exact derivative of the discrete RK4 map */
     GRAPE_GRAD_FIRST_ORDER = 1   /* the paper's Eq. (dphidu), first order in dt */
 } grape_grad_mode;
@@ -75,7 +82,10 @@ typedef struct {
     const double *sigma;        /* [n_states or 1][d][d] complex target/observable */
     int32_t sigma_broadcast;    /* 1: one sigma for all states */
     int32_t grad_mode;          /* grape_grad_mode */
-    int32_t ckpt_stride;        /* reserved, 0 */
+    int32_t ckpt_stride;        /* slices per checkpoint segment of the gradient;
+                                   0 = automatic (no recomputation when the stage
+                                   storage fits in 60% of the free device memory) */
+    int32_t precision;          /* grape_precision of the kernels */
 } grape_problem_desc;
 
 typedef struct grape_problem *grape_problem_t;

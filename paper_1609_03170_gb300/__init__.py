@@ -7,10 +7,12 @@ the C ABI of ``include/grape.h`` (``libgrape.so``).  This package holds the
 build script, the ctypes binding and the problem front end.
 """
 from . import _lib
-from ._lib import (GRAPE_GRAD_EXACT, GRAPE_GRAD_FIRST_ORDER, GrapeError, grape_forward,
+from ._lib import (GRAPE_GRAD_EXACT, GRAPE_GRAD_FIRST_ORDER, GRAPE_PREC_DF64, GRAPE_PREC_FP64,
+                   GrapeError, grape_forward,
                    grape_gradient, grape_problem_create, grape_problem_destroy)
 from .problem import BandModel, BandOp, GrapeProblem, band_model
 
-__all__ = ["GRAPE_GRAD_EXACT", "GRAPE_GRAD_FIRST_ORDER", "GrapeError", "GrapeProblem",
+__all__ = ["GRAPE_GRAD_EXACT", "GRAPE_GRAD_FIRST_ORDER", "GRAPE_PREC_DF64", "GRAPE_PREC_FP64",
+           "GrapeError", "GrapeProblem",
            "BandModel", "BandOp", "band_model", "grape_forward", "grape_gradient",
            "grape_problem_create", "grape_problem_destroy"]

@@ -17,6 +17,7 @@ P = ctypes.POINTER
 GRAPE_OK, GRAPE_EINVAL, GRAPE_ENOMEM, GRAPE_ECUDA, GRAPE_ETIMEOUT, GRAPE_EBUSY, \
     GRAPE_ENOTREADY, GRAPE_EINTERNAL = range(8)
 GRAPE_GRAD_EXACT, GRAPE_GRAD_FIRST_ORDER = 0, 1
+GRAPE_PREC_DF64, GRAPE_PREC_FP64 = 0, 1
 
 STATUS_NAMES = {0: "GRAPE_OK", 1: "GRAPE_EINVAL", 2: "GRAPE_ENOMEM", 3: "GRAPE_ECUDA",
                 4: "GRAPE_ETIMEOUT", 5: "GRAPE_EBUSY", 6: "GRAPE_ENOTREADY", 7: "GRAPE_EINTERNAL"}
@@ -32,7 +33,8 @@ class grape_problem_desc(ctypes.Structure):
                 ("T", c_double),
                 ("H0", grape_band_op), ("Hc", P(grape_band_op)), ("jumps", P(grape_band_op)),
                 ("rates", P(c_double)), ("rho0", P(c_double)), ("sigma", P(c_double)),
-                ("sigma_broadcast", c_int32), ("grad_mode", c_int32), ("ckpt_stride", c_int32)]
+                ("sigma_broadcast", c_int32), ("grad_mode", c_int32), ("ckpt_stride", c_int32),
+                ("precision", c_int32)]
 
 
 class GrapeError(RuntimeError):

@@ -9,6 +9,7 @@
 // runs in the kernels of grape_kernels.cu.
 #include "grape.h"
 #include "grape_internal.h"
+#include "grape_num.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -202,6 +203,7 @@ class DeviceGuard {
 struct grape_problem {
     int device = 0;
     int d = 0, R = 0, J = 0, ns = 0, n_slices = 0, n_rk = 0, mode = 0;
+    int prec = GRAPE_PREC_DF64;      // number type of the kernels and of every state buffer
     double T = 0.0;
     size_t d2 = 0;
     int ncl = 1, threads = 256, ept = 1, chunk = 0, halo = 0, win = 0, reach = 0;
@@ -210,8 +212,11 @@ struct grape_problem {
     int seg = 0, nseg = 0;           // gradient segment plan (0 until first gradient)
     PropTables tab[2];               // [0] forward, [1] dual
     TraceArgs trace{};
+    // state buffers hold 16-byte entries in the kernels' storage format
+    // (double2 for FP64, float4 hi/lo pairs for double-float)
     double2 *d_rho0 = nullptr, *d_sigma = nullptr, *d_x = nullptr, *d_mu = nullptr;
     double2 *d_Y = nullptr, *d_K = nullptr, *d_ckpt = nullptr;
+    double2 *d_out = nullptr;        // complex128 staging of rho(T)
     double *d_u = nullptr, *d_F = nullptr, *d_G = nullptr;
     size_t bytes = 0;
     bool profiling = false;
@@ -291,6 +296,36 @@ grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
     return GRAPE_OK;
 }
 
+// Kernel launches in the problem's number type.
+cudaError_t k_prop(const grape_problem *P, const PropArgs &a, cudaStream_t s) {
+    return P->prec == GRAPE_PREC_FP64 ? grape_launch_prop_f64(a, P->threads, P->ept, P->smem, s)
+                                      : grape_launch_prop_df(a, P->threads, P->ept, P->smem, s);
+}
+cudaError_t k_trace(const grape_problem *P, const TraceArgs &t, cudaStream_t s) {
+    return P->prec == GRAPE_PREC_FP64 ? grape_launch_trace_f64(t, s) : grape_launch_trace_df(t, s);
+}
+cudaError_t k_cost(const grape_problem *P, const void *rho, double *F, cudaStream_t s) {
+    return P->prec == GRAPE_PREC_FP64
+               ? grape_launch_cost_f64(rho, P->d_sigma, P->ns, (int)P->d2, F, s)
+               : grape_launch_cost_df(rho, P->d_sigma, P->ns, (int)P->d2, F, s);
+}
+cudaError_t k_to_double(const grape_problem *P, const void *src, double2 *dst, size_t n,
+                        cudaStream_t s) {
+    return P->prec == GRAPE_PREC_FP64 ? grape_launch_to_double_f64(src, dst, n, s)
+                                      : grape_launch_to_double_df(src, dst, n, s);
+}
+
+// complex128 -> one 16-byte storage entry
+double2 encode(const grape_problem *P, cplx v) {
+    if (P->prec == GRAPE_PREC_FP64) return make_double2(v.real(), v.imag());
+    const grape_num::ff re = grape_num::ff_from_double(v.real());
+    const grape_num::ff im = grape_num::ff_from_double(v.imag());
+    const float4 f = make_float4(re.h, re.l, im.h, im.l);
+    double2 out;
+    std::memcpy(&out, &f, sizeof(out));
+    return out;
+}
+
 grape_status choose_geometry(grape_problem *P, int omax) {
     int max_smem = 0;
     GRAPE_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
@@ -311,10 +346,13 @@ grape_status choose_geometry(grape_problem *P, int omax) {
         bool ok = smem <= (size_t)max_smem && ept <= 16;
         if (ok) {
             // the attribute is an upper bound shared by all problems: use the device maximum
-            cudaError_t e = grape_prepare_prop(ept, (size_t)max_smem, ncl);
+            cudaError_t e = P->prec == GRAPE_PREC_FP64 ? grape_prepare_prop_f64(ept, (size_t)max_smem, ncl)
+                                                       : grape_prepare_prop_df(ept, (size_t)max_smem, ncl);
             int clusters = 0;
             if (e == cudaSuccess)
-                e = grape_max_active_clusters(threads, ept, smem, ncl, ncl * P->ns, &clusters);
+                e = P->prec == GRAPE_PREC_FP64
+                        ? grape_max_active_clusters_f64(threads, ept, smem, ncl, ncl * P->ns, &clusters)
+                        : grape_max_active_clusters_df(threads, ept, smem, ncl, ncl * P->ns, &clusters);
             if (e != cudaSuccess) cudaGetLastError();
             ok = (e == cudaSuccess && clusters >= 1);
             if (ok) {
@@ -439,7 +477,7 @@ grape_status timed(grape_problem *P, int phase, cudaStream_t s, F &&launch) {
 
 grape_status launch_prop(grape_problem *P, const PropArgs &a, cudaStream_t s) {
     return timed(P, a.reverse ? PH_ADJOINT : PH_FORWARD, s,
-                 [&] { return grape_launch_prop(a, P->threads, P->ept, P->smem, s); });
+                 [&] { return k_prop(P, a, s); });
 }
 
 grape_status stage_inputs(grape_problem *P, const double *u, const double **u_dev,
@@ -462,7 +500,7 @@ extern "C" {
 
 const char *grape_last_error(void) { return g_last_error.c_str(); }
 
-const char *grape_version(void) { return "grape-gb300 0.1 (sm_103a, fp64)"; }
+const char *grape_version(void) { return "grape-gb300 0.2 (sm_103a, df64/fp64)"; }
 
 grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_t *out) {
     if (!desc || !out) return fail(GRAPE_EINVAL, "NULL descriptor or output");
@@ -477,6 +515,8 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
     if (desc->grad_mode != GRAPE_GRAD_EXACT && desc->grad_mode != GRAPE_GRAD_FIRST_ORDER)
         return fail(GRAPE_EINVAL, "unknown grad_mode");
     if (desc->ckpt_stride < 0) return fail(GRAPE_EINVAL, "ckpt_stride must be >= 0");
+    if (desc->precision != GRAPE_PREC_DF64 && desc->precision != GRAPE_PREC_FP64)
+        return fail(GRAPE_EINVAL, "unknown precision");
     if (!desc->rho0 || !desc->sigma) return fail(GRAPE_EINVAL, "rho0 and sigma are required");
     if (desc->n_controls > 0 && !desc->Hc) return fail(GRAPE_EINVAL, "Hc is NULL");
     if (desc->n_jumps > 0 && (!desc->jumps || !desc->rates)) return fail(GRAPE_EINVAL, "jumps/rates NULL");
@@ -521,7 +561,7 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
 
     // initial states (Hermitian) and the Hermitian part of sigma
     const size_t d2 = (size_t)d * d;
-    std::vector<double2> rho0(d2 * desc->n_states), sig(d2 * desc->n_states);
+    std::vector<cplx> rho0(d2 * desc->n_states), sig(d2 * desc->n_states);
     for (int s = 0; s < desc->n_states; ++s) {
         const double *r = desc->rho0 + 2 * d2 * s;
         double mx = 0.0, asym = 0.0;
@@ -533,7 +573,7 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
                     return fail(GRAPE_EINVAL, "rho0 has non-finite entries");
                 mx = std::max(mx, std::abs(a));
                 asym = std::max(asym, std::abs(a - std::conj(b)));
-                rho0[s * d2 + i * d + j] = make_double2(a.real(), a.imag());
+                rho0[s * d2 + i * d + j] = a;
             }
         if (asym > 1e-12 * std::max(mx, 1e-300)) return fail(GRAPE_EINVAL, "rho0 is not Hermitian");
         const double *g = desc->sigma + (desc->sigma_broadcast ? 0 : 2 * d2 * s);
@@ -544,7 +584,7 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
                 if (!std::isfinite(a.real()) || !std::isfinite(a.imag()))
                     return fail(GRAPE_EINVAL, "sigma has non-finite entries");
                 const cplx hpart = 0.5 * (a + std::conj(b));
-                sig[s * d2 + i * d + j] = make_double2(hpart.real(), hpart.imag());
+                sig[s * d2 + i * d + j] = hpart;
             }
     }
 
@@ -593,6 +633,7 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
     P->T = desc->T;
     P->mode = desc->grad_mode;
     P->ckpt_stride = desc->ckpt_stride;
+    P->prec = desc->precision;
     auto bail = [&](grape_status s) { delete P; return s; };
     if ((st = upload_dir(P, hf, &P->tab[0])) != GRAPE_OK) return bail(st);
     if ((st = upload_dir(P, ha, &P->tab[1])) != GRAPE_OK) return bail(st);
@@ -604,18 +645,24 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
             omax = std::max(omax, std::max(std::abs(h.oL[q]), std::abs(h.oR[q])));
     }
     if ((st = choose_geometry(P, omax)) != GRAPE_OK) return bail(st);
-    if ((st = upload(P, rho0, &P->d_rho0)) != GRAPE_OK) return bail(st);
-    if ((st = upload(P, sig, &P->d_sigma)) != GRAPE_OK) return bail(st);
+    {
+        std::vector<double2> r(rho0.size()), g2(sig.size());
+        for (size_t i = 0; i < r.size(); ++i) r[i] = encode(P, rho0[i]);
+        for (size_t i = 0; i < g2.size(); ++i) g2[i] = encode(P, sig[i]);
+        if ((st = upload(P, r, &P->d_rho0)) != GRAPE_OK) return bail(st);
+        if ((st = upload(P, g2, &P->d_sigma)) != GRAPE_OK) return bail(st);
+    }
     double2 *cb = nullptr;
     if ((st = upload(P, cbv, &cb)) != GRAPE_OK) return bail(st);
     tr.cb_val = cb;
     P->trace = tr;
     P->d_x = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
     P->d_mu = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
+    P->d_out = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
     P->d_u = static_cast<double *>(P->alloc((size_t)P->n_slices * std::max(P->R, 1) * sizeof(double)));
     P->d_F = static_cast<double *>(P->alloc(sizeof(double)));
     P->d_G = static_cast<double *>(P->alloc((size_t)P->n_slices * std::max(P->R, 1) * sizeof(double)));
-    if (!P->d_x || !P->d_mu || !P->d_u || !P->d_F || !P->d_G) return bail(fail(GRAPE_ENOMEM, "cudaMalloc failed"));
+    if (!P->d_x || !P->d_mu || !P->d_out || !P->d_u || !P->d_F || !P->d_G) return bail(fail(GRAPE_ENOMEM, "cudaMalloc failed"));
     *out = P;
     return GRAPE_OK;
 }
@@ -690,16 +737,18 @@ grape_status grape_forward(grape_problem_t P, const double *u, double *F, double
     if ((st = launch_prop(P, a, s)) != GRAPE_OK) return st;
     const bool f_dev = is_device_ptr(F);
     if ((st = timed(P, PH_COST, s, [&] {
-             return grape_launch_cost(P->d_x, P->d_sigma, P->ns, (int)P->d2, f_dev ? F : P->d_F, s);
+             return k_cost(P, P->d_x, f_dev ? F : P->d_F, s);
          })) != GRAPE_OK)
         return st;
     bool sync = false;
     if (rhoT) {
-        const size_t nb = P->d2 * P->ns * sizeof(double2);
+        const size_t n = P->d2 * P->ns;
         const bool r_dev = is_device_ptr(rhoT);
-        GRAPE_CUDA_TRY(cudaMemcpyAsync(rhoT, P->d_x, nb,
-                                       r_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-        sync |= !r_dev;
+        GRAPE_CUDA_TRY(k_to_double(P, P->d_x, r_dev ? reinterpret_cast<double2 *>(rhoT) : P->d_out, n, s));
+        if (!r_dev) {
+            GRAPE_CUDA_TRY(cudaMemcpyAsync(rhoT, P->d_out, n * sizeof(double2), cudaMemcpyDeviceToHost, s));
+            sync = true;
+        }
     }
     if (!f_dev) {
         GRAPE_CUDA_TRY(cudaMemcpyAsync(F, P->d_F, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -741,7 +790,7 @@ grape_status grape_gradient(grape_problem_t P, const double *u, double *F, doubl
     }
     if ((st = launch_prop(P, f, s)) != GRAPE_OK) return st;
     if ((st = timed(P, PH_COST, s, [&] {
-             return grape_launch_cost(P->d_x, P->d_sigma, P->ns, (int)P->d2, f_dev ? F : P->d_F, s);
+             return k_cost(P, P->d_x, f_dev ? F : P->d_F, s);
          })) != GRAPE_OK)
         return st;
     GRAPE_CUDA_TRY(cudaMemcpyAsync(P->d_mu, P->d_sigma, mat * sizeof(double2),
@@ -782,7 +831,7 @@ grape_status grape_gradient(grape_problem_t P, const double *u, double *F, doubl
             t.npairs = P->ns;
             t.weight = dt;
         }
-        if (P->R > 0 && (st = timed(P, PH_TRACE, s, [&] { return grape_launch_trace(t, s); })) != GRAPE_OK)
+        if (P->R > 0 && (st = timed(P, PH_TRACE, s, [&] { return k_trace(P, t, s); })) != GRAPE_OK)
             return st;
     }
     bool sync = false;
@@ -888,8 +937,8 @@ grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F
         f.bound_store = ckpt;
         f.bound_step = seg * P->n_rk;
     }
-    GRAPE_CUDA_TRY(grape_launch_prop(f, P->threads, P->ept, P->smem, s));
-    GRAPE_CUDA_TRY(grape_launch_cost(x, P->d_sigma, P->ns, (int)P->d2, F, s));
+    GRAPE_CUDA_TRY(k_prop(P, f, s));
+    GRAPE_CUDA_TRY(k_cost(P, x, F, s));
     GRAPE_CUDA_TRY(cudaMemcpyAsync(mu, P->d_sigma, m * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     for (int gi = nseg - 1; gi >= 0; --gi) {
         const long long j0 = (long long)gi * seg;
@@ -902,7 +951,7 @@ grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F
             r.x_out = x;
             if (exact) r.stage_store = Y;
             else { r.bound_store = Y; r.bound_step = P->n_rk; }
-            GRAPE_CUDA_TRY(grape_launch_prop(r, P->threads, P->ept, P->smem, s));
+            GRAPE_CUDA_TRY(k_prop(P, r, s));
         }
         PropArgs b = base_args(P, 1, u);
         b.sub_begin = j0 * P->n_rk;
@@ -912,7 +961,7 @@ grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F
         b.x_out = mu;
         if (exact) b.stage_store = K;
         else { b.bound_store = K; b.bound_step = P->n_rk; }
-        GRAPE_CUDA_TRY(grape_launch_prop(b, P->threads, P->ept, P->smem, s));
+        GRAPE_CUDA_TRY(k_prop(P, b, s));
         TraceArgs t = P->trace;
         t.n_rows = (int)(j1 - j0);
         t.G = grad + (size_t)j0 * P->R;
@@ -927,7 +976,7 @@ grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F
             t.npairs = P->ns;
             t.weight = P->T / P->n_slices;
         }
-        if (P->R > 0) GRAPE_CUDA_TRY(grape_launch_trace(t, s));
+        if (P->R > 0) GRAPE_CUDA_TRY(k_trace(P, t, s));
     }
     return GRAPE_OK;
 }

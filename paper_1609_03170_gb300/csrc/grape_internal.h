@@ -46,10 +46,12 @@ struct PropArgs {
     int reverse;
     double g[4], a[4], b[4];
     int store_map[4];                   // stage s -> slot of the stage store
-    const double2 *x_in;                // [n_states][d*d]
-    double2 *x_out;                     // [n_states][d*d] (may alias x_in)
-    double2 *stage_store;               // [(n - sub_begin)][4][n_states][d*d] or null
-    double2 *bound_store;               // [slot][n_states][d*d] or null
+    // state buffers are in the kernel's storage format (16 bytes per complex
+    // entry: double2 for FP64, float4 hi/lo pairs for double-float)
+    const void *x_in;                   // [n_states][d*d]
+    void *x_out;                        // [n_states][d*d] (may alias x_in)
+    void *stage_store;                  // [(n - sub_begin)][4][n_states][d*d] or null
+    void *bound_store;                  // [slot][n_states][d*d] or null
     long long bound_step;               // substeps between bound stores
 };
 
@@ -64,19 +66,26 @@ struct TraceArgs {
     int cb_do[GRAPE_MAXCB];     // distinct-offset index of band entry c
     int do_off[GRAPE_MAXDO];    // distinct offsets
     const double2 *cb_val;      // [ncb][d]  Hk_b[m]
-    const double2 *K;           // adjoint-side matrices
-    const double2 *Y;           // forward-side matrices
+    const void *K;              // adjoint-side matrices (storage format)
+    const void *Y;              // forward-side matrices (storage format)
     long long npairs;           // matrices per output row
     int n_rows;
     double weight;
     double *G;                  // [n_rows][R]
 };
 
-cudaError_t grape_launch_prop(const PropArgs &p, int threads, int ept, size_t smem,
-                              cudaStream_t stream);
-cudaError_t grape_prepare_prop(int ept, size_t smem, int ncl);
-cudaError_t grape_max_active_clusters(int threads, int ept, size_t smem, int ncl,
-                                      int n_blocks, int *clusters);
-cudaError_t grape_launch_trace(const TraceArgs &p, cudaStream_t stream);
-cudaError_t grape_launch_cost(const double2 *rho, const double2 *sigma, int n_states,
-                              int d2, double *F, cudaStream_t stream);
+// Launchers, one set per number type: _f64 native FP64, _df double-float.
+#define GRAPE_DECLARE_LAUNCHERS(SUFFIX)                                                        \
+    cudaError_t grape_launch_prop_##SUFFIX(const PropArgs &p, int threads, int ept, size_t smem, \
+                                           cudaStream_t stream);                                \
+    cudaError_t grape_prepare_prop_##SUFFIX(int ept, size_t smem, int ncl);                    \
+    cudaError_t grape_max_active_clusters_##SUFFIX(int threads, int ept, size_t smem, int ncl,  \
+                                                   int n_blocks, int *clusters);               \
+    cudaError_t grape_launch_trace_##SUFFIX(const TraceArgs &p, cudaStream_t stream);          \
+    cudaError_t grape_launch_cost_##SUFFIX(const void *rho, const void *sigma, int n_states,    \
+                                           int d2, double *F, cudaStream_t stream);             \
+    cudaError_t grape_launch_to_double_##SUFFIX(const void *src, double2 *dst, size_t n,        \
+                                                cudaStream_t stream);
+
+GRAPE_DECLARE_LAUNCHERS(f64)
+GRAPE_DECLARE_LAUNCHERS(df)

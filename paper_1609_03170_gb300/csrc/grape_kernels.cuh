@@ -1,0 +1,469 @@
+// grape_kernels.cuh - sm_103a kernels of the open-GRAPE hot path, written
+// once over the number type (grape_num.cuh) and instantiated for native FP64
+// (grape_kernels_f64.cu) and double-float on the FP32 pipes
+// (grape_kernels_df.cu).
+//
+//  prop_kernel   RK4 propagation of one density matrix (forward, Sec. 3
+//                Eq. rkmaster) or of its adjoint (backward, Eq. lambda) per
+//                thread-block cluster.  The d x d matrix is split into
+//                contiguous chunks of its row-major flat index, one per CTA
+//                of the cluster.  Each CTA keeps the current stage input of
+//                its chunk plus a halo of omax*(d+1) entries on both sides in
+//                shared memory; new stage values are pushed into the
+//                neighbours' halos with distributed-shared-memory stores and
+//                one cluster barrier separates consecutive RK stages.  The
+//                slice's Hamiltonian bands A(u_j) are rebuilt in shared
+//                memory once per slice.  Stage inputs (forward y_s, adjoint
+//                kb_s) and slice-boundary states are streamed to HBM for the
+//                gradient.
+//  trace_kernel  per-slice gradient reduction of Eq. (dphidu): one CTA per
+//                slice, row dot-products of K and conj(Y) on the control
+//                bands, lane-private accumulation, warp-shuffle plus a
+//                fixed-order shared-memory tree (deterministic).
+//  cost_kernel   Phi = sum_s Re Tr(sigma_s rho_s(T)) (Eq. phi), fixed order.
+//  to_double_kernel  storage format -> complex128 (rho(T) output).
+#pragma once
+
+#include "grape_internal.h"
+#include "grape_num.cuh"
+
+namespace grape_k {
+
+using namespace grape_num;
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_remote(uint32_t addr, double2 v) {
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(v.x), "d"(v.y)
+                 : "memory");
+}
+__device__ __forceinline__ void st_remote(uint32_t addr, float4 v) {
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x),
+                 "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// A(u_j) = A0 + sum_k u_k(j) Ak (FP64), stored in the number type.
+template <class Num>
+__device__ __forceinline__ void build_bands(typename Num::store_t *dst, const PropArgs &p,
+                                            int slice) {
+    const int nbd = p.tab.nb * p.d;
+    const double *uj = p.u + (size_t)slice * p.R;
+    for (int idx = threadIdx.x; idx < nbd; idx += blockDim.x) {
+        double2 v = __ldg(&p.tab.A0[idx]);
+        for (int k = 0; k < p.R; ++k) {
+            const double uk = __ldg(&uj[k]);
+            const double2 h = __ldg(&p.tab.Ak[(size_t)k * nbd + idx]);
+            v.x = fma(uk, h.x, v.x);
+            v.y = fma(uk, h.y, v.y);
+        }
+        dst[idx] = Num::store(Num::from_double2(v));
+    }
+}
+
+// Write stage value z of flat element e into the own window and into every
+// neighbour window of the cluster that covers e.
+template <class S>
+__device__ __forceinline__ void push_value(S *buf, const PropArgs &p, int rank, int e, S z) {
+    const int wbase = rank * p.chunk - p.halo;
+    buf[e - wbase] = z;
+    const int c_lo = max(0, rank - p.reach), c_hi = min(p.ncl - 1, rank + p.reach);
+    for (int c = c_lo; c <= c_hi; ++c) {
+        if (c == rank) continue;
+        const int cb = c * p.chunk - p.halo;
+        if (e >= cb && e < cb + p.win)
+            st_remote(map_to_rank(smem_u32(&buf[e - cb]), (uint32_t)c), z);
+    }
+}
+
+// W = Op(z) at element (i, j) of the window `cur` (local flat index le):
+//   W = -i (A z - z A^+)[i][j] + sum_t vL_t[i] conj(vR_t[j]) z[i+oL_t][j+oR_t]
+template <class Num>
+__device__ __forceinline__ typename Num::val lindblad_at(const typename Num::store_t *cur, int le,
+                                                         int i, int j, int d, const PropTables &t,
+                                                         const typename Num::store_t *A,
+                                                         const typename Num::store_t *vL,
+                                                         const typename Num::store_t *vR) {
+    typename Num::acc w = Num::acc_zero();
+#pragma unroll
+    for (int b = 0; b < GRAPE_MAXB; ++b) {
+        if (b < t.nb) {
+            Num::mac(w, Num::load(A[b * d + i]), Num::load(cur[le + t.off_row[b]]));
+            Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[le + t.off[b]]));
+        }
+    }
+    w = Num::acc_minus_i(w);                     // -i (A z - z A^+)
+#pragma unroll
+    for (int q = 0; q < GRAPE_MAXT; ++q) {
+        if (q < t.nt) {
+            const typename Num::val coef = Num::mul_conjb(Num::load(vL[q * d + i]),
+                                                          Num::load(vR[q * d + j]));
+            Num::mac(w, coef, Num::load(cur[le + t.jflat[q]]));
+        }
+    }
+    return Num::done(w);
+}
+
+template <class Num, int EPT>
+__global__ void __launch_bounds__(256) prop_kernel(const PropArgs p) {
+    using S = typename Num::store_t;
+    using V = typename Num::val;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S *buf0 = reinterpret_cast<S *>(smem_raw);
+    S *buf1 = buf0 + p.win;
+    const int d = p.d, d2 = d * d;
+    const int nbd = p.tab.nb * d;
+    S *bands = buf1 + p.win;                 // [2][nb][d]
+    S *vL = bands + 2 * nbd;                 // [nt][d]
+    S *vR = vL + p.tab.nt * d;               // [nt][d]
+    const S *x_in = static_cast<const S *>(p.x_in);
+    S *x_out = static_cast<S *>(p.x_out);
+    S *stage_store = static_cast<S *>(p.stage_store);
+    S *bound_store = static_cast<S *>(p.bound_store);
+
+    const int rank = blockIdx.x % p.ncl;
+    const int state = blockIdx.x / p.ncl;
+    const int e0 = rank * p.chunk;
+    const int e1 = min(e0 + p.chunk, d2);
+    const int wbase = e0 - p.halo;
+    const size_t soff = (size_t)state * d2;
+
+    const V vzero = Num::zero();
+    for (int i = threadIdx.x; i < 2 * p.win; i += blockDim.x) buf0[i] = Num::store(vzero);
+    for (int i = threadIdx.x; i < p.tab.nt * d; i += blockDim.x) {
+        vL[i] = Num::store(Num::from_double2(__ldg(&p.tab.vL[i])));
+        vR[i] = Num::store(Num::from_double2(__ldg(&p.tab.vR[i])));
+    }
+    typename Num::real_t g[4], a[4], b[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        g[s] = Num::real_const(p.g[s]);
+        a[s] = Num::real_const(p.a[s]);
+        b[s] = Num::real_const(p.b[s]);
+    }
+    const long long nsub = p.sub_end - p.sub_begin;
+    long long n_first = p.reverse ? p.sub_end - 1 : p.sub_begin;
+    if (nsub <= 0) n_first = p.sub_begin;
+    int jcur = (int)(n_first / p.n_rk);
+    build_bands<Num>(bands, p, jcur);
+    cluster_sync_all();   // every CTA of the cluster runs and has zeroed its windows
+
+    V x[EPT], acc[EPT];
+    int el[EPT], ri[EPT], ci[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int e = e0 + threadIdx.x + k * blockDim.x;
+        el[k] = (e < e1) ? e : -1;
+        ri[k] = (e < e1) ? e / d : 0;
+        ci[k] = (e < e1) ? e - (e / d) * d : 0;
+        x[k] = (e < e1) ? Num::load(x_in[soff + e]) : vzero;
+        if (e < e1) push_value(buf0, p, rank, e, Num::store(Num::scale(g[0], x[k])));
+    }
+    cluster_sync_all();
+
+    int tb = 0;
+    for (long long it = 0; it < nsub; ++it) {
+        const long long n = p.reverse ? p.sub_end - 1 - it : p.sub_begin + it;
+        const long long tidx = p.reverse ? n + 1 : n;
+        if (bound_store && ((tidx - p.sub_begin) % p.bound_step) == 0) {
+            S *dst = bound_store + ((size_t)((tidx - p.sub_begin) / p.bound_step) * p.n_states) * d2 + soff;
+#pragma unroll
+            for (int k = 0; k < EPT; ++k)
+                if (el[k] >= 0) dst[el[k]] = Num::store(x[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) acc[k] = x[k];
+        const S *A = bands + tb * nbd;
+        bool flip = false;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const S *cur = (s & 1) ? buf1 : buf0;
+            S *nxt = (s & 1) ? buf0 : buf1;
+            S *st = nullptr;
+            if (stage_store)
+                st = stage_store + ((size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states) * d2 + soff;
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+                if (el[k] < 0) continue;
+                const int le = el[k] - wbase;
+                const V w = lindblad_at<Num>(cur, le, ri[k], ci[k], d, p.tab, A, vL, vR);
+                if (st) st[el[k]] = cur[le];
+                acc[k] = Num::axpy(a[s], w, acc[k]);
+                V z;
+                if (s < 3) {
+                    z = Num::lin2(g[s + 1], x[k], b[s + 1], w);
+                } else {
+                    x[k] = acc[k];
+                    z = Num::scale(g[0], x[k]);
+                }
+                push_value(nxt, p, rank, el[k], Num::store(z));
+            }
+            if (s == 3 && it + 1 < nsub) {
+                const long long nn = p.reverse ? n - 1 : n + 1;
+                const int jn = (int)(nn / p.n_rk);
+                if (jn != jcur) {
+                    build_bands<Num>(bands + (tb ^ 1) * nbd, p, jn);
+                    jcur = jn;
+                    flip = true;
+                }
+            }
+            cluster_sync_all();
+        }
+        if (flip) tb ^= 1;
+    }
+    const long long tend = p.reverse ? p.sub_begin : p.sub_end;
+    if (bound_store && ((tend - p.sub_begin) % p.bound_step) == 0) {
+        S *dst = bound_store + ((size_t)((tend - p.sub_begin) / p.bound_step) * p.n_states) * d2 + soff;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k)
+            if (el[k] >= 0) dst[el[k]] = Num::store(x[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < EPT; ++k)
+        if (el[k] >= 0) x_out[soff + el[k]] = Num::store(x[k]);
+}
+
+template <class Num>
+__global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
+    using S = typename Num::store_t;
+    const int row = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int d = p.d;
+    const size_t d2 = (size_t)d * d;
+    double2 Z[GRAPE_MAXCB];
+#pragma unroll
+    for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = make_double2(0.0, 0.0);
+    const S *Kb = static_cast<const S *>(p.K);
+    const S *Yb = static_cast<const S *>(p.Y);
+
+    for (long long q = 0; q < p.npairs; ++q) {
+        const size_t moff = ((size_t)row * p.npairs + q) * d2;
+        const S *K = Kb + moff;
+        const S *Y = Yb + moff;
+        for (int m = warp; m < d; m += nwarps) {
+            typename Num::acc P[GRAPE_MAXDO];
+#pragma unroll
+            for (int o = 0; o < GRAPE_MAXDO; ++o) P[o] = Num::acc_zero();
+            for (int l = lane; l < d; l += 32) {
+                const typename Num::val y = Num::load(Y[(size_t)m * d + l]);
+#pragma unroll
+                for (int o = 0; o < GRAPE_MAXDO; ++o) {
+                    if (o < p.ndo) {
+                        const int r = m + p.do_off[o];
+                        if (r >= 0 && r < d) Num::mac_conjb(P[o], Num::load(K[(size_t)r * d + l]), y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < GRAPE_MAXDO; ++o) {
+                if (o < p.ndo) {
+                    const double2 pv = Num::to_double2(Num::done(P[o]));
+#pragma unroll
+                    for (int c = 0; c < GRAPE_MAXCB; ++c) {
+                        if (c < p.ncb && p.cb_do[c] == o) {
+                            const double2 hv = __ldg(&p.cb_val[(size_t)c * d + m]);
+                            Z[c].x = fma(hv.x, pv.x, fma(-hv.y, pv.y, Z[c].x));
+                            Z[c].y = fma(hv.x, pv.y, fma(hv.y, pv.x, Z[c].y));
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // deterministic reduction: warp shuffles, then warps in index order
+    __shared__ double red[GRAPE_MAXCB][32];
+#pragma unroll
+    for (int c = 0; c < GRAPE_MAXCB; ++c) {
+        double v = Z[c].y;
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
+        if (lane == 0) red[c][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < GRAPE_MAXR) {
+        const int k = threadIdx.x;
+        if (k < p.R) {
+            double s = 0.0;
+            for (int c = 0; c < p.ncb; ++c) {
+                if (p.cb_k[c] != k) continue;
+                double t = 0.0;
+                for (int w = 0; w < nwarps; ++w) t += red[c][w];
+                s += t;
+            }
+            p.G[(size_t)row * p.R + k] = p.weight * (-2.0 * s);
+        }
+    }
+}
+
+template <class Num>
+__global__ void __launch_bounds__(256) cost_kernel(const void *rho_v, const void *sigma_v,
+                                                   int n_states, int d2, double *F) {
+    using S = typename Num::store_t;
+    const S *rho = static_cast<const S *>(rho_v);
+    const S *sigma = static_cast<const S *>(sigma_v);
+    double acc = 0.0;
+    for (int s = 0; s < n_states; ++s)
+        for (int e = threadIdx.x; e < d2; e += blockDim.x) {
+            const double2 r = Num::to_double2(Num::load(rho[(size_t)s * d2 + e]));
+            const double2 g = Num::to_double2(Num::load(sigma[(size_t)s * d2 + e]));
+            acc = fma(g.x, r.x, fma(g.y, r.y, acc));    // Re(conj(sigma_ij) rho_ij)
+        }
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, sh);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        *F = s;
+    }
+}
+
+template <class Num>
+__global__ void __launch_bounds__(256) to_double_kernel(const void *src_v, double2 *dst, size_t n) {
+    using S = typename Num::store_t;
+    const S *src = static_cast<const S *>(src_v);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = Num::to_double2(Num::load(src[i]));
+}
+
+// ------------------------------------------------------------------ launchers
+template <class Num, int EPT>
+cudaError_t launch_prop_t(const PropArgs &p, int threads, size_t smem, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(p.n_states * p.ncl));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)p.ncl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, prop_kernel<Num, EPT>, p);
+}
+
+template <class Num, int EPT>
+cudaError_t prepare_t(size_t smem, int ncl) {
+    cudaError_t e = cudaFuncSetAttribute(prop_kernel<Num, EPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (ncl > 8)
+        e = cudaFuncSetAttribute(prop_kernel<Num, EPT>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+template <class Num, int EPT>
+cudaError_t clusters_t(int threads, size_t smem, int ncl, int n_blocks, int *clusters) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_blocks);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ncl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(clusters, prop_kernel<Num, EPT>, &cfg);
+}
+
+template <class Num>
+cudaError_t launch_prop(const PropArgs &p, int threads, int ept, size_t smem, cudaStream_t s) {
+    switch (ept) {
+    case 1: return launch_prop_t<Num, 1>(p, threads, smem, s);
+    case 2: return launch_prop_t<Num, 2>(p, threads, smem, s);
+    case 4: return launch_prop_t<Num, 4>(p, threads, smem, s);
+    case 8: return launch_prop_t<Num, 8>(p, threads, smem, s);
+    case 16: return launch_prop_t<Num, 16>(p, threads, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class Num>
+cudaError_t prepare(int ept, size_t smem, int ncl) {
+    switch (ept) {
+    case 1: return prepare_t<Num, 1>(smem, ncl);
+    case 2: return prepare_t<Num, 2>(smem, ncl);
+    case 4: return prepare_t<Num, 4>(smem, ncl);
+    case 8: return prepare_t<Num, 8>(smem, ncl);
+    case 16: return prepare_t<Num, 16>(smem, ncl);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class Num>
+cudaError_t max_clusters(int threads, int ept, size_t smem, int ncl, int n_blocks, int *clusters) {
+    switch (ept) {
+    case 1: return clusters_t<Num, 1>(threads, smem, ncl, n_blocks, clusters);
+    case 2: return clusters_t<Num, 2>(threads, smem, ncl, n_blocks, clusters);
+    case 4: return clusters_t<Num, 4>(threads, smem, ncl, n_blocks, clusters);
+    case 8: return clusters_t<Num, 8>(threads, smem, ncl, n_blocks, clusters);
+    case 16: return clusters_t<Num, 16>(threads, smem, ncl, n_blocks, clusters);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class Num>
+cudaError_t launch_trace(const TraceArgs &p, cudaStream_t s) {
+    if (p.n_rows <= 0) return cudaSuccess;
+    trace_kernel<Num><<<p.n_rows, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <class Num>
+cudaError_t launch_cost(const void *rho, const void *sigma, int n_states, int d2, double *F,
+                        cudaStream_t s) {
+    cost_kernel<Num><<<1, 256, 0, s>>>(rho, sigma, n_states, d2, F);
+    return cudaGetLastError();
+}
+
+template <class Num>
+cudaError_t launch_to_double(const void *src, double2 *dst, size_t n, cudaStream_t s) {
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 1024);
+    if (blocks <= 0) return cudaSuccess;
+    to_double_kernel<Num><<<blocks, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace grape_k
+
+#define GRAPE_DEFINE_LAUNCHERS(SUFFIX, NUM)                                                     \
+    cudaError_t grape_launch_prop_##SUFFIX(const PropArgs &p, int threads, int ept, size_t smem, \
+                                           cudaStream_t s) {                                    \
+        return grape_k::launch_prop<NUM>(p, threads, ept, smem, s);                             \
+    }                                                                                           \
+    cudaError_t grape_prepare_prop_##SUFFIX(int ept, size_t smem, int ncl) {                    \
+        return grape_k::prepare<NUM>(ept, smem, ncl);                                           \
+    }                                                                                           \
+    cudaError_t grape_max_active_clusters_##SUFFIX(int threads, int ept, size_t smem, int ncl,  \
+                                                   int n_blocks, int *clusters) {               \
+        return grape_k::max_clusters<NUM>(threads, ept, smem, ncl, n_blocks, clusters);         \
+    }                                                                                           \
+    cudaError_t grape_launch_trace_##SUFFIX(const TraceArgs &p, cudaStream_t s) {               \
+        return grape_k::launch_trace<NUM>(p, s);                                                \
+    }                                                                                           \
+    cudaError_t grape_launch_cost_##SUFFIX(const void *rho, const void *sigma, int n_states,    \
+                                           int d2, double *F, cudaStream_t s) {                 \
+        return grape_k::launch_cost<NUM>(rho, sigma, n_states, d2, F, s);                       \
+    }                                                                                           \
+    cudaError_t grape_launch_to_double_##SUFFIX(const void *src, double2 *dst, size_t n,        \
+                                                cudaStream_t s) {                               \
+        return grape_k::launch_to_double<NUM>(src, dst, n, s);                                  \
+    }

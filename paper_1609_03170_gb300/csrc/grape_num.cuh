@@ -1,0 +1,186 @@
+// grape_num.cuh - the two complex number types the kernels are written over.
+//
+//  NumD   native FP64 complex (double2 storage).
+//  NumF   double-float complex: every real part is an unevaluated sum hi + lo
+//         of two FP32 numbers with |lo| <= ulp(hi)/2, about 48 significant
+//         bits (float4 storage: re.hi, re.lo, im.hi, im.lo).  Arithmetic
+//         uses the error-free transformations TwoSum (Knuth), Fast2Sum
+//         (Dekker) and TwoProduct through the fused multiply-add, all with
+//         explicitly rounded intrinsics so the compiler can neither contract
+//         nor reassociate them.  GB300 issues FP32 at ~67x its FP64 rate,
+//         which is what makes the pair arithmetic the fast path.
+//
+// Both types are 16 bytes per complex entry, so every buffer of the path has
+// the same size in either precision.  Accumulators (Acc) collect products of
+// complex numbers; for NumF the high parts are summed with TwoSum and all
+// rounding errors and cross terms gather in the low parts, normalised once
+// at the end (lazy renormalisation).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace grape_num {
+
+// ---------------------------------------------------------------- FP32 EFTs
+struct ff {
+    float h, l;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {       // accurate sum
+    ff s = two_sum(a.h, b.h);
+    const ff t = two_sum(a.l, b.l);
+    s.l = __fadd_rn(s.l, t.h);
+    s = fast_two_sum(s.h, s.l);
+    s.l = __fadd_rn(s.l, t.l);
+    return fast_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+__host__ __device__ __forceinline__ ff ff_from_double(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__host__ __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.h + (double)a.l; }
+
+// lazy accumulator of one real part: acc += a*b (sign s = +1/-1)
+struct lacc {
+    float h, l;
+};
+__device__ __forceinline__ void lacc_fma(lacc &acc, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    const ff s = two_sum(acc.h, p);
+    acc.h = s.h;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
+}
+__device__ __forceinline__ void lacc_fms(lacc &acc, float ah, float al, float bh, float bl) {
+    lacc_fma(acc, -ah, -al, bh, bl);
+}
+__device__ __forceinline__ ff lacc_done(lacc a) { return two_sum(a.h, a.l); }
+
+// ------------------------------------------------------------ number types
+struct NumD {
+    using store_t = double2;
+    using real_t = double;
+    struct val { double re, im; };
+    struct acc { double re, im; };
+
+    static __device__ __forceinline__ val load(const store_t &s) { return {s.x, s.y}; }
+    static __device__ __forceinline__ store_t store(val v) { return make_double2(v.re, v.im); }
+    static __device__ __forceinline__ val zero() { return {0.0, 0.0}; }
+    static __device__ __forceinline__ acc acc_zero() { return {0.0, 0.0}; }
+    static __device__ __forceinline__ real_t real_const(double x) { return x; }
+    // acc += a * b
+    static __device__ __forceinline__ void mac(acc &c, val a, val b) {
+        c.re = fma(a.re, b.re, fma(-a.im, b.im, c.re));
+        c.im = fma(a.re, b.im, fma(a.im, b.re, c.im));
+    }
+    // acc -= conj(a) * b
+    static __device__ __forceinline__ void mac_conj_neg(acc &c, val a, val b) {
+        c.re = fma(-a.re, b.re, fma(-a.im, b.im, c.re));
+        c.im = fma(-a.re, b.im, fma(a.im, b.re, c.im));
+    }
+    // acc += a * conj(b)
+    static __device__ __forceinline__ void mac_conjb(acc &c, val a, val b) {
+        c.re = fma(a.re, b.re, fma(a.im, b.im, c.re));
+        c.im = fma(a.im, b.re, fma(-a.re, b.im, c.im));
+    }
+    static __device__ __forceinline__ val done(acc c) { return {c.re, c.im}; }
+    static __device__ __forceinline__ acc acc_minus_i(acc c) { return {c.im, -c.re}; }
+    // a * conj(b)
+    static __device__ __forceinline__ val mul_conjb(val a, val b) {
+        return {fma(a.re, b.re, a.im * b.im), fma(a.im, b.re, -a.re * b.im)};
+    }
+    static __device__ __forceinline__ val minus_i(val a) { return {a.im, -a.re}; }
+    // x + s*w
+    static __device__ __forceinline__ val axpy(real_t s, val w, val x) {
+        return {fma(s, w.re, x.re), fma(s, w.im, x.im)};
+    }
+    // g*x + b*w
+    static __device__ __forceinline__ val lin2(real_t g, val x, real_t b, val w) {
+        return {fma(g, x.re, b * w.re), fma(g, x.im, b * w.im)};
+    }
+    static __device__ __forceinline__ val scale(real_t s, val a) { return {s * a.re, s * a.im}; }
+    static __device__ __forceinline__ double2 to_double2(val v) { return make_double2(v.re, v.im); }
+    static __device__ __forceinline__ val from_double2(double2 v) { return {v.x, v.y}; }
+};
+
+struct NumF {
+    using store_t = float4;   // re.h, re.l, im.h, im.l
+    using real_t = ff;
+    struct val { ff re, im; };
+    struct acc { lacc re, im; };
+
+    static __device__ __forceinline__ val load(const store_t &s) { return {{s.x, s.y}, {s.z, s.w}}; }
+    static __device__ __forceinline__ store_t store(val v) {
+        return make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+    }
+    static __device__ __forceinline__ val zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+    static __device__ __forceinline__ acc acc_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+    static __device__ __forceinline__ real_t real_const(double x) { return ff_from_double(x); }
+    static __device__ __forceinline__ void mac(acc &c, val a, val b) {
+        lacc_fma(c.re, a.re.h, a.re.l, b.re.h, b.re.l);
+        lacc_fms(c.re, a.im.h, a.im.l, b.im.h, b.im.l);
+        lacc_fma(c.im, a.re.h, a.re.l, b.im.h, b.im.l);
+        lacc_fma(c.im, a.im.h, a.im.l, b.re.h, b.re.l);
+    }
+    static __device__ __forceinline__ void mac_conj_neg(acc &c, val a, val b) {
+        // -(a.re - i a.im)(b.re + i b.im) = -(a.re b.re + a.im b.im) - i(a.re b.im - a.im b.re)
+        lacc_fms(c.re, a.re.h, a.re.l, b.re.h, b.re.l);
+        lacc_fms(c.re, a.im.h, a.im.l, b.im.h, b.im.l);
+        lacc_fms(c.im, a.re.h, a.re.l, b.im.h, b.im.l);
+        lacc_fma(c.im, a.im.h, a.im.l, b.re.h, b.re.l);
+    }
+    static __device__ __forceinline__ void mac_conjb(acc &c, val a, val b) {
+        // a conj(b) = (a.re b.re + a.im b.im) + i(a.im b.re - a.re b.im)
+        lacc_fma(c.re, a.re.h, a.re.l, b.re.h, b.re.l);
+        lacc_fma(c.re, a.im.h, a.im.l, b.im.h, b.im.l);
+        lacc_fma(c.im, a.im.h, a.im.l, b.re.h, b.re.l);
+        lacc_fms(c.im, a.re.h, a.re.l, b.im.h, b.im.l);
+    }
+    static __device__ __forceinline__ val done(acc c) { return {lacc_done(c.re), lacc_done(c.im)}; }
+    static __device__ __forceinline__ acc acc_minus_i(acc c) { return {c.im, {-c.re.h, -c.re.l}}; }
+    static __device__ __forceinline__ val mul_conjb(val a, val b) {
+        acc c = acc_zero();
+        mac_conjb(c, a, b);
+        return done(c);
+    }
+    static __device__ __forceinline__ val minus_i(val a) {
+        return {a.im, {-a.re.h, -a.re.l}};
+    }
+    static __device__ __forceinline__ val axpy(real_t s, val w, val x) {
+        return {ff_add(x.re, ff_mul(s, w.re)), ff_add(x.im, ff_mul(s, w.im))};
+    }
+    static __device__ __forceinline__ val lin2(real_t g, val x, real_t b, val w) {
+        return {ff_add(ff_mul(g, x.re), ff_mul(b, w.re)), ff_add(ff_mul(g, x.im), ff_mul(b, w.im))};
+    }
+    static __device__ __forceinline__ val scale(real_t s, val a) {
+        return {ff_mul(s, a.re), ff_mul(s, a.im)};
+    }
+    static __device__ __forceinline__ double2 to_double2(val v) {
+        return make_double2(ff_to_double(v.re), ff_to_double(v.im));
+    }
+    static __device__ __forceinline__ val from_double2(double2 v) {
+        return {ff_from_double(v.x), ff_from_double(v.y)};
+    }
+};
+
+}  // namespace grape_num

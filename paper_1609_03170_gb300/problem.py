@@ -99,7 +99,7 @@ class GrapeProblem:
 
     def __init__(self, model: BandModel, rho0: np.ndarray, sigma: np.ndarray, T: float,
                  n_slices: int, n_rk: int, grad_mode: int = _lib.GRAPE_GRAD_EXACT,
-                 ckpt_stride: int = 0):
+                 ckpt_stride: int = 0, precision: int = _lib.GRAPE_PREC_DF64):
         _lib.load()
         d = model.d
         rho0 = np.ascontiguousarray(rho0, dtype=np.complex128)
@@ -127,14 +127,16 @@ class GrapeProblem:
         desc = _lib.grape_problem_desc(
             d, self.R, J, self.n_states, self.n_slices, self.n_rk, self.T,
             band(model.H0), Hc, jumps, _dptr(rates), _dptr(rho_f), _dptr(sig_f),
-            1 if sigma.ndim == 2 else 0, int(grad_mode), int(ckpt_stride))
+            1 if sigma.ndim == 2 else 0, int(grad_mode), int(ckpt_stride), int(precision))
+        self.precision = int(precision)
         self._h = _lib.grape_problem_create(desc)
         del keep
 
     @classmethod
-    def from_workload(cls, w, grad_mode: int = _lib.GRAPE_GRAD_EXACT, ckpt_stride: int = 0):
+    def from_workload(cls, w, grad_mode: int = _lib.GRAPE_GRAD_EXACT, ckpt_stride: int = 0,
+                      precision: int = _lib.GRAPE_PREC_DF64):
         return cls(band_model(w.phys), w.rho0, w.sigma, w.T, w.n_slices, w.n_rk,
-                   grad_mode=grad_mode, ckpt_stride=ckpt_stride)
+                   grad_mode=grad_mode, ckpt_stride=ckpt_stride, precision=precision)
 
     # -- lifetime ---------------------------------------------------------
     def close(self):

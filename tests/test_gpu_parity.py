@@ -2,7 +2,9 @@
 
 Tolerance: 1e-10 relative (max-abs error over max-abs reference) on rho(T),
 Phi and dPhi/du, as stated for the method; finite differences of the GPU's
-own Phi agree with its gradient to 1e-6 relative.
+own Phi agree with its gradient to 1e-6 relative.  Every parity case runs in
+both kernel precisions: double-float on the FP32 pipes (the default) and
+native FP64.
 """
 import os
 
@@ -15,6 +17,7 @@ from oracle import dense, operators, sparse
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
+PRECS = [0, 1]          # GRAPE_PREC_DF64, GRAPE_PREC_FP64
 
 
 def rel(a, b):
@@ -54,39 +57,42 @@ def with_cluster(n):
 
 
 # --------------------------------------------------------------------------
-def test_forward_small_matches_dense_oracle(gp):
+@pytest.mark.parametrize("prec", PRECS)
+def test_forward_small_matches_dense_oracle(gp, prec):
     w = rich()
     m = operators.build(w.phys)
     F_ref, r_ref = dense.forward(m, w.u, w.rho0, w.sigma, w.T, w.n_rk)
-    P = gp.GrapeProblem.from_workload(w)
+    P = gp.GrapeProblem.from_workload(w, precision=prec)
     F, r = P.forward(w.u)
     assert rel(r, r_ref) < TOL
     assert abs(F - F_ref) < TOL * abs(F_ref)
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("mode", [0, 1])
-def test_gradient_small_matches_dense_oracle(gp, mode):
+def test_gradient_small_matches_dense_oracle(gp, mode, prec):
     w = rich()
     m = operators.build(w.phys)
     if mode == 0:
         F_ref, G_ref = dense.gradient_exact(m, w.u, w.rho0, w.sigma, w.T, w.n_rk)
     else:
         F_ref, G_ref = dense.gradient_first_order(m, w.u, w.rho0, w.sigma, w.T, w.n_rk)
-    P = gp.GrapeProblem.from_workload(w, grad_mode=mode)
+    P = gp.GrapeProblem.from_workload(w, grad_mode=mode, precision=prec)
     F, G = P.gradient(w.u)
     assert abs(F - F_ref) < TOL * abs(F_ref)
     assert rel(G, G_ref) < TOL
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("cluster", [1, 2, 4, 16])
-def test_d20_full_size_all_cluster_widths(gp, cluster):
+def test_d20_full_size_all_cluster_widths(gp, cluster, prec):
     """The 2-level qubit x N=10 resonator problem (d=20, N_t=200, n_RK=4) at
     full size; cluster 16 splits 400 entries into chunks of 25 with a 42-entry
     halo, so halos span two neighbours."""
     w = workloads.qubit_resonator_d20()
     F_ref, G_ref, r_ref, _ = sparse.run_workload(w, threads=2)
     with with_cluster(cluster):
-        P = gp.GrapeProblem.from_workload(w)
+        P = gp.GrapeProblem.from_workload(w, precision=prec)
     assert P.geometry()[0] == cluster
     F, r = P.forward(w.u)
     assert rel(r, r_ref) < TOL
@@ -95,26 +101,28 @@ def test_d20_full_size_all_cluster_widths(gp, cluster):
     assert rel(G, G_ref) < TOL
 
 
-def test_cluster_width_does_not_change_bits(gp):
+@pytest.mark.parametrize("prec", PRECS)
+def test_cluster_width_does_not_change_bits(gp, prec):
     """Every entry is computed by the same arithmetic whatever CTA owns it."""
     w = workloads.transmon_resonator_d120(n_slices=6)
     out = []
     for c in (4, 8, 16):
         with with_cluster(c):
-            P = gp.GrapeProblem.from_workload(w)
+            P = gp.GrapeProblem.from_workload(w, precision=prec)
         out.append(P.gradient(w.u))
     for F, G in out[1:]:
         assert F == out[0][0]
         assert np.array_equal(G, out[0][1])
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("mode", [0, 1])
-def test_d120_reduced_slices_matches_c_oracle(gp, mode):
+def test_d120_reduced_slices_matches_c_oracle(gp, mode, prec):
     """The d=120 transmon-resonator problem (three controls, three jump
     operators, Kerr) with N_t = 40 slices."""
     w = workloads.transmon_resonator_d120(n_slices=40)
     F_ref, G_ref, r_ref, _ = sparse.run_workload(w, mode=1 + mode, threads=3)
-    P = gp.GrapeProblem.from_workload(w, grad_mode=mode)
+    P = gp.GrapeProblem.from_workload(w, grad_mode=mode, precision=prec)
     F, r = P.forward(w.u)
     assert rel(r, r_ref) < TOL
     F2, G = P.gradient(w.u)
@@ -122,13 +130,14 @@ def test_d120_reduced_slices_matches_c_oracle(gp, mode):
     assert rel(G, G_ref) < TOL
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("stride", [1, 7, 40])
-def test_checkpointed_gradient_equals_stored(gp, stride):
+def test_checkpointed_gradient_equals_stored(gp, stride, prec):
     """Segments with checkpoints and recomputation give the same bits as
     keeping every stage input."""
     w = workloads.qubit_resonator_d20(n_slices=40)
-    ref = gp.GrapeProblem.from_workload(w).gradient(w.u)
-    P = gp.GrapeProblem.from_workload(w, ckpt_stride=stride)
+    ref = gp.GrapeProblem.from_workload(w, precision=prec).gradient(w.u)
+    P = gp.GrapeProblem.from_workload(w, ckpt_stride=stride, precision=prec)
     F, G = P.gradient(w.u)
     assert F == ref[0]
     assert np.array_equal(G, ref[1])
@@ -136,9 +145,10 @@ def test_checkpointed_gradient_equals_stored(gp, stride):
         assert P.gradient_launches() == 2 + 3 * ((40 + stride - 1) // stride)
 
 
-def test_gpu_gradient_matches_finite_differences_of_gpu_forward(gp):
+@pytest.mark.parametrize("prec", PRECS)
+def test_gpu_gradient_matches_finite_differences_of_gpu_forward(gp, prec):
     w = workloads.transmon_resonator_d120(n_slices=8)
-    P = gp.GrapeProblem.from_workload(w)
+    P = gp.GrapeProblem.from_workload(w, precision=prec)
     _, G = P.gradient(w.u)
     for (j, k) in [(0, 0), (3, 2), (7, 1), (5, 0)]:
         up = w.u.copy(); up[j, k] += 1e-5
@@ -164,25 +174,28 @@ def test_device_pointers_equal_host_pointers(gp):
     assert np.array_equal(rd.cpu().numpy(), rh)
 
 
-def test_edge_single_slice_single_substep(gp):
+@pytest.mark.parametrize("prec", PRECS)
+def test_edge_single_slice_single_substep(gp, prec):
     w = rich(n_slices=1, n_rk=1, T=0.05)
     m = operators.build(w.phys)
     F_ref, G_ref = dense.gradient_exact(m, w.u, w.rho0, w.sigma, w.T, w.n_rk)
-    F, G = gp.GrapeProblem.from_workload(w).gradient(w.u)
+    F, G = gp.GrapeProblem.from_workload(w, precision=prec).gradient(w.u)
     assert abs(F - F_ref) < TOL * abs(F_ref)
     assert rel(G, G_ref) < TOL
 
 
-def test_edge_one_level_system(gp):
+@pytest.mark.parametrize("prec", PRECS)
+def test_edge_one_level_system(gp, prec):
     """Q=1, N=1: d=1, every operator is a number (the trace is conserved)."""
     phys = workloads.Physics(Q=1, N=1, chi=(0.3,), kappa=1.0, controls=("res_x",))
     w = workloads.make("d1", phys, T=1.0, n_slices=3, n_rk=2, states=[(0, 0.0)], u_bound=1.0)
-    F, G = gp.GrapeProblem.from_workload(w).gradient(w.u)
+    F, G = gp.GrapeProblem.from_workload(w, precision=prec).gradient(w.u)
     assert abs(F - 1.0) < 1e-15
     assert np.all(G == 0.0)
 
 
-def test_ragged_dimension_and_transmon_drive(gp):
+@pytest.mark.parametrize("prec", PRECS)
+def test_ragged_dimension_and_transmon_drive(gp, prec):
     """d = 3*7 = 21 (odd, d^2 not a multiple of any cluster width) with all
     four control kinds and a transmon-decay jump."""
     w = workloads.small(Q=3, N=7, n_slices=9, n_rk=3, T=0.9, gamma1=0.2, gamma_phi=0.1,
@@ -191,13 +204,14 @@ def test_ragged_dimension_and_transmon_drive(gp):
     F_ref, G_ref = dense.gradient_exact(m, w.u, w.rho0, w.sigma, w.T, w.n_rk)
     for c in (1, 8):
         with with_cluster(c):
-            P = gp.GrapeProblem.from_workload(w)
+            P = gp.GrapeProblem.from_workload(w, precision=prec)
         F, G = P.gradient(w.u)
         assert abs(F - F_ref) < TOL * abs(F_ref)
         assert rel(G, G_ref) < TOL
 
 
-def test_per_state_sigma_and_non_hermitian_sigma(gp):
+@pytest.mark.parametrize("prec", PRECS)
+def test_per_state_sigma_and_non_hermitian_sigma(gp, prec):
     """sigma enters only through its Hermitian part; per-state targets."""
     w = rich()
     rng = np.random.default_rng(3)
@@ -206,7 +220,8 @@ def test_per_state_sigma_and_non_hermitian_sigma(gp):
     m = operators.build(w.phys)
     sig_h = 0.5 * (sig + np.conj(np.transpose(sig, (0, 2, 1))))
     F_ref, G_ref = dense.gradient_exact(m, w.u, w.rho0, sig_h, w.T, w.n_rk)
-    P = gp.GrapeProblem(gp.band_model(w.phys), w.rho0, sig, w.T, w.n_slices, w.n_rk)
+    P = gp.GrapeProblem(gp.band_model(w.phys), w.rho0, sig, w.T, w.n_slices, w.n_rk,
+                        precision=prec)
     F, G = P.gradient(w.u)
     assert abs(F - F_ref) < TOL * max(1.0, abs(F_ref))
     assert rel(G, G_ref) < TOL
@@ -214,15 +229,18 @@ def test_per_state_sigma_and_non_hermitian_sigma(gp):
 
 def test_d120_full_size_against_c_oracle(gp):
     """The full d=120, N_t=2000, n_RK=4 problem the benchmark times: Phi,
-    rho(T) and the whole gradient against the plain-C oracle."""
+    rho(T) and the whole gradient against the plain-C oracle, in both
+    precisions."""
     w = workloads.transmon_resonator_d120()
     F_ref, G_ref, r_ref, _ = sparse.run_workload(w, threads=3)
-    P = gp.GrapeProblem.from_workload(w)
-    F, r = P.forward(w.u)
-    assert rel(r, r_ref) < TOL
-    F2, G = P.gradient(w.u)
-    assert abs(F - F_ref) < TOL * abs(F_ref)
-    assert rel(G, G_ref) < TOL
-    for rr in r:
-        assert abs(np.trace(rr) - 1) < 1e-12
-        assert np.max(np.abs(rr - rr.conj().T)) < 1e-13
+    for prec in PRECS:
+        P = gp.GrapeProblem.from_workload(w, precision=prec)
+        F, r = P.forward(w.u)
+        assert rel(r, r_ref) < TOL
+        F2, G = P.gradient(w.u)
+        assert abs(F - F_ref) < TOL * abs(F_ref)
+        assert rel(G, G_ref) < TOL
+        for rr in r:
+            assert abs(np.trace(rr) - 1) < 1e-12
+            assert np.max(np.abs(rr - rr.conj().T)) < 1e-13
+        P.close()
