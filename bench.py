@@ -135,6 +135,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_source_sha():
+    """sha256 over the kernel sources (the profile summaries record it)."""
+    h = hashlib.sha256()
+    for f in ("grape_kernels.cuh", "grape_num.cuh", "grape_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1609_03170_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def profiled_traffic(kernel_src_sha):
     """DRAM bytes per launch of the forward propagation kernel from the
     committed ncu summary, if it was taken on the current kernel source."""
@@ -294,8 +302,7 @@ def main():
     dom = "forward" if fwd_ms >= adj_ms else "adjoint"
     dom_ms = (fwd_ms / max(fwd_n, 1)) if dom == "forward" else (adj_ms / max(adj_n, 1))
     achieved = counts["flops_" + dom] / (dom_ms * 1e-3) / 1e12
-    src = open(os.path.join(ROOT, "paper_1609_03170_gb300", "csrc", "grape_kernels.cu"), "rb").read()
-    sha = hashlib.sha256(src).hexdigest()
+    sha = kernel_source_sha()
     traffic = profiled_traffic(sha)
     peaks = {}
     try:

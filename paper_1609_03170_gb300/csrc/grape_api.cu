@@ -206,7 +206,8 @@ struct grape_problem {
     int prec = GRAPE_PREC_DF64;      // number type of the kernels and of every state buffer
     double T = 0.0;
     size_t d2 = 0;
-    int ncl = 1, threads = 256, ept = 1, chunk = 0, halo = 0, win = 0, reach = 0;
+    int ncl = 1, threads = GRAPE_PROP_THREADS, chunk = 0, halo = 0, win = 0, reach = 0;
+    int variant = 0;                 // prop_kernel variant: bit 0 = real jump tables
     size_t smem = 0;
     int ckpt_stride = 0;
     int seg = 0, nseg = 0;           // gradient segment plan (0 until first gradient)
@@ -298,8 +299,8 @@ grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
 
 // Kernel launches in the problem's number type.
 cudaError_t k_prop(const grape_problem *P, const PropArgs &a, cudaStream_t s) {
-    return P->prec == GRAPE_PREC_FP64 ? grape_launch_prop_f64(a, P->threads, P->ept, P->smem, s)
-                                      : grape_launch_prop_df(a, P->threads, P->ept, P->smem, s);
+    return P->prec == GRAPE_PREC_FP64 ? grape_launch_prop_f64(a, P->threads, P->variant, P->smem, s)
+                                      : grape_launch_prop_df(a, P->threads, P->variant, P->smem, s);
 }
 cudaError_t k_trace(const grape_problem *P, const TraceArgs &t, cudaStream_t s) {
     return P->prec == GRAPE_PREC_FP64 ? grape_launch_trace_f64(t, s) : grape_launch_trace_df(t, s);
@@ -340,19 +341,22 @@ grape_status choose_geometry(grape_problem *P, int omax) {
     for (;;) {
         const int chunk = (int)((d2 + ncl - 1) / ncl);
         const int win = chunk + 2 * P->halo;
-        const size_t smem = ((size_t)2 * win + 2 * (size_t)nb * P->d + 2 * (size_t)nt * P->d) * sizeof(double2);
-        const int threads = 256;   // the kernel is compiled for 256-thread blocks
-        const int ept = pow2ceil((chunk + threads - 1) / threads);
-        bool ok = smem <= (size_t)max_smem && ept <= 16;
+        // windows, base values and accumulators, bands, jump tables (16 B each),
+        // plus the (row, column) table of the owned entries
+        const size_t smem = ((size_t)2 * win + 2 * (size_t)chunk + 2 * (size_t)nb * P->d +
+                             2 * (size_t)nt * P->d) * sizeof(double2) + (size_t)chunk * sizeof(int2);
+        const int threads = GRAPE_PROP_THREADS;
+        bool ok = smem <= (size_t)max_smem;
         if (ok) {
             // the attribute is an upper bound shared by all problems: use the device maximum
-            cudaError_t e = P->prec == GRAPE_PREC_FP64 ? grape_prepare_prop_f64(ept, (size_t)max_smem, ncl)
-                                                       : grape_prepare_prop_df(ept, (size_t)max_smem, ncl);
+            cudaError_t e = P->prec == GRAPE_PREC_FP64
+                                ? grape_prepare_prop_f64(P->variant, (size_t)max_smem, ncl)
+                                : grape_prepare_prop_df(P->variant, (size_t)max_smem, ncl);
             int clusters = 0;
             if (e == cudaSuccess)
                 e = P->prec == GRAPE_PREC_FP64
-                        ? grape_max_active_clusters_f64(threads, ept, smem, ncl, ncl * P->ns, &clusters)
-                        : grape_max_active_clusters_df(threads, ept, smem, ncl, ncl * P->ns, &clusters);
+                        ? grape_max_active_clusters_f64(threads, P->variant, smem, ncl, ncl * P->ns, &clusters)
+                        : grape_max_active_clusters_df(threads, P->variant, smem, ncl, ncl * P->ns, &clusters);
             if (e != cudaSuccess) cudaGetLastError();
             ok = (e == cudaSuccess && clusters >= 1);
             if (ok) {
@@ -361,7 +365,6 @@ grape_status choose_geometry(grape_problem *P, int omax) {
                 P->win = win;
                 P->smem = smem;
                 P->threads = threads;
-                P->ept = ept;
                 P->reach = (ncl > 1) ? (P->halo + chunk - 1) / chunk : 0;
                 return GRAPE_OK;
             }
@@ -635,6 +638,13 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
     P->ckpt_stride = desc->ckpt_stride;
     P->prec = desc->precision;
     auto bail = [&](grape_status s) { delete P; return s; };
+    {
+        bool real_jumps = true;
+        for (const HostDir *h : {&hf, &ha})
+            for (const auto *v : {&h->vL, &h->vR})
+                for (const cplx &c : *v) real_jumps = real_jumps && c.imag() == 0.0;
+        P->variant = real_jumps ? 1 : 0;
+    }
     if ((st = upload_dir(P, hf, &P->tab[0])) != GRAPE_OK) return bail(st);
     if ((st = upload_dir(P, ha, &P->tab[1])) != GRAPE_OK) return bail(st);
     int omax = 0;
@@ -685,7 +695,7 @@ grape_status grape_problem_geometry(grape_problem_t P, int32_t *cluster, int32_t
     if (!P) return fail(GRAPE_EINVAL, "NULL problem");
     if (cluster) *cluster = P->ncl;
     if (threads) *threads = P->threads;
-    if (ept) *ept = P->ept;
+    if (ept) *ept = (P->chunk + P->threads - 1) / P->threads;
     return GRAPE_OK;
 }
 

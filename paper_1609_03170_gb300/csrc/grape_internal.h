@@ -10,6 +10,7 @@
 #define GRAPE_MAXR 8     // control Hamiltonians
 #define GRAPE_MAXCB 8    // (control, band) pairs seen by the trace kernel
 #define GRAPE_MAXDO 8    // distinct band offsets among the control bands
+#define GRAPE_PROP_THREADS 512   // threads per CTA of the propagation kernel
 
 // One direction of the Lindblad action in the common form
 //   W = -i (A X - X A^+) + sum_t vL_t[i] conj(vR_t[j]) X[i + oL_t][j + oR_t]
@@ -76,11 +77,11 @@ struct TraceArgs {
 
 // Launchers, one set per number type: _f64 native FP64, _df double-float.
 #define GRAPE_DECLARE_LAUNCHERS(SUFFIX)                                                        \
-    cudaError_t grape_launch_prop_##SUFFIX(const PropArgs &p, int threads, int ept, size_t smem, \
-                                           cudaStream_t stream);                                \
-    cudaError_t grape_prepare_prop_##SUFFIX(int ept, size_t smem, int ncl);                    \
-    cudaError_t grape_max_active_clusters_##SUFFIX(int threads, int ept, size_t smem, int ncl,  \
-                                                   int n_blocks, int *clusters);               \
+    cudaError_t grape_launch_prop_##SUFFIX(const PropArgs &p, int threads, int variant,         \
+                                           size_t smem, cudaStream_t stream);                   \
+    cudaError_t grape_prepare_prop_##SUFFIX(int variant, size_t smem, int ncl);                \
+    cudaError_t grape_max_active_clusters_##SUFFIX(int threads, int variant, size_t smem,       \
+                                                   int ncl, int n_blocks, int *clusters);      \
     cudaError_t grape_launch_trace_##SUFFIX(const TraceArgs &p, cudaStream_t stream);          \
     cudaError_t grape_launch_cost_##SUFFIX(const void *rho, const void *sigma, int n_states,    \
                                            int d2, double *F, cudaStream_t stream);             \

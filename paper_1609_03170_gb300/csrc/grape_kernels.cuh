@@ -88,24 +88,30 @@ __device__ __forceinline__ void push_value(S *buf, const PropArgs &p, int rank, 
 
 // W = Op(z) at element (i, j) of the window `cur` (local flat index le):
 //   W = -i (A z - z A^+)[i][j] + sum_t vL_t[i] conj(vR_t[j]) z[i+oL_t][j+oR_t]
-template <class Num>
+// REALJ: the jump tables are real, so each jump coefficient is one real
+// product.  Loops run over the problem's band and term counts (kept rolled:
+// the pair arithmetic makes every iteration long, and unrolled copies
+// overflow the instruction cache).
+template <class Num, bool REALJ>
 __device__ __forceinline__ typename Num::val lindblad_at(const typename Num::store_t *cur, int le,
                                                          int i, int j, int d, const PropTables &t,
                                                          const typename Num::store_t *A,
                                                          const typename Num::store_t *vL,
                                                          const typename Num::store_t *vR) {
     typename Num::acc w = Num::acc_zero();
-#pragma unroll
-    for (int b = 0; b < GRAPE_MAXB; ++b) {
-        if (b < t.nb) {
-            Num::mac(w, Num::load(A[b * d + i]), Num::load(cur[le + t.off_row[b]]));
-            Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[le + t.off[b]]));
-        }
+#pragma unroll 1
+    for (int b = 0; b < t.nb; ++b) {
+        Num::mac(w, Num::load(A[b * d + i]), Num::load(cur[le + t.off_row[b]]));
+        Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[le + t.off[b]]));
     }
     w = Num::acc_minus_i(w);                     // -i (A z - z A^+)
-#pragma unroll
-    for (int q = 0; q < GRAPE_MAXT; ++q) {
-        if (q < t.nt) {
+#pragma unroll 1
+    for (int q = 0; q < t.nt; ++q) {
+        if (REALJ) {
+            const typename Num::real_t c =
+                Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j])));
+            Num::mac_real(w, c, Num::load(cur[le + t.jflat[q]]));
+        } else {
             const typename Num::val coef = Num::mul_conjb(Num::load(vL[q * d + i]),
                                                           Num::load(vR[q * d + j]));
             Num::mac(w, coef, Num::load(cur[le + t.jflat[q]]));
@@ -114,18 +120,29 @@ __device__ __forceinline__ typename Num::val lindblad_at(const typename Num::sto
     return Num::done(w);
 }
 
-template <class Num, int EPT>
-__global__ void __launch_bounds__(256) prop_kernel(const PropArgs p) {
+// Shared-memory layout of prop_kernel (all 16-byte entries in storage format):
+//   buf0, buf1 [win]      stage-input windows (chunk + halo on both sides)
+//   xs, as     [chunk]    base value and RK accumulator of the owned entries
+//   bands      [2][nb][d] A(u_j) of the current and the next slice
+//   vL, vR     [nt][d]    jump tables
+//   rc         [chunk]    (row, column) of the owned entries (int2)
+template <class Num, bool REALJ>
+__global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_kernel(const PropArgs p) {
     using S = typename Num::store_t;
     using V = typename Num::val;
+    using R = typename Num::real_t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    S *buf0 = reinterpret_cast<S *>(smem_raw);
-    S *buf1 = buf0 + p.win;
     const int d = p.d, d2 = d * d;
     const int nbd = p.tab.nb * d;
-    S *bands = buf1 + p.win;                 // [2][nb][d]
+    S *buf0 = reinterpret_cast<S *>(smem_raw);
+    S *buf1 = buf0 + p.win;
+    S *xs = buf1 + p.win;
+    S *as = xs + p.chunk;
+    S *bands = as + p.chunk;                 // [2][nb][d]
     S *vL = bands + 2 * nbd;                 // [nt][d]
     S *vR = vL + p.tab.nt * d;               // [nt][d]
+    int2 *rc = reinterpret_cast<int2 *>(vR + p.tab.nt * d);
+    __shared__ R cg[4], ca[4], cb[4];
     const S *x_in = static_cast<const S *>(p.x_in);
     S *x_out = static_cast<S *>(p.x_out);
     S *stage_store = static_cast<S *>(p.stage_store);
@@ -137,19 +154,19 @@ __global__ void __launch_bounds__(256) prop_kernel(const PropArgs p) {
     const int e1 = min(e0 + p.chunk, d2);
     const int wbase = e0 - p.halo;
     const size_t soff = (size_t)state * d2;
+    const int nth = blockDim.x;
 
     const V vzero = Num::zero();
-    for (int i = threadIdx.x; i < 2 * p.win; i += blockDim.x) buf0[i] = Num::store(vzero);
-    for (int i = threadIdx.x; i < p.tab.nt * d; i += blockDim.x) {
+    for (int i = threadIdx.x; i < 2 * p.win; i += nth) buf0[i] = Num::store(vzero);
+    for (int i = threadIdx.x; i < p.tab.nt * d; i += nth) {
         vL[i] = Num::store(Num::from_double2(__ldg(&p.tab.vL[i])));
         vR[i] = Num::store(Num::from_double2(__ldg(&p.tab.vR[i])));
     }
-    typename Num::real_t g[4], a[4], b[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        g[s] = Num::real_const(p.g[s]);
-        a[s] = Num::real_const(p.a[s]);
-        b[s] = Num::real_const(p.b[s]);
+    for (int e = e0 + threadIdx.x; e < e1; e += nth) rc[e - e0] = make_int2(e / d, e % d);
+    if (threadIdx.x < 4) {
+        cg[threadIdx.x] = Num::real_const(p.g[threadIdx.x]);
+        ca[threadIdx.x] = Num::real_const(p.a[threadIdx.x]);
+        cb[threadIdx.x] = Num::real_const(p.b[threadIdx.x]);
     }
     const long long nsub = p.sub_end - p.sub_begin;
     long long n_first = p.reverse ? p.sub_end - 1 : p.sub_begin;
@@ -158,16 +175,10 @@ __global__ void __launch_bounds__(256) prop_kernel(const PropArgs p) {
     build_bands<Num>(bands, p, jcur);
     cluster_sync_all();   // every CTA of the cluster runs and has zeroed its windows
 
-    V x[EPT], acc[EPT];
-    int el[EPT], ri[EPT], ci[EPT];
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-        const int e = e0 + threadIdx.x + k * blockDim.x;
-        el[k] = (e < e1) ? e : -1;
-        ri[k] = (e < e1) ? e / d : 0;
-        ci[k] = (e < e1) ? e - (e / d) * d : 0;
-        x[k] = (e < e1) ? Num::load(x_in[soff + e]) : vzero;
-        if (e < e1) push_value(buf0, p, rank, e, Num::store(Num::scale(g[0], x[k])));
+    for (int e = e0 + threadIdx.x; e < e1; e += nth) {
+        const V x = Num::load(x_in[soff + e]);
+        xs[e - e0] = Num::store(x);
+        push_value(buf0, p, rank, e, Num::store(Num::scale(cg[0], x)));
     }
     cluster_sync_all();
 
@@ -177,36 +188,35 @@ __global__ void __launch_bounds__(256) prop_kernel(const PropArgs p) {
         const long long tidx = p.reverse ? n + 1 : n;
         if (bound_store && ((tidx - p.sub_begin) % p.bound_step) == 0) {
             S *dst = bound_store + ((size_t)((tidx - p.sub_begin) / p.bound_step) * p.n_states) * d2 + soff;
-#pragma unroll
-            for (int k = 0; k < EPT; ++k)
-                if (el[k] >= 0) dst[el[k]] = Num::store(x[k]);
+            for (int e = e0 + threadIdx.x; e < e1; e += nth) dst[e] = xs[e - e0];
         }
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) acc[k] = x[k];
         const S *A = bands + tb * nbd;
         bool flip = false;
-#pragma unroll
+#pragma unroll 1
         for (int s = 0; s < 4; ++s) {
             const S *cur = (s & 1) ? buf1 : buf0;
             S *nxt = (s & 1) ? buf0 : buf1;
             S *st = nullptr;
             if (stage_store)
                 st = stage_store + ((size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states) * d2 + soff;
-#pragma unroll
-            for (int k = 0; k < EPT; ++k) {
-                if (el[k] < 0) continue;
-                const int le = el[k] - wbase;
-                const V w = lindblad_at<Num>(cur, le, ri[k], ci[k], d, p.tab, A, vL, vR);
-                if (st) st[el[k]] = cur[le];
-                acc[k] = Num::axpy(a[s], w, acc[k]);
+            const R as_ = ca[s];
+#pragma unroll 1
+            for (int e = e0 + threadIdx.x; e < e1; e += nth) {
+                const int le = e - wbase, li = e - e0;
+                const int2 ij = rc[li];
+                const V w = lindblad_at<Num, REALJ>(cur, le, ij.x, ij.y, d, p.tab, A, vL, vR);
+                if (st) st[e] = cur[le];
+                const V x = Num::load(xs[li]);
+                const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
                 V z;
                 if (s < 3) {
-                    z = Num::lin2(g[s + 1], x[k], b[s + 1], w);
+                    as[li] = Num::store(acc);
+                    z = Num::lin2(cg[s + 1], x, cb[s + 1], w);
                 } else {
-                    x[k] = acc[k];
-                    z = Num::scale(g[0], x[k]);
+                    xs[li] = Num::store(acc);
+                    z = Num::scale(cg[0], acc);
                 }
-                push_value(nxt, p, rank, el[k], Num::store(z));
+                push_value(nxt, p, rank, e, Num::store(z));
             }
             if (s == 3 && it + 1 < nsub) {
                 const long long nn = p.reverse ? n - 1 : n + 1;
@@ -224,13 +234,9 @@ __global__ void __launch_bounds__(256) prop_kernel(const PropArgs p) {
     const long long tend = p.reverse ? p.sub_begin : p.sub_end;
     if (bound_store && ((tend - p.sub_begin) % p.bound_step) == 0) {
         S *dst = bound_store + ((size_t)((tend - p.sub_begin) / p.bound_step) * p.n_states) * d2 + soff;
-#pragma unroll
-        for (int k = 0; k < EPT; ++k)
-            if (el[k] >= 0) dst[el[k]] = Num::store(x[k]);
+        for (int e = e0 + threadIdx.x; e < e1; e += nth) dst[e] = xs[e - e0];
     }
-#pragma unroll
-    for (int k = 0; k < EPT; ++k)
-        if (el[k] >= 0) x_out[soff + el[k]] = Num::store(x[k]);
+    for (int e = e0 + threadIdx.x; e < e1; e += nth) x_out[soff + e] = xs[e - e0];
 }
 
 template <class Num>
@@ -246,35 +252,28 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
     const S *Kb = static_cast<const S *>(p.K);
     const S *Yb = static_cast<const S *>(p.Y);
 
+#pragma unroll 1
     for (long long q = 0; q < p.npairs; ++q) {
         const size_t moff = ((size_t)row * p.npairs + q) * d2;
         const S *K = Kb + moff;
         const S *Y = Yb + moff;
+#pragma unroll 1
         for (int m = warp; m < d; m += nwarps) {
-            typename Num::acc P[GRAPE_MAXDO];
+#pragma unroll 1
+            for (int o = 0; o < p.ndo; ++o) {
+                const int r = m + p.do_off[o];
+                if (r < 0 || r >= d) continue;
+                typename Num::acc P = Num::acc_zero();
+#pragma unroll 1
+                for (int l = lane; l < d; l += 32)
+                    Num::mac_conjb(P, Num::load(K[(size_t)r * d + l]), Num::load(Y[(size_t)m * d + l]));
+                const double2 pv = Num::to_double2(Num::done(P));
 #pragma unroll
-            for (int o = 0; o < GRAPE_MAXDO; ++o) P[o] = Num::acc_zero();
-            for (int l = lane; l < d; l += 32) {
-                const typename Num::val y = Num::load(Y[(size_t)m * d + l]);
-#pragma unroll
-                for (int o = 0; o < GRAPE_MAXDO; ++o) {
-                    if (o < p.ndo) {
-                        const int r = m + p.do_off[o];
-                        if (r >= 0 && r < d) Num::mac_conjb(P[o], Num::load(K[(size_t)r * d + l]), y);
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = 0; o < GRAPE_MAXDO; ++o) {
-                if (o < p.ndo) {
-                    const double2 pv = Num::to_double2(Num::done(P[o]));
-#pragma unroll
-                    for (int c = 0; c < GRAPE_MAXCB; ++c) {
-                        if (c < p.ncb && p.cb_do[c] == o) {
-                            const double2 hv = __ldg(&p.cb_val[(size_t)c * d + m]);
-                            Z[c].x = fma(hv.x, pv.x, fma(-hv.y, pv.y, Z[c].x));
-                            Z[c].y = fma(hv.x, pv.y, fma(hv.y, pv.x, Z[c].y));
-                        }
+                for (int c = 0; c < GRAPE_MAXCB; ++c) {
+                    if (c < p.ncb && p.cb_do[c] == o) {
+                        const double2 hv = __ldg(&p.cb_val[(size_t)c * d + m]);
+                        Z[c].x = fma(hv.x, pv.x, fma(-hv.y, pv.y, Z[c].x));
+                        Z[c].y = fma(hv.x, pv.y, fma(hv.y, pv.x, Z[c].y));
                     }
                 }
             }
@@ -340,7 +339,7 @@ __global__ void __launch_bounds__(256) to_double_kernel(const void *src_v, doubl
 }
 
 // ------------------------------------------------------------------ launchers
-template <class Num, int EPT>
+template <class Num, bool REALJ>
 cudaError_t launch_prop_t(const PropArgs &p, int threads, size_t smem, cudaStream_t stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(p.n_states * p.ncl));
@@ -354,21 +353,21 @@ cudaError_t launch_prop_t(const PropArgs &p, int threads, size_t smem, cudaStrea
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, prop_kernel<Num, EPT>, p);
+    return cudaLaunchKernelEx(&cfg, prop_kernel<Num, REALJ>, p);
 }
 
-template <class Num, int EPT>
+template <class Num, bool REALJ>
 cudaError_t prepare_t(size_t smem, int ncl) {
-    cudaError_t e = cudaFuncSetAttribute(prop_kernel<Num, EPT>,
+    cudaError_t e = cudaFuncSetAttribute(prop_kernel<Num, REALJ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (ncl > 8)
-        e = cudaFuncSetAttribute(prop_kernel<Num, EPT>,
+        e = cudaFuncSetAttribute(prop_kernel<Num, REALJ>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
 
-template <class Num, int EPT>
+template <class Num, bool REALJ>
 cudaError_t clusters_t(int threads, size_t smem, int ncl, int n_blocks, int *clusters) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)n_blocks);
@@ -381,43 +380,25 @@ cudaError_t clusters_t(int threads, size_t smem, int ncl, int n_blocks, int *clu
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(clusters, prop_kernel<Num, EPT>, &cfg);
+    return cudaOccupancyMaxActiveClusters(clusters, prop_kernel<Num, REALJ>, &cfg);
+}
+
+// `variant` bit 0: the jump tables are real.
+template <class Num>
+cudaError_t launch_prop(const PropArgs &p, int threads, int variant, size_t smem, cudaStream_t s) {
+    return (variant & 1) ? launch_prop_t<Num, true>(p, threads, smem, s)
+                         : launch_prop_t<Num, false>(p, threads, smem, s);
 }
 
 template <class Num>
-cudaError_t launch_prop(const PropArgs &p, int threads, int ept, size_t smem, cudaStream_t s) {
-    switch (ept) {
-    case 1: return launch_prop_t<Num, 1>(p, threads, smem, s);
-    case 2: return launch_prop_t<Num, 2>(p, threads, smem, s);
-    case 4: return launch_prop_t<Num, 4>(p, threads, smem, s);
-    case 8: return launch_prop_t<Num, 8>(p, threads, smem, s);
-    case 16: return launch_prop_t<Num, 16>(p, threads, smem, s);
-    default: return cudaErrorInvalidValue;
-    }
+cudaError_t prepare(int variant, size_t smem, int ncl) {
+    return (variant & 1) ? prepare_t<Num, true>(smem, ncl) : prepare_t<Num, false>(smem, ncl);
 }
 
 template <class Num>
-cudaError_t prepare(int ept, size_t smem, int ncl) {
-    switch (ept) {
-    case 1: return prepare_t<Num, 1>(smem, ncl);
-    case 2: return prepare_t<Num, 2>(smem, ncl);
-    case 4: return prepare_t<Num, 4>(smem, ncl);
-    case 8: return prepare_t<Num, 8>(smem, ncl);
-    case 16: return prepare_t<Num, 16>(smem, ncl);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template <class Num>
-cudaError_t max_clusters(int threads, int ept, size_t smem, int ncl, int n_blocks, int *clusters) {
-    switch (ept) {
-    case 1: return clusters_t<Num, 1>(threads, smem, ncl, n_blocks, clusters);
-    case 2: return clusters_t<Num, 2>(threads, smem, ncl, n_blocks, clusters);
-    case 4: return clusters_t<Num, 4>(threads, smem, ncl, n_blocks, clusters);
-    case 8: return clusters_t<Num, 8>(threads, smem, ncl, n_blocks, clusters);
-    case 16: return clusters_t<Num, 16>(threads, smem, ncl, n_blocks, clusters);
-    default: return cudaErrorInvalidValue;
-    }
+cudaError_t max_clusters(int threads, int variant, size_t smem, int ncl, int n_blocks, int *clusters) {
+    return (variant & 1) ? clusters_t<Num, true>(threads, smem, ncl, n_blocks, clusters)
+                         : clusters_t<Num, false>(threads, smem, ncl, n_blocks, clusters);
 }
 
 template <class Num>
@@ -445,16 +426,16 @@ cudaError_t launch_to_double(const void *src, double2 *dst, size_t n, cudaStream
 }  // namespace grape_k
 
 #define GRAPE_DEFINE_LAUNCHERS(SUFFIX, NUM)                                                     \
-    cudaError_t grape_launch_prop_##SUFFIX(const PropArgs &p, int threads, int ept, size_t smem, \
-                                           cudaStream_t s) {                                    \
-        return grape_k::launch_prop<NUM>(p, threads, ept, smem, s);                             \
+    cudaError_t grape_launch_prop_##SUFFIX(const PropArgs &p, int threads, int variant,         \
+                                           size_t smem, cudaStream_t s) {                       \
+        return grape_k::launch_prop<NUM>(p, threads, variant, smem, s);                         \
     }                                                                                           \
-    cudaError_t grape_prepare_prop_##SUFFIX(int ept, size_t smem, int ncl) {                    \
-        return grape_k::prepare<NUM>(ept, smem, ncl);                                           \
+    cudaError_t grape_prepare_prop_##SUFFIX(int variant, size_t smem, int ncl) {                \
+        return grape_k::prepare<NUM>(variant, smem, ncl);                                       \
     }                                                                                           \
-    cudaError_t grape_max_active_clusters_##SUFFIX(int threads, int ept, size_t smem, int ncl,  \
-                                                   int n_blocks, int *clusters) {               \
-        return grape_k::max_clusters<NUM>(threads, ept, smem, ncl, n_blocks, clusters);         \
+    cudaError_t grape_max_active_clusters_##SUFFIX(int threads, int variant, size_t smem,       \
+                                                   int ncl, int n_blocks, int *clusters) {      \
+        return grape_k::max_clusters<NUM>(threads, variant, smem, ncl, n_blocks, clusters);     \
     }                                                                                           \
     cudaError_t grape_launch_trace_##SUFFIX(const TraceArgs &p, cudaStream_t s) {               \
         return grape_k::launch_trace<NUM>(p, s);                                                \

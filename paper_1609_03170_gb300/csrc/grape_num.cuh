@@ -110,6 +110,13 @@ struct NumD {
         return {fma(a.re, b.re, a.im * b.im), fma(a.im, b.re, -a.re * b.im)};
     }
     static __device__ __forceinline__ val minus_i(val a) { return {a.im, -a.re}; }
+    static __device__ __forceinline__ real_t re(val a) { return a.re; }
+    static __device__ __forceinline__ real_t real_mul(real_t a, real_t b) { return a * b; }
+    // acc += c * b, c real
+    static __device__ __forceinline__ void mac_real(acc &w, real_t c, val b) {
+        w.re = fma(c, b.re, w.re);
+        w.im = fma(c, b.im, w.im);
+    }
     // x + s*w
     static __device__ __forceinline__ val axpy(real_t s, val w, val x) {
         return {fma(s, w.re, x.re), fma(s, w.im, x.im)};
@@ -165,6 +172,12 @@ struct NumF {
     }
     static __device__ __forceinline__ val minus_i(val a) {
         return {a.im, {-a.re.h, -a.re.l}};
+    }
+    static __device__ __forceinline__ real_t re(val a) { return a.re; }
+    static __device__ __forceinline__ real_t real_mul(real_t a, real_t b) { return ff_mul(a, b); }
+    static __device__ __forceinline__ void mac_real(acc &w, real_t c, val b) {
+        lacc_fma(w.re, c.h, c.l, b.re.h, b.re.l);
+        lacc_fma(w.im, c.h, c.l, b.im.h, b.im.l);
     }
     static __device__ __forceinline__ val axpy(real_t s, val w, val x) {
         return {ff_add(x.re, ff_mul(s, w.re)), ff_add(x.im, ff_mul(s, w.im))};
