@@ -333,48 +333,47 @@ grape_status choose_geometry(grape_problem *P, int omax) {
     const long long d2 = (long long)P->d2;
     P->halo = omax * (P->d + 1);
     const int nb = std::max(P->tab[0].nb, P->tab[1].nb), nt = std::max(P->tab[0].nt, P->tab[1].nt);
-    int ncl = std::min(16, pow2ceil((d2 + 1023) / 1024));
+    int start = std::min(16, pow2ceil((d2 + 1023) / 1024));
     if (const char *env = std::getenv("GRAPE_CLUSTER")) {
         const int v = std::atoi(env);
-        if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) ncl = v;
+        if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) start = v;
     }
-    for (;;) {
+    cudaError_t e = P->prec == GRAPE_PREC_FP64 ? grape_prepare_prop_f64(P->variant, (size_t)max_smem, 16)
+                                               : grape_prepare_prop_df(P->variant, (size_t)max_smem, 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GRAPE_ECUDA, std::string("prop kernel attributes: ") + cudaGetErrorString(e));
+    }
+    // candidate cluster widths: the preferred one and wider, then narrower (bounded search)
+    int widths[8], nw = 0;
+    for (int c = start; c <= 16; c *= 2) widths[nw++] = c;
+    for (int c = start / 2; c >= 1; c /= 2) widths[nw++] = c;
+    for (int wi = 0; wi < nw; ++wi) {
+        const int ncl = widths[wi];
         const int chunk = (int)((d2 + ncl - 1) / ncl);
         const int win = chunk + 2 * P->halo;
         // windows, base values and accumulators, bands, jump tables (16 B each),
-        // plus the (row, column) table of the owned entries
+        // the (row, column) table of the owned entries and 12 RK coefficients
         const size_t smem = ((size_t)2 * win + 2 * (size_t)chunk + 2 * (size_t)nb * P->d +
-                             2 * (size_t)nt * P->d) * sizeof(double2) + (size_t)chunk * sizeof(int2);
-        const int threads = GRAPE_PROP_THREADS;
-        bool ok = smem <= (size_t)max_smem;
-        if (ok) {
-            // the attribute is an upper bound shared by all problems: use the device maximum
-            cudaError_t e = P->prec == GRAPE_PREC_FP64
-                                ? grape_prepare_prop_f64(P->variant, (size_t)max_smem, ncl)
-                                : grape_prepare_prop_df(P->variant, (size_t)max_smem, ncl);
-            int clusters = 0;
-            if (e == cudaSuccess)
-                e = P->prec == GRAPE_PREC_FP64
-                        ? grape_max_active_clusters_f64(threads, P->variant, smem, ncl, ncl * P->ns, &clusters)
-                        : grape_max_active_clusters_df(threads, P->variant, smem, ncl, ncl * P->ns, &clusters);
-            if (e != cudaSuccess) cudaGetLastError();
-            ok = (e == cudaSuccess && clusters >= 1);
-            if (ok) {
-                P->ncl = ncl;
-                P->chunk = chunk;
-                P->win = win;
-                P->smem = smem;
-                P->threads = threads;
-                P->reach = (ncl > 1) ? (P->halo + chunk - 1) / chunk : 0;
-                return GRAPE_OK;
-            }
-            if (ncl > 1 && smem <= (size_t)max_smem) {   // cluster too wide to schedule: narrow it
-                ncl /= 2;
-                if (ncl >= 1) continue;
-            }
+                             2 * (size_t)nt * P->d) * sizeof(double2) +
+                            (size_t)chunk * sizeof(int2) + 12 * sizeof(double);
+        if (smem + 1024 > (size_t)max_smem) continue;   // keep room for static shared memory
+        int clusters = 0;
+        e = P->prec == GRAPE_PREC_FP64
+                ? grape_max_active_clusters_f64(GRAPE_PROP_THREADS, P->variant, smem, ncl, ncl * P->ns, &clusters)
+                : grape_max_active_clusters_df(GRAPE_PROP_THREADS, P->variant, smem, ncl, ncl * P->ns, &clusters);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
         }
-        if (ncl >= 16) break;
-        ncl *= 2;
+        if (clusters < 1) continue;
+        P->ncl = ncl;
+        P->chunk = chunk;
+        P->win = win;
+        P->smem = smem;
+        P->threads = GRAPE_PROP_THREADS;
+        P->reach = (ncl > 1) ? (P->halo + chunk - 1) / chunk : 0;
+        return GRAPE_OK;
     }
     return fail(GRAPE_EINVAL, "problem too large for the cluster propagation kernel "
                               "(state window does not fit in shared memory)");

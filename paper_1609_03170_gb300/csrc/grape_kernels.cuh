@@ -31,9 +31,14 @@ namespace grape_k {
 
 using namespace grape_num;
 
+// Cluster-wide barrier between RK stages.  The per-entry loops before it
+// leave warps diverged (the chunk is not a multiple of the block size), so
+// the warp is reconverged explicitly and the non-.aligned forms are used,
+// which are defined for threads arriving independently.
 __device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
-                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.release;\n\t"
+                 "barrier.cluster.wait.acquire;" ::: "memory");
 }
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -126,6 +131,7 @@ __device__ __forceinline__ typename Num::val lindblad_at(const typename Num::sto
 //   bands      [2][nb][d] A(u_j) of the current and the next slice
 //   vL, vR     [nt][d]    jump tables
 //   rc         [chunk]    (row, column) of the owned entries (int2)
+//   cg, ca, cb [4] each   RK coefficients in the number type (8 bytes each)
 template <class Num, bool REALJ>
 __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_kernel(const PropArgs p) {
     using S = typename Num::store_t;
@@ -142,7 +148,9 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_kernel(const PropA
     S *vL = bands + 2 * nbd;                 // [nt][d]
     S *vR = vL + p.tab.nt * d;               // [nt][d]
     int2 *rc = reinterpret_cast<int2 *>(vR + p.tab.nt * d);
-    __shared__ R cg[4], ca[4], cb[4];
+    R *cg = reinterpret_cast<R *>(rc + p.chunk);   // RK coefficients g, a, b
+    R *ca = cg + 4;
+    R *cb = cg + 8;
     const S *x_in = static_cast<const S *>(p.x_in);
     S *x_out = static_cast<S *>(p.x_out);
     S *stage_store = static_cast<S *>(p.stage_store);
@@ -242,13 +250,18 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_kernel(const PropA
 template <class Num>
 __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
     using S = typename Num::store_t;
+    extern __shared__ __align__(16) unsigned char tsmem[];
+    S *hv = reinterpret_cast<S *>(tsmem);            // [ncb][d] control band values
     const int row = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int d = p.d;
     const size_t d2 = (size_t)d * d;
-    double2 Z[GRAPE_MAXCB];
+    for (int i = threadIdx.x; i < p.ncb * d; i += blockDim.x)
+        hv[i] = Num::store(Num::from_double2(__ldg(&p.cb_val[i])));
+    __syncthreads();
+    typename Num::acc Z[GRAPE_MAXCB];                // lane-private, in the number type
 #pragma unroll
-    for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = Num::acc_zero();
     const S *Kb = static_cast<const S *>(p.K);
     const S *Yb = static_cast<const S *>(p.Y);
 
@@ -267,23 +280,18 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
 #pragma unroll 1
                 for (int l = lane; l < d; l += 32)
                     Num::mac_conjb(P, Num::load(K[(size_t)r * d + l]), Num::load(Y[(size_t)m * d + l]));
-                const double2 pv = Num::to_double2(Num::done(P));
+                const typename Num::val pv = Num::done(P);
 #pragma unroll
-                for (int c = 0; c < GRAPE_MAXCB; ++c) {
-                    if (c < p.ncb && p.cb_do[c] == o) {
-                        const double2 hv = __ldg(&p.cb_val[(size_t)c * d + m]);
-                        Z[c].x = fma(hv.x, pv.x, fma(-hv.y, pv.y, Z[c].x));
-                        Z[c].y = fma(hv.x, pv.y, fma(hv.y, pv.x, Z[c].y));
-                    }
-                }
+                for (int c = 0; c < GRAPE_MAXCB; ++c)
+                    if (c < p.ncb && p.cb_do[c] == o) Num::mac(Z[c], Num::load(hv[c * d + m]), pv);
             }
         }
     }
-    // deterministic reduction: warp shuffles, then warps in index order
+    // deterministic reduction: warp shuffles, then warps in index order (FP64)
     __shared__ double red[GRAPE_MAXCB][32];
 #pragma unroll
     for (int c = 0; c < GRAPE_MAXCB; ++c) {
-        double v = Z[c].y;
+        double v = Num::to_double2(Num::done(Z[c])).y;
 #pragma unroll
         for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
         if (lane == 0) red[c][warp] = v;
@@ -356,10 +364,16 @@ cudaError_t launch_prop_t(const PropArgs &p, int threads, size_t smem, cudaStrea
     return cudaLaunchKernelEx(&cfg, prop_kernel<Num, REALJ>, p);
 }
 
+// smem_total: the per-block shared-memory budget; the dynamic limit is that
+// budget minus the kernel's static shared memory.
 template <class Num, bool REALJ>
-cudaError_t prepare_t(size_t smem, int ncl) {
-    cudaError_t e = cudaFuncSetAttribute(prop_kernel<Num, REALJ>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t prepare_t(size_t smem_total, int ncl) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, prop_kernel<Num, REALJ>);
+    if (e != cudaSuccess) return e;
+    if (fa.sharedSizeBytes > smem_total) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(prop_kernel<Num, REALJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(smem_total - fa.sharedSizeBytes));
     if (e != cudaSuccess) return e;
     if (ncl > 8)
         e = cudaFuncSetAttribute(prop_kernel<Num, REALJ>,
@@ -404,7 +418,13 @@ cudaError_t max_clusters(int threads, int variant, size_t smem, int ncl, int n_b
 template <class Num>
 cudaError_t launch_trace(const TraceArgs &p, cudaStream_t s) {
     if (p.n_rows <= 0) return cudaSuccess;
-    trace_kernel<Num><<<p.n_rows, 256, 0, s>>>(p);
+    const size_t smem = (size_t)p.ncb * p.d * sizeof(typename Num::store_t);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(trace_kernel<Num>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    trace_kernel<Num><<<p.n_rows, 256, smem, s>>>(p);
     return cudaGetLastError();
 }
 
