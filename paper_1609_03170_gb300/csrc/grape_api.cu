@@ -207,7 +207,9 @@ struct grape_problem {
     double T = 0.0;
     size_t d2 = 0;
     int ncl = 1, threads = GRAPE_PROP_THREADS, chunk = 0, halo = 0, win = 0, reach = 0;
-    int variant = 0;                 // prop_kernel variant: bit 0 = real jump tables
+    int variant = 0;                 // bit 0 = real jump tables, bit 1 = Hermitian kernel
+    int hb = 0, cu = 0, maxwin = 0, htab_len = 0;   // Hermitian kernel geometry
+    int *d_htab = nullptr;
     size_t smem = 0;
     int ckpt_stride = 0;
     int seg = 0, nseg = 0;           // gradient segment plan (0 until first gradient)
@@ -278,7 +280,11 @@ grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
         t->off[b] = h.off[b];
         t->off_row[b] = h.off[b] * d;
     }
-    for (int q = 0; q < t->nt; ++q) t->jflat[q] = h.oL[q] * d + h.oR[q];
+    for (int q = 0; q < t->nt; ++q) {
+        t->jflat[q] = h.oL[q] * d + h.oR[q];
+        t->joL[q] = h.oL[q];
+        t->joR[q] = h.oR[q];
+    }
     auto cvt = [](const std::vector<cplx> &v) {
         std::vector<double2> o(v.size());
         for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
@@ -379,6 +385,125 @@ grape_status choose_geometry(grape_problem *P, int omax) {
                               "(state window does not fit in shared memory)");
 }
 
+// Geometry of the Hermitian (upper-triangle) kernel for a cluster of ncl
+// CTAs: ownership ranges, compact windows and the table described in
+// grape_internal.h.  Returns the table, the largest window and the entries
+// per CTA.
+std::vector<int> hermitian_table(int d, int ncl, int omax, int hb, int *maxwin, int *cu) {
+    const long long NU = (long long)d * (d + 1) / 2;
+    const int c = (int)((NU + ncl - 1) / ncl);
+    auto row_start = [d](long long i) { return i * d - i * (i - 1) / 2; };
+    auto row_of = [&](long long u) {
+        long long lo = 0, hi = d - 1;
+        while (lo < hi) {
+            const long long mid = (lo + hi + 1) / 2;
+            if (row_start(mid) <= u) lo = mid; else hi = mid - 1;
+        }
+        return (int)lo;
+    };
+    auto cs = [hb](int r) { return r > hb ? r - hb : 0; };
+    std::vector<int> head(4 * ncl), starts(ncl + 1), lists;
+    std::vector<int> wr0(ncl), wr1(ncl);
+    int mw = 0;
+    for (int k = 0; k < ncl; ++k) {
+        const long long u0 = std::min<long long>(NU, (long long)k * c);
+        const long long u1 = std::min<long long>(NU, u0 + c);
+        int r0 = 0, nrows = 0;
+        if (u1 > u0) {
+            r0 = std::max(0, row_of(u0) - omax);
+            const int r1 = std::min(d - 1, row_of(u1 - 1) + omax);
+            nrows = r1 - r0 + 1;
+        }
+        head[4 * k + 0] = (int)u0;
+        head[4 * k + 1] = (int)u1;
+        head[4 * k + 2] = r0;
+        head[4 * k + 3] = nrows;
+        wr0[k] = r0;
+        wr1[k] = r0 + nrows - 1;
+        starts[k] = 4 * ncl + ncl + 1 + (int)lists.size();
+        int acc = 0;
+        lists.push_back(0);
+        for (int r = r0; r < r0 + nrows; ++r) {
+            acc += d - cs(r);
+            lists.push_back(acc);
+        }
+        mw = std::max(mw, acc);
+    }
+    starts[ncl] = 4 * ncl + ncl + 1 + (int)lists.size();
+    std::vector<int> kf(d, ncl), kl(d, -1);
+    for (int k = 0; k < ncl; ++k)
+        for (int r = wr0[k]; r <= wr1[k]; ++r) {
+            kf[r] = std::min(kf[r], k);
+            kl[r] = std::max(kl[r], k);
+        }
+    std::vector<int> tab;
+    tab.insert(tab.end(), head.begin(), head.end());
+    tab.insert(tab.end(), starts.begin(), starts.end());
+    tab.insert(tab.end(), lists.begin(), lists.end());
+    tab.insert(tab.end(), kf.begin(), kf.end());
+    tab.insert(tab.end(), kl.begin(), kl.end());
+    *maxwin = mw;
+    *cu = c;
+    return tab;
+}
+
+grape_status choose_geometry_h(grape_problem *P, int omax, int hb) {
+    int max_smem = 0;
+    GRAPE_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+    const int d = P->d;
+    const long long NU = (long long)d * (d + 1) / 2;
+    const int nb = std::max(P->tab[0].nb, P->tab[1].nb), nt = std::max(P->tab[0].nt, P->tab[1].nt);
+    int start = std::min(16, pow2ceil((NU + 511) / 512));
+    if (const char *env = std::getenv("GRAPE_CLUSTER")) {
+        const int v = std::atoi(env);
+        if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) start = v;
+    }
+    const int variant = P->variant | 2;
+    cudaError_t e = P->prec == GRAPE_PREC_FP64 ? grape_prepare_prop_f64(variant, (size_t)max_smem, 16)
+                                               : grape_prepare_prop_df(variant, (size_t)max_smem, 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GRAPE_ECUDA, std::string("hermitian kernel attributes: ") + cudaGetErrorString(e));
+    }
+    int widths[8], nw = 0;
+    for (int c = start; c <= 16; c *= 2) widths[nw++] = c;
+    for (int c = start / 2; c >= 1; c /= 2) widths[nw++] = c;
+    for (int wi = 0; wi < nw; ++wi) {
+        const int ncl = widths[wi];
+        int maxwin = 0, cu = 0;
+        const std::vector<int> tab = hermitian_table(d, ncl, omax, hb, &maxwin, &cu);
+        const size_t smem = ((size_t)2 * maxwin + 2 * (size_t)cu + 2 * (size_t)nb * d +
+                             2 * (size_t)nt * d) * sizeof(double2) +
+                            (size_t)cu * sizeof(int2) + 12 * sizeof(double) + tab.size() * sizeof(int);
+        if (smem + 1024 > (size_t)max_smem) continue;
+        int clusters = 0;
+        e = P->prec == GRAPE_PREC_FP64
+                ? grape_max_active_clusters_f64(GRAPE_PROP_THREADS, variant, smem, ncl, ncl * P->ns, &clusters)
+                : grape_max_active_clusters_df(GRAPE_PROP_THREADS, variant, smem, ncl, ncl * P->ns, &clusters);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (clusters < 1) continue;
+        grape_status st = upload(P, tab, &P->d_htab);
+        if (st != GRAPE_OK) return st;
+        P->variant = variant;
+        P->ncl = ncl;
+        P->cu = cu;
+        P->maxwin = maxwin;
+        P->hb = hb;
+        P->htab_len = (int)tab.size();
+        P->smem = smem;
+        P->threads = GRAPE_PROP_THREADS;
+        P->chunk = cu;
+        P->halo = 0;
+        P->win = maxwin;
+        P->reach = 0;
+        return GRAPE_OK;
+    }
+    return fail(GRAPE_EINVAL, "problem too large for the Hermitian cluster kernel");
+}
+
 void rk_coefficients(double h, bool adjoint, PropArgs *a) {
     if (!adjoint) {
         const double g[4] = {1.0, 1.0, 1.0, 1.0};
@@ -409,6 +534,11 @@ PropArgs base_args(const grape_problem *P, int dir, const double *u) {
     a.u = u;
     a.n_rk = P->n_rk;
     a.bound_step = 1;
+    a.htab = P->d_htab;
+    a.htab_len = P->htab_len;
+    a.hb = P->hb;
+    a.cu = P->cu;
+    a.maxwin = P->maxwin;
     rk_coefficients(P->T / P->n_slices / P->n_rk, dir == 1, &a);
     return a;
 }
@@ -653,7 +783,19 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
         for (size_t q = 0; q < h.oL.size(); ++q)
             omax = std::max(omax, std::max(std::abs(h.oL[q]), std::abs(h.oR[q])));
     }
-    if ((st = choose_geometry(P, omax)) != GRAPE_OK) return bail(st);
+    int hb = omax;   // lower entries the stencil reads: within max(omax, oL - oR) of the diagonal
+    for (int dir = 0; dir < 2; ++dir) {
+        const HostDir &h = dir ? ha : hf;
+        for (size_t q = 0; q < h.oL.size(); ++q) hb = std::max(hb, h.oL[q] - h.oR[q]);
+    }
+    bool herm = true;
+    if (const char *env = std::getenv("GRAPE_HERMITIAN")) herm = std::atoi(env) != 0;
+    if (herm) {
+        st = choose_geometry_h(P, omax, hb);
+        if (st != GRAPE_OK && st != GRAPE_EINVAL) return bail(st);
+        if (st == GRAPE_EINVAL) herm = false;    // fall back to the full-matrix kernel
+    }
+    if (!herm && (st = choose_geometry(P, omax)) != GRAPE_OK) return bail(st);
     {
         std::vector<double2> r(rho0.size()), g2(sig.size());
         for (size_t i = 0; i < r.size(); ++i) r[i] = encode(P, rho0[i]);

@@ -23,6 +23,8 @@ struct PropTables {
     int off[GRAPE_MAXB];        // band offsets o_b: A_b[i] = A[i][i + o_b]
     int off_row[GRAPE_MAXB];    // o_b * d (flat shift of row i -> i + o_b)
     int jflat[GRAPE_MAXT];      // oL_t * d + oR_t
+    int joL[GRAPE_MAXT];        // oL_t
+    int joR[GRAPE_MAXT];        // oR_t
     const double2 *A0;          // [nb][d]
     const double2 *Ak;          // [R][nb][d]
     const double2 *vL;          // [nt][d]
@@ -54,7 +56,22 @@ struct PropArgs {
     void *stage_store;                  // [(n - sub_begin)][4][n_states][d*d] or null
     void *bound_store;                  // [slot][n_states][d*d] or null
     long long bound_step;               // substeps between bound stores
+    // Hermitian kernel (upper triangle only): the cluster's ownership and
+    // window tables, see GRAPE_HTAB_* below
+    const int *htab;
+    int htab_len;                       // ints in htab
+    int hb;                             // stored half-band below the diagonal
+    int cu;                             // upper-triangle entries per CTA
+    int maxwin;                         // largest window (entries) of the cluster
 };
+
+// Layout of the Hermitian kernel's table (ints), for a cluster of ncl CTAs:
+//   [4k + 0..3]            u0, u1 (owned upper-triangle range), wr0, nrows of CTA k
+//   [4 ncl + k]            start of CTA k's row-offset list (k = 0..ncl)
+//   [row-offset lists]     CTA k: nrows_k + 1 cumulative window offsets
+//   [kfirst[d], klast[d]]  first and last CTA whose window holds row r
+#define GRAPE_HTAB_CTA(k) (4 * (k))
+#define GRAPE_HTAB_LISTS(ncl) (4 * (ncl))
 
 // Trace products of the gradient (Eq. dphidu), per output row j:
 //   G[j][k] = weight * sum_q (-2) Im sum_b sum_m Hk_b[m] P_{o_b}[m],

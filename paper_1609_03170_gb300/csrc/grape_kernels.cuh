@@ -247,6 +247,233 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_kernel(const PropA
     for (int e = e0 + threadIdx.x; e < e1; e += nth) x_out[soff + e] = xs[e - e0];
 }
 
+// ---------------------------------------------------------------------------
+// Hermitian propagation: every stage value is Hermitian (rho, sigma and the
+// stage combinations are, and both Lindbladians preserve it), so only the
+// upper triangle j >= i is computed.  CTA k of the cluster owns the upper
+// entries [u0, u1) in row-major order (equal counts), and its window holds
+// rows [wr0, wr0 + nrows) stored as columns [cs(r), d) with
+// cs(r) = max(0, r - hb): the upper part plus the hb entries left of the
+// diagonal, which are the only lower entries the stencil reads; those are
+// filled with conjugate mirrors of the upper entries near the diagonal.
+// Stage, boundary and output stores to HBM write full matrices (the lower
+// triangle as conjugates), so every other kernel sees ordinary d x d data.
+struct HWin {
+    const int *tab;    // shared-memory copy of htab
+    int ncl, d, hb;
+};
+
+__device__ __forceinline__ int cs_of(int r, int hb) { return r > hb ? r - hb : 0; }
+
+// window offset of (r, c) in CTA k's window
+__device__ __forceinline__ int hwin_addr(const HWin &h, int k, int r, int c) {
+    const int wr0 = h.tab[GRAPE_HTAB_CTA(k) + 2];
+    const int *ofs = h.tab + h.tab[GRAPE_HTAB_LISTS(h.ncl) + k];
+    return ofs[r - wr0] + (c - cs_of(r, h.hb));
+}
+
+// write z at (r, c) into every window of the cluster that holds row r
+template <class S>
+__device__ __forceinline__ void hpush(S *buf, const HWin &h, int rank, int r, int c, S z) {
+    const int *kf = h.tab + (h.tab[GRAPE_HTAB_LISTS(h.ncl) + h.ncl]);
+    const int kfirst = kf[r], klast = kf[h.d + r];
+    for (int k = kfirst; k <= klast; ++k) {
+        S *dst = &buf[hwin_addr(h, k, r, c)];
+        if (k == rank) *dst = z;
+        else st_remote(map_to_rank(smem_u32(dst), (uint32_t)k), z);
+    }
+}
+
+template <class Num>
+__device__ __forceinline__ typename Num::store_t conj_store(typename Num::val v) {
+    v.im = Num::neg_real(v.im);
+    return Num::store(v);
+}
+
+// W = Op(z) at upper entry (i, j), reading the compact window
+template <class Num, bool REALJ>
+__device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::store_t *cur,
+                                                           const int *ofs, int wr0, int i, int j,
+                                                           int d, int hb, const PropTables &t,
+                                                           const typename Num::store_t *A,
+                                                           const typename Num::store_t *vL,
+                                                           const typename Num::store_t *vR) {
+    const int own = ofs[i - wr0] + (j - cs_of(i, hb));
+    typename Num::acc w = Num::acc_zero();
+#pragma unroll 1
+    for (int b = 0; b < t.nb; ++b) {
+        const int o = t.off[b];
+        const int r = i + o;
+        if (r >= 0 && r < d)
+            Num::mac(w, Num::load(A[b * d + i]), Num::load(cur[ofs[r - wr0] + (j - cs_of(r, hb))]));
+        const int c = j + o;
+        if (c >= 0 && c < d)
+            Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[own + o]));
+    }
+    w = Num::acc_minus_i(w);
+#pragma unroll 1
+    for (int q = 0; q < t.nt; ++q) {
+        const int r = i + t.joL[q], c = j + t.joR[q];
+        if (r < 0 || r >= d || c < 0 || c >= d) continue;
+        const typename Num::store_t zv = cur[ofs[r - wr0] + (c - cs_of(r, hb))];
+        if (REALJ) {
+            const typename Num::real_t cf =
+                Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j])));
+            Num::mac_real(w, cf, Num::load(zv));
+        } else {
+            Num::mac(w, Num::mul_conjb(Num::load(vL[q * d + i]), Num::load(vR[q * d + j])),
+                     Num::load(zv));
+        }
+    }
+    return Num::done(w);
+}
+
+// full-matrix store of upper entry (i, j) and its conjugate mirror
+template <class Num>
+__device__ __forceinline__ void store_herm(typename Num::store_t *dst, int d, int i, int j,
+                                           typename Num::store_t v) {
+    dst[(size_t)i * d + j] = v;
+    if (j != i) dst[(size_t)j * d + i] = conj_store<Num>(Num::load(v));
+}
+
+// Shared memory: buf0, buf1 [maxwin]; xs, as [cu]; bands [2][nb][d];
+// vL, vR [nt][d]; rc [cu] (int2); 12 RK coefficients; htab copy (ints).
+template <class Num, bool REALJ>
+__global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const PropArgs p) {
+    using S = typename Num::store_t;
+    using V = typename Num::val;
+    using R = typename Num::real_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int d = p.d, d2 = d * d;
+    const int nbd = p.tab.nb * d;
+    S *buf0 = reinterpret_cast<S *>(smem_raw);
+    S *buf1 = buf0 + p.maxwin;
+    S *xs = buf1 + p.maxwin;
+    S *as = xs + p.cu;
+    S *bands = as + p.cu;
+    S *vL = bands + 2 * nbd;
+    S *vR = vL + p.tab.nt * d;
+    int2 *rc = reinterpret_cast<int2 *>(vR + p.tab.nt * d);
+    R *cg = reinterpret_cast<R *>(rc + p.cu);
+    R *ca = cg + 4;
+    R *cb = cg + 8;
+    int *tab = reinterpret_cast<int *>(cg + 12);
+    const S *x_in = static_cast<const S *>(p.x_in);
+    S *x_out = static_cast<S *>(p.x_out);
+    S *stage_store = static_cast<S *>(p.stage_store);
+    S *bound_store = static_cast<S *>(p.bound_store);
+    const int rank = blockIdx.x % p.ncl;
+    const int state = blockIdx.x / p.ncl;
+    const size_t soff = (size_t)state * d2;
+    const int nth = blockDim.x;
+
+    for (int i = threadIdx.x; i < p.htab_len; i += nth) tab[i] = __ldg(&p.htab[i]);
+    const V vzero = Num::zero();
+    for (int i = threadIdx.x; i < 2 * p.maxwin; i += nth) buf0[i] = Num::store(vzero);
+    for (int i = threadIdx.x; i < p.tab.nt * d; i += nth) {
+        vL[i] = Num::store(Num::from_double2(__ldg(&p.tab.vL[i])));
+        vR[i] = Num::store(Num::from_double2(__ldg(&p.tab.vR[i])));
+    }
+    if (threadIdx.x < 4) {
+        cg[threadIdx.x] = Num::real_const(p.g[threadIdx.x]);
+        ca[threadIdx.x] = Num::real_const(p.a[threadIdx.x]);
+        cb[threadIdx.x] = Num::real_const(p.b[threadIdx.x]);
+    }
+    const long long nsub = p.sub_end - p.sub_begin;
+    long long n_first = p.reverse ? p.sub_end - 1 : p.sub_begin;
+    if (nsub <= 0) n_first = p.sub_begin;
+    int jcur = (int)(n_first / p.n_rk);
+    build_bands<Num>(bands, p, jcur);
+    __syncthreads();
+    const int u0 = tab[GRAPE_HTAB_CTA(rank) + 0], u1 = tab[GRAPE_HTAB_CTA(rank) + 1];
+    const int wr0 = tab[GRAPE_HTAB_CTA(rank) + 2];
+    const int *ofs = tab + tab[GRAPE_HTAB_LISTS(p.ncl) + rank];
+    const HWin hw{tab, p.ncl, d, p.hb};
+    // (row, column) of the owned upper entries: row-major offset of row i is
+    // i d - i (i - 1) / 2
+    for (int u = u0 + threadIdx.x; u < u1; u += nth) {
+        const double b2 = 2.0 * d + 1.0;
+        int i = (int)floor(0.5 * (b2 - sqrt(b2 * b2 - 8.0 * (double)u)));
+        i = max(0, min(d - 1, i));
+        while (i > 0 && (long long)i * d - (long long)i * (i - 1) / 2 > u) --i;
+        while (i + 1 < d && (long long)(i + 1) * d - (long long)(i + 1) * i / 2 <= u) ++i;
+        const int j = i + (int)(u - ((long long)i * d - (long long)i * (i - 1) / 2));
+        rc[u - u0] = make_int2(i, j);
+    }
+    cluster_sync_all();   // every CTA runs, windows zeroed, tables loaded
+
+    for (int u = u0 + threadIdx.x; u < u1; u += nth) {
+        const int2 ij = rc[u - u0];
+        const V x = Num::load(x_in[soff + (size_t)ij.x * d + ij.y]);
+        xs[u - u0] = Num::store(x);
+        const V z = Num::scale(cg[0], x);
+        hpush(buf0, hw, rank, ij.x, ij.y, Num::store(z));
+        if (ij.y > ij.x && ij.y - ij.x <= p.hb) hpush(buf0, hw, rank, ij.y, ij.x, conj_store<Num>(z));
+    }
+    cluster_sync_all();
+
+    int tb = 0;
+    for (long long it = 0; it < nsub; ++it) {
+        const long long n = p.reverse ? p.sub_end - 1 - it : p.sub_begin + it;
+        const long long tidx = p.reverse ? n + 1 : n;
+        if (bound_store && ((tidx - p.sub_begin) % p.bound_step) == 0) {
+            S *dst = bound_store + ((size_t)((tidx - p.sub_begin) / p.bound_step) * p.n_states) * d2 + soff;
+            for (int u = u0 + threadIdx.x; u < u1; u += nth)
+                store_herm<Num>(dst, d, rc[u - u0].x, rc[u - u0].y, xs[u - u0]);
+        }
+        const S *A = bands + tb * nbd;
+        bool flip = false;
+#pragma unroll 1
+        for (int s = 0; s < 4; ++s) {
+            const S *cur = (s & 1) ? buf1 : buf0;
+            S *nxt = (s & 1) ? buf0 : buf1;
+            S *st = nullptr;
+            if (stage_store)
+                st = stage_store + ((size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states) * d2 + soff;
+            const R as_ = ca[s];
+#pragma unroll 1
+            for (int u = u0 + threadIdx.x; u < u1; u += nth) {
+                const int li = u - u0;
+                const int2 ij = rc[li];
+                const V w = lindblad_h_at<Num, REALJ>(cur, ofs, wr0, ij.x, ij.y, d, p.hb, p.tab, A, vL, vR);
+                if (st) store_herm<Num>(st, d, ij.x, ij.y, cur[ofs[ij.x - wr0] + (ij.y - cs_of(ij.x, p.hb))]);
+                const V x = Num::load(xs[li]);
+                const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
+                V z;
+                if (s < 3) {
+                    as[li] = Num::store(acc);
+                    z = Num::lin2(cg[s + 1], x, cb[s + 1], w);
+                } else {
+                    xs[li] = Num::store(acc);
+                    z = Num::scale(cg[0], acc);
+                }
+                hpush(nxt, hw, rank, ij.x, ij.y, Num::store(z));
+                if (ij.y > ij.x && ij.y - ij.x <= p.hb)
+                    hpush(nxt, hw, rank, ij.y, ij.x, conj_store<Num>(z));
+            }
+            if (s == 3 && it + 1 < nsub) {
+                const long long nn = p.reverse ? n - 1 : n + 1;
+                const int jn = (int)(nn / p.n_rk);
+                if (jn != jcur) {
+                    build_bands<Num>(bands + (tb ^ 1) * nbd, p, jn);
+                    jcur = jn;
+                    flip = true;
+                }
+            }
+            cluster_sync_all();
+        }
+        if (flip) tb ^= 1;
+    }
+    const long long tend = p.reverse ? p.sub_begin : p.sub_end;
+    if (bound_store && ((tend - p.sub_begin) % p.bound_step) == 0) {
+        S *dst = bound_store + ((size_t)((tend - p.sub_begin) / p.bound_step) * p.n_states) * d2 + soff;
+        for (int u = u0 + threadIdx.x; u < u1; u += nth)
+            store_herm<Num>(dst, d, rc[u - u0].x, rc[u - u0].y, xs[u - u0]);
+    }
+    for (int u = u0 + threadIdx.x; u < u1; u += nth)
+        store_herm<Num>(x_out + soff, d, rc[u - u0].x, rc[u - u0].y, xs[u - u0]);
+}
+
 template <class Num>
 __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
     using S = typename Num::store_t;
@@ -347,7 +574,7 @@ __global__ void __launch_bounds__(256) to_double_kernel(const void *src_v, doubl
 }
 
 // ------------------------------------------------------------------ launchers
-template <class Num, bool REALJ>
+template <class Num, bool REALJ, bool HERM>
 cudaError_t launch_prop_t(const PropArgs &p, int threads, size_t smem, cudaStream_t stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(p.n_states * p.ncl));
@@ -361,27 +588,32 @@ cudaError_t launch_prop_t(const PropArgs &p, int threads, size_t smem, cudaStrea
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (HERM) return cudaLaunchKernelEx(&cfg, prop_h_kernel<Num, REALJ>, p);
     return cudaLaunchKernelEx(&cfg, prop_kernel<Num, REALJ>, p);
 }
 
 // smem_total: the per-block shared-memory budget; the dynamic limit is that
 // budget minus the kernel's static shared memory.
-template <class Num, bool REALJ>
-cudaError_t prepare_t(size_t smem_total, int ncl) {
+template <typename K>
+cudaError_t prepare_kernel(K kernel, size_t smem_total, int ncl) {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, prop_kernel<Num, REALJ>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
     if (e != cudaSuccess) return e;
     if (fa.sharedSizeBytes > smem_total) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(prop_kernel<Num, REALJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(smem_total - fa.sharedSizeBytes));
     if (e != cudaSuccess) return e;
-    if (ncl > 8)
-        e = cudaFuncSetAttribute(prop_kernel<Num, REALJ>,
-                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (ncl > 8) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
 
-template <class Num, bool REALJ>
+template <class Num, bool REALJ, bool HERM>
+cudaError_t prepare_t(size_t smem_total, int ncl) {
+    if (HERM) return prepare_kernel(prop_h_kernel<Num, REALJ>, smem_total, ncl);
+    return prepare_kernel(prop_kernel<Num, REALJ>, smem_total, ncl);
+}
+
+template <class Num, bool REALJ, bool HERM>
 cudaError_t clusters_t(int threads, size_t smem, int ncl, int n_blocks, int *clusters) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)n_blocks);
@@ -394,25 +626,32 @@ cudaError_t clusters_t(int threads, size_t smem, int ncl, int n_blocks, int *clu
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (HERM) return cudaOccupancyMaxActiveClusters(clusters, prop_h_kernel<Num, REALJ>, &cfg);
     return cudaOccupancyMaxActiveClusters(clusters, prop_kernel<Num, REALJ>, &cfg);
 }
 
-// `variant` bit 0: the jump tables are real.
+// `variant` bit 0: the jump tables are real; bit 1: Hermitian (upper-triangle) kernel.
+#define GRAPE_VARIANT_DISPATCH(FN, ...)                                   \
+    switch (variant & 3) {                                                \
+    case 0: return FN<Num, false, false>(__VA_ARGS__);                    \
+    case 1: return FN<Num, true, false>(__VA_ARGS__);                     \
+    case 2: return FN<Num, false, true>(__VA_ARGS__);                     \
+    default: return FN<Num, true, true>(__VA_ARGS__);                     \
+    }
+
 template <class Num>
 cudaError_t launch_prop(const PropArgs &p, int threads, int variant, size_t smem, cudaStream_t s) {
-    return (variant & 1) ? launch_prop_t<Num, true>(p, threads, smem, s)
-                         : launch_prop_t<Num, false>(p, threads, smem, s);
+    GRAPE_VARIANT_DISPATCH(launch_prop_t, p, threads, smem, s)
 }
 
 template <class Num>
 cudaError_t prepare(int variant, size_t smem, int ncl) {
-    return (variant & 1) ? prepare_t<Num, true>(smem, ncl) : prepare_t<Num, false>(smem, ncl);
+    GRAPE_VARIANT_DISPATCH(prepare_t, smem, ncl)
 }
 
 template <class Num>
 cudaError_t max_clusters(int threads, int variant, size_t smem, int ncl, int n_blocks, int *clusters) {
-    return (variant & 1) ? clusters_t<Num, true>(threads, smem, ncl, n_blocks, clusters)
-                         : clusters_t<Num, false>(threads, smem, ncl, n_blocks, clusters);
+    GRAPE_VARIANT_DISPATCH(clusters_t, threads, smem, ncl, n_blocks, clusters)
 }
 
 template <class Num>

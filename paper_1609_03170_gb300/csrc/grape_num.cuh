@@ -111,6 +111,7 @@ struct NumD {
     }
     static __device__ __forceinline__ val minus_i(val a) { return {a.im, -a.re}; }
     static __device__ __forceinline__ real_t re(val a) { return a.re; }
+    static __device__ __forceinline__ real_t neg_real(real_t a) { return -a; }
     static __device__ __forceinline__ real_t real_mul(real_t a, real_t b) { return a * b; }
     // acc += c * b, c real
     static __device__ __forceinline__ void mac_real(acc &w, real_t c, val b) {
@@ -174,6 +175,7 @@ struct NumF {
         return {a.im, {-a.re.h, -a.re.l}};
     }
     static __device__ __forceinline__ real_t re(val a) { return a.re; }
+    static __device__ __forceinline__ real_t neg_real(real_t a) { return {-a.h, -a.l}; }
     static __device__ __forceinline__ real_t real_mul(real_t a, real_t b) { return ff_mul(a, b); }
     static __device__ __forceinline__ void mac_real(acc &w, real_t c, val b) {
         lacc_fma(w.re, c.h, c.l, b.re.h, b.re.l);

@@ -42,18 +42,32 @@ def rich(**kw):
     return workloads.small(**args)
 
 
-def with_cluster(n):
+def with_env(**kv):
     class _Ctx:
         def __enter__(self):
-            self.old = os.environ.get("GRAPE_CLUSTER")
-            os.environ["GRAPE_CLUSTER"] = str(n)
+            self.old = {k: os.environ.get(k) for k in kv}
+            for k, v in kv.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = str(v)
 
         def __exit__(self, *a):
-            if self.old is None:
-                os.environ.pop("GRAPE_CLUSTER", None)
-            else:
-                os.environ["GRAPE_CLUSTER"] = self.old
+            for k, v in self.old.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
     return _Ctx()
+
+
+def with_cluster(n, hermitian=None):
+    """GRAPE_CLUSTER picks the cluster width at create time; GRAPE_HERMITIAN=0
+    selects the full-matrix kernel instead of the upper-triangle one."""
+    return with_env(GRAPE_CLUSTER=n, GRAPE_HERMITIAN=None if hermitian is None else int(hermitian))
+
+
+KERNELS = [True, False]   # upper-triangle (Hermitian) kernel, full-matrix kernel
 
 
 # --------------------------------------------------------------------------
@@ -83,15 +97,17 @@ def test_gradient_small_matches_dense_oracle(gp, mode, prec):
     assert rel(G, G_ref) < TOL
 
 
+@pytest.mark.parametrize("herm", KERNELS)
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("cluster", [1, 2, 4, 16])
-def test_d20_full_size_all_cluster_widths(gp, cluster, prec):
+def test_d20_full_size_all_cluster_widths(gp, cluster, prec, herm):
     """The 2-level qubit x N=10 resonator problem (d=20, N_t=200, n_RK=4) at
-    full size; cluster 16 splits 400 entries into chunks of 25 with a 42-entry
-    halo, so halos span two neighbours."""
+    full size; cluster 16 splits 400 entries (full kernel) into chunks of 25
+    with a 42-entry halo, so halos span two neighbours, and the 210 upper
+    entries (Hermitian kernel) into 14 per CTA with windows spanning several."""
     w = workloads.qubit_resonator_d20()
     F_ref, G_ref, r_ref, _ = sparse.run_workload(w, threads=2)
-    with with_cluster(cluster):
+    with with_cluster(cluster, herm):
         P = gp.GrapeProblem.from_workload(w, precision=prec)
     assert P.geometry()[0] == cluster
     F, r = P.forward(w.u)
@@ -101,18 +117,33 @@ def test_d20_full_size_all_cluster_widths(gp, cluster, prec):
     assert rel(G, G_ref) < TOL
 
 
+@pytest.mark.parametrize("herm", KERNELS)
 @pytest.mark.parametrize("prec", PRECS)
-def test_cluster_width_does_not_change_bits(gp, prec):
+def test_cluster_width_does_not_change_bits(gp, prec, herm):
     """Every entry is computed by the same arithmetic whatever CTA owns it."""
     w = workloads.transmon_resonator_d120(n_slices=6)
     out = []
     for c in (4, 8, 16):
-        with with_cluster(c):
+        with with_cluster(c, herm):
             P = gp.GrapeProblem.from_workload(w, precision=prec)
         out.append(P.gradient(w.u))
     for F, G in out[1:]:
         assert F == out[0][0]
         assert np.array_equal(G, out[0][1])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_hermitian_and_full_kernels_agree(gp, prec):
+    """The upper-triangle kernel mirrors the lower triangle instead of
+    computing it: both kernels agree to rounding."""
+    w = workloads.transmon_resonator_d120(n_slices=20)
+    out = []
+    for herm in KERNELS:
+        with with_cluster(16, herm):
+            P = gp.GrapeProblem.from_workload(w, precision=prec)
+        out.append((P.forward(w.u)[1], P.gradient(w.u)))
+    (r1, (F1, G1)), (r2, (F2, G2)) = out
+    assert rel(r1, r2) < 1e-12 and abs(F1 - F2) < 1e-12 * abs(F2) and rel(G1, G2) < 1e-12
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -194,8 +225,9 @@ def test_edge_one_level_system(gp, prec):
     assert np.all(G == 0.0)
 
 
+@pytest.mark.parametrize("herm", KERNELS)
 @pytest.mark.parametrize("prec", PRECS)
-def test_ragged_dimension_and_transmon_drive(gp, prec):
+def test_ragged_dimension_and_transmon_drive(gp, prec, herm):
     """d = 3*7 = 21 (odd, d^2 not a multiple of any cluster width) with all
     four control kinds and a transmon-decay jump."""
     w = workloads.small(Q=3, N=7, n_slices=9, n_rk=3, T=0.9, gamma1=0.2, gamma_phi=0.1,
@@ -203,7 +235,7 @@ def test_ragged_dimension_and_transmon_drive(gp, prec):
     m = operators.build(w.phys)
     F_ref, G_ref = dense.gradient_exact(m, w.u, w.rho0, w.sigma, w.T, w.n_rk)
     for c in (1, 8):
-        with with_cluster(c):
+        with with_cluster(c, herm):
             P = gp.GrapeProblem.from_workload(w, precision=prec)
         F, G = P.gradient(w.u)
         assert abs(F - F_ref) < TOL * abs(F_ref)
@@ -230,17 +262,19 @@ def test_per_state_sigma_and_non_hermitian_sigma(gp, prec):
 def test_d120_full_size_against_c_oracle(gp):
     """The full d=120, N_t=2000, n_RK=4 problem the benchmark times: Phi,
     rho(T) and the whole gradient against the plain-C oracle, in both
-    precisions."""
+    precisions and with both propagation kernels."""
     w = workloads.transmon_resonator_d120()
     F_ref, G_ref, r_ref, _ = sparse.run_workload(w, threads=3)
     for prec in PRECS:
-        P = gp.GrapeProblem.from_workload(w, precision=prec)
-        F, r = P.forward(w.u)
-        assert rel(r, r_ref) < TOL
-        F2, G = P.gradient(w.u)
-        assert abs(F - F_ref) < TOL * abs(F_ref)
-        assert rel(G, G_ref) < TOL
-        for rr in r:
-            assert abs(np.trace(rr) - 1) < 1e-12
-            assert np.max(np.abs(rr - rr.conj().T)) < 1e-13
-        P.close()
+        for herm in KERNELS:
+            with with_cluster(None, herm):
+                P = gp.GrapeProblem.from_workload(w, precision=prec)
+            F, r = P.forward(w.u)
+            assert rel(r, r_ref) < TOL
+            F2, G = P.gradient(w.u)
+            assert abs(F - F_ref) < TOL * abs(F_ref)
+            assert rel(G, G_ref) < TOL
+            for rr in r:
+                assert abs(np.trace(rr) - 1) < 1e-12
+                assert np.max(np.abs(rr - rr.conj().T)) < 1e-13
+            P.close()
