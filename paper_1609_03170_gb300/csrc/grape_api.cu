@@ -208,7 +208,7 @@ struct grape_problem {
     size_t d2 = 0;
     int ncl = 1, threads = GRAPE_PROP_THREADS, chunk = 0, halo = 0, win = 0, reach = 0;
     int variant = 0;                 // bit 0 = real jump tables, bit 1 = Hermitian kernel
-    int hb = 0, cu = 0, maxwin = 0, htab_len = 0;   // Hermitian kernel geometry
+    int hb = 0, cu = 0, maxwin = 0, htab_len = 0, rt_rows = 0;   // Hermitian kernel geometry
     int *d_htab = nullptr;
     size_t smem = 0;
     int ckpt_stride = 0;
@@ -389,7 +389,8 @@ grape_status choose_geometry(grape_problem *P, int omax) {
 // CTAs: ownership ranges, compact windows and the table described in
 // grape_internal.h.  Returns the table, the largest window and the entries
 // per CTA.
-std::vector<int> hermitian_table(int d, int ncl, int omax, int hb, int *maxwin, int *cu) {
+std::vector<int> hermitian_table(int d, int ncl, int omax, int hb, int *maxwin, int *cu,
+                                 int *rt_rows) {
     const long long NU = (long long)d * (d + 1) / 2;
     const int c = (int)((NU + ncl - 1) / ncl);
     auto row_start = [d](long long i) { return i * d - i * (i - 1) / 2; };
@@ -404,12 +405,14 @@ std::vector<int> hermitian_table(int d, int ncl, int omax, int hb, int *maxwin, 
     auto cs = [hb](int r) { return r > hb ? r - hb : 0; };
     std::vector<int> head(4 * ncl), starts(ncl + 1), lists;
     std::vector<int> wr0(ncl), wr1(ncl);
-    int mw = 0;
+    int mw = 0, rt = 1;
     for (int k = 0; k < ncl; ++k) {
         const long long u0 = std::min<long long>(NU, (long long)k * c);
         const long long u1 = std::min<long long>(NU, u0 + c);
         int r0 = 0, nrows = 0;
         if (u1 > u0) {
+            // rows written by the CTA: its own and, for mirrors, hb below
+            rt = std::max(rt, std::min(d - 1, row_of(u1 - 1) + hb) - row_of(u0) + 1);
             r0 = std::max(0, row_of(u0) - omax);
             const int r1 = std::min(d - 1, row_of(u1 - 1) + omax);
             nrows = r1 - r0 + 1;
@@ -444,6 +447,7 @@ std::vector<int> hermitian_table(int d, int ncl, int omax, int hb, int *maxwin, 
     tab.insert(tab.end(), kl.begin(), kl.end());
     *maxwin = mw;
     *cu = c;
+    *rt_rows = rt;
     return tab;
 }
 
@@ -470,11 +474,14 @@ grape_status choose_geometry_h(grape_problem *P, int omax, int hb) {
     for (int c = start / 2; c >= 1; c /= 2) widths[nw++] = c;
     for (int wi = 0; wi < nw; ++wi) {
         const int ncl = widths[wi];
-        int maxwin = 0, cu = 0;
-        const std::vector<int> tab = hermitian_table(d, ncl, omax, hb, &maxwin, &cu);
+        int maxwin = 0, cu = 0, rt_rows = 0;
+        const std::vector<int> tab = hermitian_table(d, ncl, omax, hb, &maxwin, &cu, &rt_rows);
+        if (maxwin >= 32768) continue;   // neighbour addresses are 16-bit
         const size_t smem = ((size_t)2 * maxwin + 2 * (size_t)cu + 2 * (size_t)nb * d +
                              2 * (size_t)nt * d) * sizeof(double2) +
-                            (size_t)cu * sizeof(int2) + 12 * sizeof(double) + tab.size() * sizeof(int);
+                            (size_t)cu * sizeof(int2) + 12 * sizeof(double) + tab.size() * sizeof(int) +
+                            (size_t)rt_rows * (ncl + 1) * sizeof(uint32_t) +
+                            (size_t)cu * (2 * nb + nt + 1) * sizeof(short);
         if (smem + 1024 > (size_t)max_smem) continue;
         int clusters = 0;
         e = P->prec == GRAPE_PREC_FP64
@@ -493,6 +500,7 @@ grape_status choose_geometry_h(grape_problem *P, int omax, int hb) {
         P->maxwin = maxwin;
         P->hb = hb;
         P->htab_len = (int)tab.size();
+        P->rt_rows = rt_rows;
         P->smem = smem;
         P->threads = GRAPE_PROP_THREADS;
         P->chunk = cu;
@@ -539,6 +547,7 @@ PropArgs base_args(const grape_problem *P, int dir, const double *u) {
     a.hb = P->hb;
     a.cu = P->cu;
     a.maxwin = P->maxwin;
+    a.rt_rows = P->rt_rows;
     rk_coefficients(P->T / P->n_slices / P->n_rk, dir == 1, &a);
     return a;
 }

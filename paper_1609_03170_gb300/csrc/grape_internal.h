@@ -63,6 +63,7 @@ struct PropArgs {
     int hb;                             // stored half-band below the diagonal
     int cu;                             // upper-triangle entries per CTA
     int maxwin;                         // largest window (entries) of the cluster
+    int rt_rows;                        // rows of the largest push table
 };
 
 // Layout of the Hermitian kernel's table (ints), for a cluster of ncl CTAs:

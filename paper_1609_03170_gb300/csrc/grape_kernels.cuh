@@ -290,39 +290,39 @@ __device__ __forceinline__ typename Num::store_t conj_store(typename Num::val v)
     return Num::store(v);
 }
 
-// W = Op(z) at upper entry (i, j), reading the compact window
+__device__ __forceinline__ void st_cluster_addr(uint32_t addr, double2 v) { st_remote(addr, v); }
+__device__ __forceinline__ void st_cluster_addr(uint32_t addr, float4 v) { st_remote(addr, v); }
+
+// W = Op(z) at an owned upper entry (i, j) from its precomputed neighbour
+// window addresses nb_ad: [2 b] = (i + o_b, j), [2 b + 1] = (i, j + o_b),
+// [2 nb + q] = (i + oL_q, j + oR_q); -1 where the neighbour lies outside the
+// matrix (its coefficient is zero there).
 template <class Num, bool REALJ>
 __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::store_t *cur,
-                                                           const int *ofs, int wr0, int i, int j,
-                                                           int d, int hb, const PropTables &t,
+                                                           const short *nb_ad, int i, int j, int d,
+                                                           const PropTables &t,
                                                            const typename Num::store_t *A,
                                                            const typename Num::store_t *vL,
                                                            const typename Num::store_t *vR) {
-    const int own = ofs[i - wr0] + (j - cs_of(i, hb));
     typename Num::acc w = Num::acc_zero();
 #pragma unroll 1
     for (int b = 0; b < t.nb; ++b) {
-        const int o = t.off[b];
-        const int r = i + o;
-        if (r >= 0 && r < d)
-            Num::mac(w, Num::load(A[b * d + i]), Num::load(cur[ofs[r - wr0] + (j - cs_of(r, hb))]));
-        const int c = j + o;
-        if (c >= 0 && c < d)
-            Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[own + o]));
+        const int aL = nb_ad[2 * b], aR = nb_ad[2 * b + 1];
+        if (aL >= 0) Num::mac(w, Num::load(A[b * d + i]), Num::load(cur[aL]));
+        if (aR >= 0) Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[aR]));
     }
     w = Num::acc_minus_i(w);
 #pragma unroll 1
     for (int q = 0; q < t.nt; ++q) {
-        const int r = i + t.joL[q], c = j + t.joR[q];
-        if (r < 0 || r >= d || c < 0 || c >= d) continue;
-        const typename Num::store_t zv = cur[ofs[r - wr0] + (c - cs_of(r, hb))];
+        const int aJ = nb_ad[2 * t.nb + q];
+        if (aJ < 0) continue;
         if (REALJ) {
             const typename Num::real_t cf =
                 Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j])));
-            Num::mac_real(w, cf, Num::load(zv));
+            Num::mac_real(w, cf, Num::load(cur[aJ]));
         } else {
             Num::mac(w, Num::mul_conjb(Num::load(vL[q * d + i]), Num::load(vR[q * d + j])),
-                     Num::load(zv));
+                     Num::load(cur[aJ]));
         }
     }
     return Num::done(w);
@@ -336,8 +336,20 @@ __device__ __forceinline__ void store_herm(typename Num::store_t *dst, int d, in
     if (j != i) dst[(size_t)j * d + i] = conj_store<Num>(Num::load(v));
 }
 
+// push value v of entry (r, c) to every window holding row r: rowtab holds,
+// per row, the target count and each target's distributed-shared-memory
+// address of (r, 0) in buf0 (buffer offset boff selects buf1)
+template <class S>
+__device__ __forceinline__ void hpush_pre(const uint32_t *rowtab, int rstride, int rrow, int c,
+                                          uint32_t boff, S v) {
+    const uint32_t *e = rowtab + rrow * rstride;
+    const int n = (int)e[0];
+    for (int t = 1; t <= n; ++t) st_cluster_addr(e[t] + boff + (uint32_t)c * (uint32_t)sizeof(S), v);
+}
+
 // Shared memory: buf0, buf1 [maxwin]; xs, as [cu]; bands [2][nb][d];
-// vL, vR [nt][d]; rc [cu] (int2); 12 RK coefficients; htab copy (ints).
+// vL, vR [nt][d]; rc [cu] (int2); 12 RK coefficients; htab copy (ints);
+// row push table [rt_rows][ncl + 1] (u32); neighbour addresses [cu][ns + 1] (i16).
 template <class Num, bool REALJ>
 __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const PropArgs p) {
     using S = typename Num::store_t;
@@ -358,6 +370,11 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     R *ca = cg + 4;
     R *cb = cg + 8;
     int *tab = reinterpret_cast<int *>(cg + 12);
+    const int rstride = p.ncl + 1;
+    uint32_t *rowtab = reinterpret_cast<uint32_t *>(tab + p.htab_len);
+    short *nbad = reinterpret_cast<short *>(rowtab + p.rt_rows * rstride);
+    const int ns = 2 * p.tab.nb + p.tab.nt;     // neighbour slots; slot ns = own address
+    const int nstride = ns + 1;
     const S *x_in = static_cast<const S *>(p.x_in);
     S *x_out = static_cast<S *>(p.x_out);
     S *stage_store = static_cast<S *>(p.stage_store);
@@ -366,6 +383,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     const int state = blockIdx.x / p.ncl;
     const size_t soff = (size_t)state * d2;
     const int nth = blockDim.x;
+    const int hb = p.hb;
 
     for (int i = threadIdx.x; i < p.htab_len; i += nth) tab[i] = __ldg(&p.htab[i]);
     const V vzero = Num::zero();
@@ -388,9 +406,9 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     const int u0 = tab[GRAPE_HTAB_CTA(rank) + 0], u1 = tab[GRAPE_HTAB_CTA(rank) + 1];
     const int wr0 = tab[GRAPE_HTAB_CTA(rank) + 2];
     const int *ofs = tab + tab[GRAPE_HTAB_LISTS(p.ncl) + rank];
-    const HWin hw{tab, p.ncl, d, p.hb};
-    // (row, column) of the owned upper entries: row-major offset of row i is
-    // i d - i (i - 1) / 2
+    const int *kfl = tab + tab[GRAPE_HTAB_LISTS(p.ncl) + p.ncl];   // kfirst[d], klast[d]
+    // (row, column) of the owned upper entries (row-major offset of row i is
+    // i d - i (i - 1) / 2) and their neighbours' window addresses
     for (int u = u0 + threadIdx.x; u < u1; u += nth) {
         const double b2 = 2.0 * d + 1.0;
         int i = (int)floor(0.5 * (b2 - sqrt(b2 * b2 - 8.0 * (double)u)));
@@ -399,19 +417,64 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
         while (i + 1 < d && (long long)(i + 1) * d - (long long)(i + 1) * i / 2 <= u) ++i;
         const int j = i + (int)(u - ((long long)i * d - (long long)i * (i - 1) / 2));
         rc[u - u0] = make_int2(i, j);
+        short *na = nbad + (size_t)(u - u0) * nstride;
+        const int own = ofs[i - wr0] + (j - cs_of(i, hb));
+        na[ns] = (short)own;
+        for (int b = 0; b < p.tab.nb; ++b) {
+            const int o = p.tab.off[b], r = i + o, c = j + o;
+            na[2 * b] = (short)((r >= 0 && r < d) ? ofs[r - wr0] + (j - cs_of(r, hb)) : -1);
+            na[2 * b + 1] = (short)((c >= 0 && c < d) ? own + o : -1);
+        }
+        for (int q = 0; q < p.tab.nt; ++q) {
+            const int r = i + p.tab.joL[q], c = j + p.tab.joR[q];
+            na[2 * p.tab.nb + q] =
+                (short)((r >= 0 && r < d && c >= 0 && c < d) ? ofs[r - wr0] + (c - cs_of(r, hb)) : -1);
+        }
     }
-    cluster_sync_all();   // every CTA runs, windows zeroed, tables loaded
+    // push targets of the rows this CTA writes: its own rows and, for the
+    // mirrors, up to hb rows below
+    int rfirst = 0, rlast = -1;
+    if (u1 > u0) {
+        // rows of the first and last owned entries (same formula as above)
+        auto row_of = [&](int u) {
+            const double b2 = 2.0 * d + 1.0;
+            int i = (int)floor(0.5 * (b2 - sqrt(b2 * b2 - 8.0 * (double)u)));
+            i = max(0, min(d - 1, i));
+            while (i > 0 && (long long)i * d - (long long)i * (i - 1) / 2 > u) --i;
+            while (i + 1 < d && (long long)(i + 1) * d - (long long)(i + 1) * i / 2 <= u) ++i;
+            return i;
+        };
+        rfirst = row_of(u0);
+        rlast = min(d - 1, row_of(u1 - 1) + hb);
+    }
+    const uint32_t buf0_sa = smem_u32(buf0);
+    for (int r = rfirst + threadIdx.x; r <= rlast; r += nth) {
+        uint32_t *e = rowtab + (r - rfirst) * rstride;
+        const int kf = kfl[r], kl = kfl[d + r];
+        int n = 0;
+        for (int k = kf; k <= kl; ++k) {
+            const int wk = tab[GRAPE_HTAB_CTA(k) + 2];
+            const int *ofk = tab + tab[GRAPE_HTAB_LISTS(p.ncl) + k];
+            const int base = ofk[r - wk] - cs_of(r, hb);       // entry index of (r, 0), may be < 0
+            e[1 + n++] = map_to_rank(buf0_sa, (uint32_t)k) + (uint32_t)(base * (int)sizeof(S));
+        }
+        e[0] = (uint32_t)n;
+    }
+    cluster_sync_all();   // every CTA runs, windows zeroed, tables built
+    const uint32_t boff1 = (uint32_t)(p.maxwin * (int)sizeof(S));
 
     for (int u = u0 + threadIdx.x; u < u1; u += nth) {
         const int2 ij = rc[u - u0];
         const V x = Num::load(x_in[soff + (size_t)ij.x * d + ij.y]);
         xs[u - u0] = Num::store(x);
         const V z = Num::scale(cg[0], x);
-        hpush(buf0, hw, rank, ij.x, ij.y, Num::store(z));
-        if (ij.y > ij.x && ij.y - ij.x <= p.hb) hpush(buf0, hw, rank, ij.y, ij.x, conj_store<Num>(z));
+        hpush_pre(rowtab, rstride, ij.x - rfirst, ij.y, 0u, Num::store(z));
+        if (ij.y > ij.x && ij.y - ij.x <= hb)
+            hpush_pre(rowtab, rstride, ij.y - rfirst, ij.x, 0u, conj_store<Num>(z));
     }
     cluster_sync_all();
 
+    const bool unit_g = (p.g[1] == 1.0 && p.g[2] == 1.0 && p.g[3] == 1.0);   // forward RK4
     int tb = 0;
     for (long long it = 0; it < nsub; ++it) {
         const long long n = p.reverse ? p.sub_end - 1 - it : p.sub_begin + it;
@@ -426,7 +489,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
 #pragma unroll 1
         for (int s = 0; s < 4; ++s) {
             const S *cur = (s & 1) ? buf1 : buf0;
-            S *nxt = (s & 1) ? buf0 : buf1;
+            const uint32_t boff = (s & 1) ? 0u : boff1;          // next buffer
             S *st = nullptr;
             if (stage_store)
                 st = stage_store + ((size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states) * d2 + soff;
@@ -435,21 +498,22 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
             for (int u = u0 + threadIdx.x; u < u1; u += nth) {
                 const int li = u - u0;
                 const int2 ij = rc[li];
-                const V w = lindblad_h_at<Num, REALJ>(cur, ofs, wr0, ij.x, ij.y, d, p.hb, p.tab, A, vL, vR);
-                if (st) store_herm<Num>(st, d, ij.x, ij.y, cur[ofs[ij.x - wr0] + (ij.y - cs_of(ij.x, p.hb))]);
+                const short *na = nbad + (size_t)li * nstride;
+                const V w = lindblad_h_at<Num, REALJ>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR);
+                if (st) store_herm<Num>(st, d, ij.x, ij.y, cur[na[ns]]);   // the stage input itself
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
                 V z;
                 if (s < 3) {
                     as[li] = Num::store(acc);
-                    z = Num::lin2(cg[s + 1], x, cb[s + 1], w);
+                    z = unit_g ? Num::axpy(cb[s + 1], w, x) : Num::lin2(cg[s + 1], x, cb[s + 1], w);
                 } else {
                     xs[li] = Num::store(acc);
                     z = Num::scale(cg[0], acc);
                 }
-                hpush(nxt, hw, rank, ij.x, ij.y, Num::store(z));
-                if (ij.y > ij.x && ij.y - ij.x <= p.hb)
-                    hpush(nxt, hw, rank, ij.y, ij.x, conj_store<Num>(z));
+                hpush_pre(rowtab, rstride, ij.x - rfirst, ij.y, boff, Num::store(z));
+                if (ij.y > ij.x && ij.y - ij.x <= hb)
+                    hpush_pre(rowtab, rstride, ij.y - rfirst, ij.x, boff, conj_store<Num>(z));
             }
             if (s == 3 && it + 1 < nsub) {
                 const long long nn = p.reverse ? n - 1 : n + 1;
