@@ -146,7 +146,7 @@ def kernel_source_sha():
 def profiled_traffic(kernel_src_sha):
     """DRAM bytes per launch of the forward propagation kernel from the
     committed ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "prop_kernel_transmon_resonator_d120.md")
+    path = os.path.join(ROOT, "profiles", "prop_h_kernel_transmon_resonator_d120.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -300,10 +300,14 @@ def main():
     adj_ms, adj_n = phases["adjoint"]
     tr_ms, tr_n = phases["trace"]
     dom = "forward" if fwd_ms >= adj_ms else "adjoint"
-    dom_ms = (fwd_ms / max(fwd_n, 1)) if dom == "forward" else (adj_ms / max(adj_n, 1))
-    achieved = counts["flops_" + dom] / (dom_ms * 1e-3) / 1e12
+    dom_total_ms, dom_n = phases[dom]
+    dom_ms = dom_total_ms / max(dom_n, 1)                      # average launch duration
+    flops_per_launch = counts["flops_" + dom] * args.steps / max(dom_n, 1)
+    achieved = flops_per_launch / (dom_ms * 1e-3) / 1e12
     sha = kernel_source_sha()
     traffic = profiled_traffic(sha)
+    if traffic is not None:
+        traffic *= flops_per_launch / counts["flops_" + dom]   # profile is per full sweep
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -338,7 +342,8 @@ def main():
                      "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
                      "traffic": traffic,
-                     "flops_per_launch": counts["flops_" + dom],
+                     "flops_per_launch": flops_per_launch,
+                     "launches_per_step": dom_n / args.steps,
                      "ms_per_launch": dom_ms,
                      "peak_source": peak_source},
         "hbm": {"bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,

@@ -156,7 +156,8 @@ grape_status grape_phase_times(grape_problem_t problem, double ms[4], int32_t la
 grape_status grape_gradient_static(grape_problem_t problem, const double *u, double *F,
                                    double *grad, void *stream);
 
-/* Kernel launches one grape_gradient call makes (for launch accounting). */
+/* Kernel launches one grape_gradient call makes (for launch accounting);
+ * -1 before the first gradient call has fixed the segment plan. */
 int32_t grape_gradient_launches(grape_problem_t problem);
 
 /* Thread-local message of the last failed call on this thread. */

@@ -222,6 +222,9 @@ struct grape_problem {
     double2 *d_out = nullptr;        // complex128 staging of rho(T)
     double *d_u = nullptr, *d_F = nullptr, *d_G = nullptr;
     size_t bytes = 0;
+    cudaStream_t s2 = nullptr;       // trace kernels overlap the adjoint sweep here
+    static constexpr int kMaxChunks = 16;
+    cudaEvent_t ev[kMaxChunks + 2] = {};
     bool profiling = false;
     struct Mark { int phase; cudaEvent_t a, b; };
     std::vector<Mark> marks;
@@ -250,6 +253,9 @@ struct grape_problem {
         return p;
     }
     ~grape_problem() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        if (s2) cudaStreamDestroy(s2);
         for (auto &m : marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
         for (auto e : event_pool) cudaEventDestroy(e);
         for (void *p : allocs) cudaFree(p);
@@ -561,6 +567,28 @@ size_t seg_bytes(const grape_problem *P, long long seg) {
     return total;
 }
 
+// The adjoint sweep of a segment runs in chunks of slices; the trace kernel
+// of each finished chunk runs on the problem's second stream while the next
+// chunk propagates, on the SMs the propagation leaves idle.
+int adjoint_chunks(const grape_problem *P, long long j0, long long j1) {
+    int n = 8;
+    if (const char *env = std::getenv("GRAPE_ADJ_CHUNKS")) n = std::atoi(env);
+    n = std::max(1, std::min(n, grape_problem::kMaxChunks));
+    return (int)std::min<long long>(n, j1 - j0);
+}
+
+int gradient_launch_count(const grape_problem *P) {
+    if (P->nseg <= 0) return -1;
+    int n = 2;                                    // forward sweep, cost
+    for (int gi = 0; gi < P->nseg; ++gi) {
+        const long long j0 = (long long)gi * P->seg;
+        const long long j1 = std::min<long long>(P->n_slices, j0 + P->seg);
+        const int nch = adjoint_chunks(P, j0, j1);
+        n += (P->nseg > 1 ? 1 : 0) + nch + (P->R > 0 ? nch : 0);
+    }
+    return n;
+}
+
 grape_status plan_gradient(grape_problem *P) {
     if (P->nseg > 0) return GRAPE_OK;
     size_t free_b = 0, total_b = 0;
@@ -823,6 +851,15 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
     P->d_F = static_cast<double *>(P->alloc(sizeof(double)));
     P->d_G = static_cast<double *>(P->alloc((size_t)P->n_slices * std::max(P->R, 1) * sizeof(double)));
     if (!P->d_x || !P->d_mu || !P->d_out || !P->d_u || !P->d_F || !P->d_G) return bail(fail(GRAPE_ENOMEM, "cudaMalloc failed"));
+    if (cudaStreamCreateWithFlags(&P->s2, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(GRAPE_ECUDA, "cudaStreamCreate failed"));
+    }
+    for (auto &e : P->ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(GRAPE_ECUDA, "cudaEventCreate failed"));
+        }
     *out = P;
     return GRAPE_OK;
 }
@@ -877,8 +914,7 @@ grape_status grape_phase_times(grape_problem_t P, double ms[4], int32_t launches
 
 int32_t grape_gradient_launches(grape_problem_t P) {
     if (!P) return -1;
-    if (P->nseg <= 1) return 4;
-    return 2 + 3 * P->nseg;
+    return gradient_launch_count(P);
 }
 
 grape_status grape_forward(grape_problem_t P, const double *u, double *F, double *rhoT,
@@ -968,31 +1004,46 @@ grape_status grape_gradient(grape_problem_t P, const double *u, double *F, doubl
             else { r.bound_store = P->d_Y; r.bound_step = P->n_rk; }
             if ((st = launch_prop(P, r, s)) != GRAPE_OK) return st;
         }
-        PropArgs b = base_args(P, 1, ud);
-        b.sub_begin = j0 * P->n_rk;
-        b.sub_end = j1 * P->n_rk;
-        b.reverse = 1;
-        b.x_in = P->d_mu;
-        b.x_out = P->d_mu;
-        if (exact) b.stage_store = P->d_K;
-        else { b.bound_store = P->d_K; b.bound_step = P->n_rk; }
-        if ((st = launch_prop(P, b, s)) != GRAPE_OK) return st;
-        TraceArgs t = P->trace;
-        t.n_rows = (int)(j1 - j0);
-        t.G = Gout + (size_t)j0 * P->R;
-        if (exact) {
-            t.K = P->d_K;
-            t.Y = P->d_Y;
-            t.npairs = (long long)P->n_rk * 4 * P->ns;
-            t.weight = 1.0;
-        } else {
-            t.K = P->d_K + mat;   // lambda_{j+1}, rho_{j+1} pair with row j
-            t.Y = P->d_Y + mat;
-            t.npairs = P->ns;
-            t.weight = dt;
+        // adjoint sweep in chunks (last slices first); the trace of each
+        // finished chunk runs on s2, overlapping the next chunk
+        const int nch = adjoint_chunks(P, j0, j1);
+        for (int ci = nch - 1; ci >= 0; --ci) {
+            const long long cA = j0 + (j1 - j0) * ci / nch;
+            const long long cB = j0 + (j1 - j0) * (ci + 1) / nch;
+            const size_t kofs = exact ? (size_t)(cA - j0) * P->n_rk * 4 * mat : (size_t)(cA - j0) * mat;
+            PropArgs b = base_args(P, 1, ud);
+            b.sub_begin = cA * P->n_rk;
+            b.sub_end = cB * P->n_rk;
+            b.reverse = 1;
+            b.x_in = P->d_mu;
+            b.x_out = P->d_mu;
+            if (exact) b.stage_store = P->d_K + kofs;
+            else { b.bound_store = P->d_K + kofs; b.bound_step = P->n_rk; }
+            if ((st = launch_prop(P, b, s)) != GRAPE_OK) return st;
+            if (P->R == 0) continue;
+            GRAPE_CUDA_TRY(cudaEventRecord(P->ev[ci], s));
+            GRAPE_CUDA_TRY(cudaStreamWaitEvent(P->s2, P->ev[ci], 0));
+            TraceArgs t = P->trace;
+            t.n_rows = (int)(cB - cA);
+            t.G = Gout + (size_t)cA * P->R;
+            if (exact) {
+                t.K = P->d_K + kofs;
+                t.Y = P->d_Y + kofs;
+                t.npairs = (long long)P->n_rk * 4 * P->ns;
+                t.weight = 1.0;
+            } else {
+                t.K = P->d_K + kofs + mat;   // lambda_{j+1}, rho_{j+1} pair with row j
+                t.Y = P->d_Y + kofs + mat;
+                t.npairs = P->ns;
+                t.weight = dt;
+            }
+            if ((st = timed(P, PH_TRACE, P->s2, [&] { return k_trace(P, t, P->s2); })) != GRAPE_OK)
+                return st;
         }
-        if (P->R > 0 && (st = timed(P, PH_TRACE, s, [&] { return k_trace(P, t, s); })) != GRAPE_OK)
-            return st;
+        if (P->R > 0) {   // the segment's stage storage is reused next: join s2 back into s
+            GRAPE_CUDA_TRY(cudaEventRecord(P->ev[grape_problem::kMaxChunks], P->s2));
+            GRAPE_CUDA_TRY(cudaStreamWaitEvent(s, P->ev[grape_problem::kMaxChunks], 0));
+        }
     }
     bool sync = false;
     if (!f_dev) {
