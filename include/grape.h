@@ -156,6 +156,31 @@ grape_status grape_phase_times(grape_problem_t problem, double ms[4], int32_t la
 grape_status grape_gradient_static(grape_problem_t problem, const double *u, double *F,
                                    double *grad, void *stream);
 
+/* ---- Batching: many problems of different sizes in one graph launch ----
+ * (the batched form of the hot path; the paper evaluates one problem at a
+ * time).  The problems are spread over n_lanes concurrent streams, longest
+ * first to the least loaded lane; each lane owns stage storage sized for its
+ * largest problem (with checkpoint segments that keep every lane within an
+ * equal share of 60% of the free device memory) and runs its problems one
+ * after another.  The first grape_batch_gradient call captures the whole
+ * batch into a CUDA graph; later calls with the same pointers and stream
+ * replay it, other pointers re-capture.  Results equal per-problem
+ * grape_gradient calls bit for bit.  The problems must outlive the batch and
+ * must not be used concurrently with it. */
+typedef struct grape_batch *grape_batch_t;
+
+/* n_lanes <= 0 picks 24 (capped at n).  Errors: GRAPE_EINVAL, GRAPE_ENOMEM. */
+grape_status grape_batch_create(grape_problem_t *problems, int32_t n, int32_t n_lanes,
+                                grape_batch_t *out);
+grape_status grape_batch_destroy(grape_batch_t batch);
+/* u[i]: problem i's controls, grad[i]: its gradient, F: n doubles - all
+ * device memory.  Enqueues the work on `stream` and returns. */
+grape_status grape_batch_gradient(grape_batch_t batch, const double *const *u, double *F,
+                                  double *const *grad, void *stream);
+/* Lanes, scratch bytes and kernel launches per grape_batch_gradient. */
+grape_status grape_batch_info(grape_batch_t batch, int32_t *n_lanes, size_t *scratch_bytes,
+                              int32_t *launches);
+
 /* Kernel launches one grape_gradient call makes (for launch accounting);
  * -1 before the first gradient call has fixed the segment plan. */
 int32_t grape_gradient_launches(grape_problem_t problem);

@@ -10,9 +10,9 @@ from . import _lib
 from ._lib import (GRAPE_GRAD_EXACT, GRAPE_GRAD_FIRST_ORDER, GRAPE_PREC_DF64, GRAPE_PREC_FP64,
                    GrapeError, grape_forward,
                    grape_gradient, grape_problem_create, grape_problem_destroy)
-from .problem import BandModel, BandOp, GrapeProblem, band_model
+from .problem import BandModel, BandOp, GrapeBatch, GrapeProblem, band_model
 
 __all__ = ["GRAPE_GRAD_EXACT", "GRAPE_GRAD_FIRST_ORDER", "GRAPE_PREC_DF64", "GRAPE_PREC_FP64",
-           "GrapeError", "GrapeProblem",
+           "GrapeError", "GrapeProblem", "GrapeBatch",
            "BandModel", "BandOp", "band_model", "grape_forward", "grape_gradient",
            "grape_problem_create", "grape_problem_destroy"]

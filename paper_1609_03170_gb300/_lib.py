@@ -48,6 +48,7 @@ _lib = None
 EXPORTS = ["grape_problem_create", "grape_problem_destroy", "grape_forward", "grape_gradient",
            "grape_problem_memory", "grape_problem_geometry", "grape_set_profiling",
            "grape_phase_times", "grape_gradient_launches", "grape_gradient_static",
+           "grape_batch_create", "grape_batch_destroy", "grape_batch_gradient", "grape_batch_info",
            "grape_last_error", "grape_version"]
 
 
@@ -74,6 +75,14 @@ def load(build_if_missing: bool = True):
     lib.grape_forward.restype = c_int32
     lib.grape_gradient.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.grape_gradient.restype = c_int32
+    lib.grape_batch_create.argtypes = [P(c_void_p), c_int32, c_int32, P(c_void_p)]
+    lib.grape_batch_create.restype = c_int32
+    lib.grape_batch_destroy.argtypes = [c_void_p]
+    lib.grape_batch_destroy.restype = c_int32
+    lib.grape_batch_gradient.argtypes = [c_void_p, P(c_void_p), c_void_p, P(c_void_p), c_void_p]
+    lib.grape_batch_gradient.restype = c_int32
+    lib.grape_batch_info.argtypes = [c_void_p, P(c_int32), P(c_size_t), P(c_int32)]
+    lib.grape_batch_info.restype = c_int32
     lib.grape_gradient_static.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.grape_gradient_static.restype = c_int32
     lib.grape_problem_memory.argtypes = [c_void_p, P(c_size_t)]
@@ -125,6 +134,33 @@ def grape_gradient_static(h, u_ptr: int, F_ptr: int, grad_ptr: int, stream_ptr: 
     array (no device allocation); u, F and grad must be device pointers."""
     check(load().grape_gradient_static(h, u_ptr or None, F_ptr or None, grad_ptr or None,
                                        stream_ptr or None), "grape_gradient_static")
+
+
+def grape_batch_create(handles, n_lanes: int = 0):
+    arr = (c_void_p * len(handles))(*[h.value if isinstance(h, c_void_p) else h for h in handles])
+    b = c_void_p()
+    check(load().grape_batch_create(arr, len(handles), int(n_lanes), ctypes.byref(b)),
+          "grape_batch_create")
+    return b
+
+
+def grape_batch_destroy(b) -> None:
+    check(load().grape_batch_destroy(b), "grape_batch_destroy")
+
+
+def grape_batch_gradient(b, u_ptrs, F_ptr: int, grad_ptrs, stream_ptr: int) -> None:
+    n = len(u_ptrs)
+    ua = (c_void_p * n)(*u_ptrs)
+    ga = (c_void_p * n)(*grad_ptrs)
+    check(load().grape_batch_gradient(b, ua, F_ptr or None, ga, stream_ptr or None),
+          "grape_batch_gradient")
+
+
+def grape_batch_info(b):
+    nl, by, la = c_int32(), c_size_t(), c_int32()
+    check(load().grape_batch_info(b, ctypes.byref(nl), ctypes.byref(by), ctypes.byref(la)),
+          "grape_batch_info")
+    return int(nl.value), int(by.value), int(la.value)
 
 
 def grape_problem_memory(h) -> int:

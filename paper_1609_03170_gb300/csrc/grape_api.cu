@@ -567,6 +567,31 @@ size_t seg_bytes(const grape_problem *P, long long seg) {
     return total;
 }
 
+// Device buffers one gradient evaluation needs beyond its inputs and outputs.
+struct GradScratch {
+    double2 *Y = nullptr, *K = nullptr, *ckpt = nullptr, *x = nullptr, *mu = nullptr;
+    int seg = 0, nseg = 0;
+    cudaStream_t s2 = nullptr;   // trace stream; null: traces run on the main stream
+    cudaEvent_t *ev = nullptr;   // kMaxChunks + 1 events when s2 is set
+};
+
+// stage storage of one segment (Y and K) and the checkpoints, in bytes
+size_t stage_bytes(const grape_problem *P, long long seg) {
+    const size_t mat = P->d2 * sizeof(double2) * P->ns;
+    return (P->mode == GRAPE_GRAD_EXACT) ? (size_t)seg * P->n_rk * 4 * mat : (size_t)(seg + 1) * mat;
+}
+size_t ckpt_bytes(const grape_problem *P, long long seg) {
+    const size_t mat = P->d2 * sizeof(double2) * P->ns;
+    return seg < P->n_slices ? (size_t)((P->n_slices + seg - 1) / seg + 1) * mat : 0;
+}
+
+// largest segment (halving from the whole problem) whose storage fits the budget
+long long seg_for_budget(const grape_problem *P, size_t budget) {
+    long long seg = P->n_slices;
+    while (seg > 1 && seg_bytes(P, seg) > budget) seg = (seg + 1) / 2;
+    return seg;
+}
+
 // The adjoint sweep of a segment runs in chunks of slices; the trace kernel
 // of each finished chunk runs on the problem's second stream while the next
 // chunk propagates, on the SMs the propagation leaves idle.
@@ -577,14 +602,14 @@ int adjoint_chunks(const grape_problem *P, long long j0, long long j1) {
     return (int)std::min<long long>(n, j1 - j0);
 }
 
-int gradient_launch_count(const grape_problem *P) {
-    if (P->nseg <= 0) return -1;
+int gradient_launch_count(const grape_problem *P, int seg, int nseg) {
+    if (nseg <= 0) return -1;
     int n = 2;                                    // forward sweep, cost
-    for (int gi = 0; gi < P->nseg; ++gi) {
-        const long long j0 = (long long)gi * P->seg;
-        const long long j1 = std::min<long long>(P->n_slices, j0 + P->seg);
+    for (int gi = 0; gi < nseg; ++gi) {
+        const long long j0 = (long long)gi * seg;
+        const long long j1 = std::min<long long>(P->n_slices, j0 + seg);
         const int nch = adjoint_chunks(P, j0, j1);
-        n += (P->nseg > 1 ? 1 : 0) + nch + (P->R > 0 ? nch : 0);
+        n += (nseg > 1 ? 1 : 0) + nch + (P->R > 0 ? nch : 0);
     }
     return n;
 }
@@ -664,6 +689,98 @@ grape_status stage_inputs(grape_problem *P, const double *u, const double **u_de
 }
 
 }  // namespace
+
+// One gradient evaluation on stream s with device pointers only: forward
+// sweep (stage storage or checkpoints), cost, then per segment (last first)
+// the recomputed forward stage inputs, the adjoint sweep in chunks and the
+// trace kernels of the finished chunks.
+grape_status run_gradient(grape_problem *P, const double *ud, double *Fd, double *Gd,
+                          cudaStream_t s, const GradScratch &S) {
+    grape_status st;
+    const bool exact = (P->mode == GRAPE_GRAD_EXACT);
+    const long long nsub = (long long)P->n_slices * P->n_rk;
+    const double dt = P->T / P->n_slices;
+    const size_t mat = P->d2 * P->ns;
+
+    // forward sweep: stage storage directly (one segment) or checkpoints
+    PropArgs f = base_args(P, 0, ud);
+    f.sub_begin = 0;
+    f.sub_end = nsub;
+    f.x_in = P->d_rho0;
+    f.x_out = S.x;
+    if (S.nseg == 1) {
+        if (exact) f.stage_store = S.Y;
+        else { f.bound_store = S.Y; f.bound_step = P->n_rk; }
+    } else {
+        f.bound_store = S.ckpt;
+        f.bound_step = (long long)S.seg * P->n_rk;
+    }
+    if ((st = launch_prop(P, f, s)) != GRAPE_OK) return st;
+    if ((st = timed(P, PH_COST, s, [&] {
+             return k_cost(P, S.x, Fd, s);
+         })) != GRAPE_OK)
+        return st;
+    GRAPE_CUDA_TRY(cudaMemcpyAsync(S.mu, P->d_sigma, mat * sizeof(double2),
+                                   cudaMemcpyDeviceToDevice, s));
+    for (int gi = S.nseg - 1; gi >= 0; --gi) {
+        const long long j0 = (long long)gi * S.seg;
+        const long long j1 = std::min<long long>(P->n_slices, j0 + S.seg);
+        if (S.nseg > 1) {   // recompute the segment's forward stage inputs from its checkpoint
+            PropArgs r = base_args(P, 0, ud);
+            r.sub_begin = j0 * P->n_rk;
+            r.sub_end = j1 * P->n_rk;
+            r.x_in = S.ckpt + (size_t)gi * mat;
+            r.x_out = S.x;
+            if (exact) r.stage_store = S.Y;
+            else { r.bound_store = S.Y; r.bound_step = P->n_rk; }
+            if ((st = launch_prop(P, r, s)) != GRAPE_OK) return st;
+        }
+        // adjoint sweep in chunks (last slices first); the trace of each
+        // finished chunk runs on s2, overlapping the next chunk
+        const int nch = adjoint_chunks(P, j0, j1);
+        for (int ci = nch - 1; ci >= 0; --ci) {
+            const long long cA = j0 + (j1 - j0) * ci / nch;
+            const long long cB = j0 + (j1 - j0) * (ci + 1) / nch;
+            const size_t kofs = exact ? (size_t)(cA - j0) * P->n_rk * 4 * mat : (size_t)(cA - j0) * mat;
+            PropArgs b = base_args(P, 1, ud);
+            b.sub_begin = cA * P->n_rk;
+            b.sub_end = cB * P->n_rk;
+            b.reverse = 1;
+            b.x_in = S.mu;
+            b.x_out = S.mu;
+            if (exact) b.stage_store = S.K + kofs;
+            else { b.bound_store = S.K + kofs; b.bound_step = P->n_rk; }
+            if ((st = launch_prop(P, b, s)) != GRAPE_OK) return st;
+            if (P->R == 0) continue;
+            cudaStream_t ts = S.s2 ? S.s2 : s;
+            if (S.s2) {
+                GRAPE_CUDA_TRY(cudaEventRecord(S.ev[ci], s));
+                GRAPE_CUDA_TRY(cudaStreamWaitEvent(S.s2, S.ev[ci], 0));
+            }
+            TraceArgs t = P->trace;
+            t.n_rows = (int)(cB - cA);
+            t.G = Gd + (size_t)cA * P->R;
+            if (exact) {
+                t.K = S.K + kofs;
+                t.Y = S.Y + kofs;
+                t.npairs = (long long)P->n_rk * 4 * P->ns;
+                t.weight = 1.0;
+            } else {
+                t.K = S.K + kofs + mat;   // lambda_{j+1}, rho_{j+1} pair with row j
+                t.Y = S.Y + kofs + mat;
+                t.npairs = P->ns;
+                t.weight = dt;
+            }
+            if ((st = timed(P, PH_TRACE, ts, [&] { return k_trace(P, t, ts); })) != GRAPE_OK)
+                return st;
+        }
+        if (P->R > 0 && S.s2) {   // the segment's stage storage is reused next: join s2 into s
+            GRAPE_CUDA_TRY(cudaEventRecord(S.ev[grape_problem::kMaxChunks], S.s2));
+            GRAPE_CUDA_TRY(cudaStreamWaitEvent(s, S.ev[grape_problem::kMaxChunks], 0));
+        }
+    }
+    return GRAPE_OK;
+}
 
 extern "C" {
 
@@ -914,7 +1031,7 @@ grape_status grape_phase_times(grape_problem_t P, double ms[4], int32_t launches
 
 int32_t grape_gradient_launches(grape_problem_t P) {
     if (!P) return -1;
-    return gradient_launch_count(P);
+    return gradient_launch_count(P, P->seg, P->nseg);
 }
 
 grape_status grape_forward(grape_problem_t P, const double *u, double *F, double *rhoT,
@@ -965,86 +1082,18 @@ grape_status grape_gradient(grape_problem_t P, const double *u, double *F, doubl
     if ((st = stage_inputs(P, u, &ud, s)) != GRAPE_OK) return st;
     const bool f_dev = is_device_ptr(F);
     const bool g_dev = grad && is_device_ptr(grad);
-    double *Gout = g_dev ? grad : P->d_G;
-    const bool exact = (P->mode == GRAPE_GRAD_EXACT);
-    const long long nsub = (long long)P->n_slices * P->n_rk;
-    const double dt = P->T / P->n_slices;
-    const size_t mat = P->d2 * P->ns;
-
-    // forward sweep: stage storage directly (one segment) or checkpoints
-    PropArgs f = base_args(P, 0, ud);
-    f.sub_begin = 0;
-    f.sub_end = nsub;
-    f.x_in = P->d_rho0;
-    f.x_out = P->d_x;
-    if (P->nseg == 1) {
-        if (exact) f.stage_store = P->d_Y;
-        else { f.bound_store = P->d_Y; f.bound_step = P->n_rk; }
-    } else {
-        f.bound_store = P->d_ckpt;
-        f.bound_step = (long long)P->seg * P->n_rk;
-    }
-    if ((st = launch_prop(P, f, s)) != GRAPE_OK) return st;
-    if ((st = timed(P, PH_COST, s, [&] {
-             return k_cost(P, P->d_x, f_dev ? F : P->d_F, s);
-         })) != GRAPE_OK)
+    GradScratch S;
+    S.Y = P->d_Y;
+    S.K = P->d_K;
+    S.ckpt = P->d_ckpt;
+    S.x = P->d_x;
+    S.mu = P->d_mu;
+    S.seg = P->seg;
+    S.nseg = P->nseg;
+    S.s2 = P->s2;
+    S.ev = P->ev;
+    if ((st = run_gradient(P, ud, f_dev ? F : P->d_F, g_dev ? grad : P->d_G, s, S)) != GRAPE_OK)
         return st;
-    GRAPE_CUDA_TRY(cudaMemcpyAsync(P->d_mu, P->d_sigma, mat * sizeof(double2),
-                                   cudaMemcpyDeviceToDevice, s));
-    for (int gi = P->nseg - 1; gi >= 0; --gi) {
-        const long long j0 = (long long)gi * P->seg;
-        const long long j1 = std::min<long long>(P->n_slices, j0 + P->seg);
-        if (P->nseg > 1) {   // recompute the segment's forward stage inputs from its checkpoint
-            PropArgs r = base_args(P, 0, ud);
-            r.sub_begin = j0 * P->n_rk;
-            r.sub_end = j1 * P->n_rk;
-            r.x_in = P->d_ckpt + (size_t)gi * mat;
-            r.x_out = P->d_x;
-            if (exact) r.stage_store = P->d_Y;
-            else { r.bound_store = P->d_Y; r.bound_step = P->n_rk; }
-            if ((st = launch_prop(P, r, s)) != GRAPE_OK) return st;
-        }
-        // adjoint sweep in chunks (last slices first); the trace of each
-        // finished chunk runs on s2, overlapping the next chunk
-        const int nch = adjoint_chunks(P, j0, j1);
-        for (int ci = nch - 1; ci >= 0; --ci) {
-            const long long cA = j0 + (j1 - j0) * ci / nch;
-            const long long cB = j0 + (j1 - j0) * (ci + 1) / nch;
-            const size_t kofs = exact ? (size_t)(cA - j0) * P->n_rk * 4 * mat : (size_t)(cA - j0) * mat;
-            PropArgs b = base_args(P, 1, ud);
-            b.sub_begin = cA * P->n_rk;
-            b.sub_end = cB * P->n_rk;
-            b.reverse = 1;
-            b.x_in = P->d_mu;
-            b.x_out = P->d_mu;
-            if (exact) b.stage_store = P->d_K + kofs;
-            else { b.bound_store = P->d_K + kofs; b.bound_step = P->n_rk; }
-            if ((st = launch_prop(P, b, s)) != GRAPE_OK) return st;
-            if (P->R == 0) continue;
-            GRAPE_CUDA_TRY(cudaEventRecord(P->ev[ci], s));
-            GRAPE_CUDA_TRY(cudaStreamWaitEvent(P->s2, P->ev[ci], 0));
-            TraceArgs t = P->trace;
-            t.n_rows = (int)(cB - cA);
-            t.G = Gout + (size_t)cA * P->R;
-            if (exact) {
-                t.K = P->d_K + kofs;
-                t.Y = P->d_Y + kofs;
-                t.npairs = (long long)P->n_rk * 4 * P->ns;
-                t.weight = 1.0;
-            } else {
-                t.K = P->d_K + kofs + mat;   // lambda_{j+1}, rho_{j+1} pair with row j
-                t.Y = P->d_Y + kofs + mat;
-                t.npairs = P->ns;
-                t.weight = dt;
-            }
-            if ((st = timed(P, PH_TRACE, P->s2, [&] { return k_trace(P, t, P->s2); })) != GRAPE_OK)
-                return st;
-        }
-        if (P->R > 0) {   // the segment's stage storage is reused next: join s2 back into s
-            GRAPE_CUDA_TRY(cudaEventRecord(P->ev[grape_problem::kMaxChunks], P->s2));
-            GRAPE_CUDA_TRY(cudaStreamWaitEvent(s, P->ev[grape_problem::kMaxChunks], 0));
-        }
-    }
     bool sync = false;
     if (!f_dev) {
         GRAPE_CUDA_TRY(cudaMemcpyAsync(F, P->d_F, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1190,6 +1239,234 @@ grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F
         if (P->R > 0) GRAPE_CUDA_TRY(k_trace(P, t, s));
     }
     return GRAPE_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched gradients: many problems of different sizes in one graph launch.
+struct grape_batch {
+    int device = 0;
+    std::vector<grape_problem *> probs;
+    int n_lanes = 0;
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> lane_done;
+    cudaEvent_t fork = nullptr, ev_in = nullptr, ev_out = nullptr;
+    cudaStream_t cap = nullptr;                // the graph is captured and launched here
+    std::vector<std::vector<int>> items;       // problem indices per lane, run in order
+    std::vector<GradScratch> scratch;          // per problem (pointers into its lane's buffers)
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void *> key;             // pointers the graph was captured with
+    ~grape_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (auto e : lane_done) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (cap) cudaStreamDestroy(cap);
+        for (auto l : lanes) cudaStreamDestroy(l);
+        for (void *p : allocs) cudaFree(p);
+    }
+};
+
+namespace {
+
+// rough device time of one gradient, for the longest-first lane assignment
+double gradient_cost(const grape_problem *P) {
+    const double per_cta = (double)P->cu > 0 ? (double)P->cu : (double)P->chunk;
+    const double stage = 1.0 + per_cta * 0.006;   // microseconds
+    return 3.0 * P->n_slices * P->n_rk * 4.0 * stage;
+}
+
+}  // namespace
+
+extern "C" {
+
+grape_status grape_batch_create(grape_problem_t *problems, int32_t n, int32_t n_lanes,
+                                grape_batch_t *out) {
+    if (!problems || n <= 0 || !out) return fail(GRAPE_EINVAL, "NULL problems/out or n <= 0");
+    *out = nullptr;
+    const int dev = problems[0] ? problems[0]->device : 0;
+    for (int i = 0; i < n; ++i) {
+        if (!problems[i]) return fail(GRAPE_EINVAL, "NULL problem in batch");
+        if (problems[i]->device != dev) return fail(GRAPE_EINVAL, "batch problems on different devices");
+    }
+    DeviceGuard g(dev);
+    grape_batch *B = new grape_batch();
+    auto bail = [&](grape_status s) { delete B; return s; };
+    B->device = dev;
+    B->probs.assign(problems, problems + n);
+    B->n_lanes = std::max(1, std::min<int>(n_lanes > 0 ? n_lanes : 24, n));
+    // longest-first assignment to the least loaded lane
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return gradient_cost(B->probs[a]) > gradient_cost(B->probs[b]);
+    });
+    B->items.assign(B->n_lanes, {});
+    std::vector<double> load(B->n_lanes, 0.0);
+    for (int i : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        B->items[l].push_back(i);
+        load[l] += gradient_cost(B->probs[i]);
+    }
+    // per-lane scratch, shared by the lane's problems (they run one after another)
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(GRAPE_ECUDA, "cudaMemGetInfo failed"));
+    }
+    double frac = 0.6;
+    if (const char *env = std::getenv("GRAPE_MEM_FRACTION")) {
+        const double v = std::atof(env);
+        if (v > 0.0 && v <= 0.95) frac = v;
+    }
+    const size_t lane_budget = (size_t)(frac * (double)free_b) / B->n_lanes;
+    B->scratch.assign(n, GradScratch{});
+    for (int l = 0; l < B->n_lanes; ++l) {
+        size_t ys = 0, cs = 0, ms = 16;
+        std::vector<long long> segs;
+        for (int i : B->items[l]) {
+            grape_problem *P = B->probs[i];
+            const size_t mat = P->d2 * sizeof(double2) * P->ns;
+            long long seg = P->ckpt_stride > 0 ? std::min<long long>(P->ckpt_stride, P->n_slices)
+                                               : seg_for_budget(P, lane_budget > 2 * mat ? lane_budget - 2 * mat : 0);
+            if (seg_bytes(P, seg) + 2 * mat > lane_budget && P->ckpt_stride <= 0)
+                return bail(fail(GRAPE_ENOMEM, "batch problem does not fit its lane's memory budget"));
+            segs.push_back(seg);
+            ys = std::max(ys, stage_bytes(P, seg));
+            cs = std::max(cs, ckpt_bytes(P, seg));
+            ms = std::max(ms, mat);
+        }
+        auto take = [&](size_t nbytes) -> double2 * {
+            void *p = nullptr;
+            if (cudaMalloc(&p, std::max<size_t>(nbytes, 16)) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            B->allocs.push_back(p);
+            B->bytes += nbytes;
+            return static_cast<double2 *>(p);
+        };
+        double2 *Y = take(ys), *K = take(ys), *C = cs ? take(cs) : nullptr, *X = take(ms), *M = take(ms);
+        if (!Y || !K || (cs && !C) || !X || !M) return bail(fail(GRAPE_ENOMEM, "cudaMalloc failed for batch scratch"));
+        for (size_t t = 0; t < B->items[l].size(); ++t) {
+            grape_problem *P = B->probs[B->items[l][t]];
+            GradScratch &S = B->scratch[B->items[l][t]];
+            S.Y = Y;
+            S.K = K;
+            S.ckpt = C;
+            S.x = X;
+            S.mu = M;
+            S.seg = (int)segs[t];
+            S.nseg = (int)((P->n_slices + segs[t] - 1) / segs[t]);
+            S.s2 = nullptr;      // lanes already run concurrently: traces stay on the lane
+            S.ev = nullptr;
+        }
+    }
+    B->lanes.resize(B->n_lanes);
+    B->lane_done.resize(B->n_lanes);
+    for (int l = 0; l < B->n_lanes; ++l) {
+        if (cudaStreamCreateWithFlags(&B->lanes[l], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->lane_done[l], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(GRAPE_ECUDA, "stream/event creation failed"));
+        }
+    }
+    if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(GRAPE_ECUDA, "event creation failed"));
+    }
+    *out = B;
+    return GRAPE_OK;
+}
+
+grape_status grape_batch_destroy(grape_batch_t B) {
+    if (!B) return GRAPE_OK;
+    DeviceGuard g(B->device);
+    delete B;
+    return GRAPE_OK;
+}
+
+grape_status grape_batch_info(grape_batch_t B, int32_t *n_lanes, size_t *scratch_bytes,
+                              int32_t *launches) {
+    if (!B) return fail(GRAPE_EINVAL, "NULL batch");
+    if (n_lanes) *n_lanes = B->n_lanes;
+    if (scratch_bytes) *scratch_bytes = B->bytes;
+    if (launches) {
+        int n = 0;
+        for (size_t i = 0; i < B->probs.size(); ++i)
+            n += gradient_launch_count(B->probs[i], B->scratch[i].seg, B->scratch[i].nseg);
+        *launches = n;
+    }
+    return GRAPE_OK;
+}
+
+grape_status grape_batch_gradient(grape_batch_t B, const double *const *u, double *F,
+                                  double *const *grad, void *stream) {
+    if (!B || !u || !F || !grad) return fail(GRAPE_EINVAL, "NULL batch, u, F or grad");
+    DeviceGuard g(B->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = (int)B->probs.size();
+    std::vector<const void *> key;
+    key.reserve(2 * n + 1);
+    key.push_back(F);
+    for (int i = 0; i < n; ++i) {
+        key.push_back(u[i]);
+        key.push_back(grad[i]);
+    }
+    // the graph runs on the batch's own stream, ordered after and before `s`
+    auto launch = [&]() -> grape_status {
+        GRAPE_CUDA_TRY(cudaEventRecord(B->ev_in, s));
+        GRAPE_CUDA_TRY(cudaStreamWaitEvent(B->cap, B->ev_in, 0));
+        GRAPE_CUDA_TRY(cudaGraphLaunch(B->exec, B->cap));
+        GRAPE_CUDA_TRY(cudaEventRecord(B->ev_out, B->cap));
+        GRAPE_CUDA_TRY(cudaStreamWaitEvent(s, B->ev_out, 0));
+        return GRAPE_OK;
+    };
+    if (B->exec && key == B->key) return launch();
+    // validate once, outside the capture
+    if (!is_device_ptr(F)) return fail(GRAPE_EINVAL, "batch F must be device memory");
+    for (int i = 0; i < n; ++i) {
+        if (!is_device_ptr(u[i]) || (B->probs[i]->R > 0 && !is_device_ptr(grad[i])))
+            return fail(GRAPE_EINVAL, "batch u and grad must be device memory");
+    }
+    if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+    if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+    std::vector<bool> prof(n);
+    for (int i = 0; i < n; ++i) { prof[i] = B->probs[i]->profiling; B->probs[i]->profiling = false; }
+    grape_status st = GRAPE_OK;
+    GRAPE_CUDA_TRY(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeRelaxed));
+    cudaError_t e = cudaEventRecord(B->fork, B->cap);
+    for (int l = 0; l < B->n_lanes && e == cudaSuccess && st == GRAPE_OK; ++l) {
+        e = cudaStreamWaitEvent(B->lanes[l], B->fork, 0);
+        for (int i : B->items[l]) {
+            if (e != cudaSuccess || st != GRAPE_OK) break;
+            st = run_gradient(B->probs[i], u[i], F + i, grad[i], B->lanes[l], B->scratch[i]);
+        }
+        if (e == cudaSuccess && st == GRAPE_OK) e = cudaEventRecord(B->lane_done[l], B->lanes[l]);
+        if (e == cudaSuccess && st == GRAPE_OK) e = cudaStreamWaitEvent(B->cap, B->lane_done[l], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(B->cap, &graph);
+    for (int i = 0; i < n; ++i) B->probs[i]->profiling = prof[i];
+    if (st != GRAPE_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(GRAPE_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    B->graph = graph;
+    GRAPE_CUDA_TRY(cudaGraphInstantiate(&B->exec, graph, 0));
+    B->key = key;
+    return launch();
 }
 
 }  // extern "C"

@@ -204,3 +204,39 @@ class GrapeProblem:
         _lib.grape_gradient(self._h, u.ctypes.data, F.ctypes.data, G.ctypes.data,
                             _stream_ptr(stream))
         return float(F[0]), G
+
+
+class GrapeBatch:
+    """Many GrapeProblems evaluated by one batched, graph-captured launch
+    (grape_batch_gradient).  Inputs and outputs are CUDA tensors."""
+
+    def __init__(self, problems, n_lanes: int = 0):
+        self.problems = list(problems)
+        self._h = _lib.grape_batch_create([p.handle for p in self.problems], n_lanes)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.grape_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        """(lanes, scratch bytes, kernel launches per call)."""
+        return _lib.grape_batch_info(self._h)
+
+    def gradient(self, us, F=None, grads=None, stream=None):
+        import torch
+        dev = us[0].device
+        if F is None:
+            F = torch.empty(len(self.problems), dtype=torch.float64, device=dev)
+        if grads is None:
+            grads = [torch.empty((p.n_slices, p.R), dtype=torch.float64, device=dev)
+                     for p in self.problems]
+        _lib.grape_batch_gradient(self._h, [u.data_ptr() for u in us], F.data_ptr(),
+                                  [g.data_ptr() for g in grads], _stream_ptr(stream))
+        return F, grads
