@@ -125,6 +125,18 @@ grape_status grape_problem_memory(grape_problem_t problem, size_t *bytes);
 grape_status grape_problem_geometry(grape_problem_t problem, int32_t *cluster,
                                     int32_t *threads, int32_t *elems_per_thread);
 
+/* Which propagation kernel the problem runs on: 0 = Hermitian cluster kernel
+ * (upper triangle, states in distributed shared memory), 1 = full-matrix
+ * cluster kernel, 2 = grid kernel (states in global memory, one cooperative
+ * grid, for states too large for a cluster's shared memory). */
+grape_status grape_problem_kernel(grape_problem_t problem, int32_t *kind);
+
+/* Waits for the device and reports whether a grid barrier of the grid
+ * kernel gave up waiting since the last check (GRAPE_ETIMEOUT; the results
+ * of that call are invalid).  Calls that return results to host memory do
+ * this check themselves.  GRAPE_OK for the cluster kernels. */
+grape_status grape_problem_status(grape_problem_t problem);
+
 /* Per-launch timing with CUDA events recorded on the caller's stream around
  * every kernel the library launches (off by default).  grape_phase_times
  * waits for the recorded events, returns the summed milliseconds and launch

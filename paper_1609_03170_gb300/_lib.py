@@ -49,6 +49,7 @@ EXPORTS = ["grape_problem_create", "grape_problem_destroy", "grape_forward", "gr
            "grape_problem_memory", "grape_problem_geometry", "grape_set_profiling",
            "grape_phase_times", "grape_gradient_launches", "grape_gradient_static",
            "grape_batch_create", "grape_batch_destroy", "grape_batch_gradient", "grape_batch_info",
+           "grape_problem_kernel", "grape_problem_status",
            "grape_last_error", "grape_version"]
 
 
@@ -75,6 +76,10 @@ def load(build_if_missing: bool = True):
     lib.grape_forward.restype = c_int32
     lib.grape_gradient.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.grape_gradient.restype = c_int32
+    lib.grape_problem_kernel.argtypes = [c_void_p, P(c_int32)]
+    lib.grape_problem_kernel.restype = c_int32
+    lib.grape_problem_status.argtypes = [c_void_p]
+    lib.grape_problem_status.restype = c_int32
     lib.grape_batch_create.argtypes = [P(c_void_p), c_int32, c_int32, P(c_void_p)]
     lib.grape_batch_create.restype = c_int32
     lib.grape_batch_destroy.argtypes = [c_void_p]
@@ -134,6 +139,19 @@ def grape_gradient_static(h, u_ptr: int, F_ptr: int, grad_ptr: int, stream_ptr: 
     array (no device allocation); u, F and grad must be device pointers."""
     check(load().grape_gradient_static(h, u_ptr or None, F_ptr or None, grad_ptr or None,
                                        stream_ptr or None), "grape_gradient_static")
+
+
+KERNEL_NAMES = {0: "hermitian-cluster", 1: "full-cluster", 2: "grid"}
+
+
+def grape_problem_kernel(h) -> str:
+    k = c_int32()
+    check(load().grape_problem_kernel(h, ctypes.byref(k)), "grape_problem_kernel")
+    return KERNEL_NAMES[int(k.value)]
+
+
+def grape_problem_status(h) -> None:
+    check(load().grape_problem_status(h), "grape_problem_status")
 
 
 def grape_batch_create(handles, n_lanes: int = 0):

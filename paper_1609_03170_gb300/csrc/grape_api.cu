@@ -209,6 +209,11 @@ struct grape_problem {
     int ncl = 1, threads = GRAPE_PROP_THREADS, chunk = 0, halo = 0, win = 0, reach = 0;
     int variant = 0;                 // bit 0 = real jump tables, bit 1 = Hermitian kernel
     int hb = 0, cu = 0, maxwin = 0, htab_len = 0, rt_rows = 0;   // Hermitian kernel geometry
+    bool grid = false;               // grid kernel (state windows in global memory)
+    int nblocks = 0, ce = 0;         // its CTAs and entries per CTA
+    long long spin_limit = 1LL << 22;   // grid-barrier polls (~0.3 s) before giving up
+    double2 *d_gbuf = nullptr;
+    unsigned *d_gbar = nullptr;
     int *d_htab = nullptr;
     size_t smem = 0;
     int ckpt_stride = 0;
@@ -311,6 +316,14 @@ grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
 
 // Kernel launches in the problem's number type.
 cudaError_t k_prop(const grape_problem *P, const PropArgs &a, cudaStream_t s) {
+    if (P->grid) {
+        // arrivals and generation restart at zero; the error flag is kept
+        // until grape_problem_status reads it
+        const cudaError_t e = cudaMemsetAsync(P->d_gbar, 0, 2 * sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        return P->prec == GRAPE_PREC_FP64 ? grape_launch_grid_f64(a, P->nblocks, P->variant, P->smem, s)
+                                          : grape_launch_grid_df(a, P->nblocks, P->variant, P->smem, s);
+    }
     return P->prec == GRAPE_PREC_FP64 ? grape_launch_prop_f64(a, P->threads, P->variant, P->smem, s)
                                       : grape_launch_prop_df(a, P->threads, P->variant, P->smem, s);
 }
@@ -518,6 +531,50 @@ grape_status choose_geometry_h(grape_problem *P, int omax, int hb) {
     return fail(GRAPE_EINVAL, "problem too large for the Hermitian cluster kernel");
 }
 
+// Grid kernel: all states' upper triangles over at most one CTA per SM.
+grape_status choose_geometry_grid(grape_problem *P) {
+    int max_smem = 0;
+    GRAPE_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+    const long long NU = (long long)P->d * (P->d + 1) / 2;
+    const long long E = NU * P->ns;
+    const int nb = std::max(P->tab[0].nb, P->tab[1].nb), nt = std::max(P->tab[0].nt, P->tab[1].nt);
+    auto smem_for = [&](long long ce) {
+        return ((size_t)2 * ce + 2 * (size_t)nb * P->d + 2 * (size_t)nt * P->d) * sizeof(double2) +
+               (size_t)ce * sizeof(int4) + 12 * sizeof(double);
+    };
+    int max_blocks = 0;
+    const size_t probe = smem_for((E + 151) / 152);
+    cudaError_t e = P->prec == GRAPE_PREC_FP64
+                        ? grape_prepare_grid_f64(P->variant, (size_t)max_smem, probe, &max_blocks)
+                        : grape_prepare_grid_df(P->variant, (size_t)max_smem, probe, &max_blocks);
+    if (e != cudaSuccess || max_blocks < 1) {
+        cudaGetLastError();
+        return fail(GRAPE_EINVAL, "problem too large for the grid propagation kernel");
+    }
+    long long want = std::max<long long>(1, (E + 63) / 64);    // >= 64 entries per CTA
+    if (const char *env = std::getenv("GRAPE_GRID_BLOCKS")) {
+        const long long v = std::atoll(env);
+        if (v > 0) want = v;
+    }
+    const int nblocks = (int)std::min<long long>(want, max_blocks);
+    const long long ce = (E + nblocks - 1) / nblocks;
+    const size_t smem = smem_for(ce);
+    if (smem + 1024 > (size_t)max_smem) return fail(GRAPE_EINVAL, "problem too large for the grid propagation kernel");
+    P->d_gbuf = static_cast<double2 *>(P->alloc((size_t)2 * P->ns * P->d2 * sizeof(double2)));
+    P->d_gbar = static_cast<unsigned *>(P->alloc(4 * sizeof(unsigned)));
+    if (!P->d_gbuf || !P->d_gbar) return fail(GRAPE_ENOMEM, "cudaMalloc failed for the grid kernel buffers");
+    GRAPE_CUDA_TRY(cudaMemset(P->d_gbar, 0, 4 * sizeof(unsigned)));
+    if (const char *env = std::getenv("GRAPE_SPIN_LIMIT")) P->spin_limit = std::atoll(env);
+    P->grid = true;
+    P->nblocks = nblocks;
+    P->ce = (int)ce;
+    P->smem = smem;
+    P->threads = GRAPE_GRID_THREADS;
+    P->ncl = 1;
+    P->chunk = (int)ce;
+    return GRAPE_OK;
+}
+
 void rk_coefficients(double h, bool adjoint, PropArgs *a) {
     if (!adjoint) {
         const double g[4] = {1.0, 1.0, 1.0, 1.0};
@@ -554,6 +611,10 @@ PropArgs base_args(const grape_problem *P, int dir, const double *u) {
     a.cu = P->cu;
     a.maxwin = P->maxwin;
     a.rt_rows = P->rt_rows;
+    a.gbuf = P->d_gbuf;
+    a.gbar = P->d_gbar;
+    a.ce = P->ce;
+    a.spin_limit = P->spin_limit;
     rk_coefficients(P->T / P->n_slices / P->n_rk, dir == 1, &a);
     return a;
 }
@@ -942,14 +1003,24 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
         const HostDir &h = dir ? ha : hf;
         for (size_t q = 0; q < h.oL.size(); ++q) hb = std::max(hb, h.oL[q] - h.oR[q]);
     }
-    bool herm = true;
-    if (const char *env = std::getenv("GRAPE_HERMITIAN")) herm = std::atoi(env) != 0;
-    if (herm) {
+    // kernel choice: Hermitian cluster kernel, else full-matrix cluster kernel,
+    // else the grid kernel (GRAPE_KERNEL=grid|cluster|full forces one)
+    std::string kern = "auto";
+    if (const char *env = std::getenv("GRAPE_KERNEL")) kern = env;
+    bool herm = kern == "auto" || kern == "cluster";
+    if (const char *env = std::getenv("GRAPE_HERMITIAN")) herm = herm && std::atoi(env) != 0;
+    bool placed = false;
+    if (kern != "grid" && herm) {
         st = choose_geometry_h(P, omax, hb);
         if (st != GRAPE_OK && st != GRAPE_EINVAL) return bail(st);
-        if (st == GRAPE_EINVAL) herm = false;    // fall back to the full-matrix kernel
+        placed = (st == GRAPE_OK);
     }
-    if (!herm && (st = choose_geometry(P, omax)) != GRAPE_OK) return bail(st);
+    if (kern != "grid" && !placed) {
+        st = choose_geometry(P, omax);
+        if (st != GRAPE_OK && st != GRAPE_EINVAL) return bail(st);
+        placed = (st == GRAPE_OK);
+    }
+    if (!placed && (st = choose_geometry_grid(P)) != GRAPE_OK) return bail(st);
     {
         std::vector<double2> r(rho0.size()), g2(sig.size());
         for (size_t i = 0; i < r.size(); ++i) r[i] = encode(P, rho0[i]);
@@ -1000,6 +1071,26 @@ grape_status grape_problem_geometry(grape_problem_t P, int32_t *cluster, int32_t
     if (cluster) *cluster = P->ncl;
     if (threads) *threads = P->threads;
     if (ept) *ept = (P->chunk + P->threads - 1) / P->threads;
+    return GRAPE_OK;
+}
+
+grape_status grape_problem_status(grape_problem_t P) {
+    if (!P) return fail(GRAPE_EINVAL, "NULL problem");
+    if (!P->grid) return GRAPE_OK;
+    DeviceGuard g(P->device);
+    unsigned flag[3] = {0, 0, 0};
+    GRAPE_CUDA_TRY(cudaDeviceSynchronize());
+    GRAPE_CUDA_TRY(cudaMemcpy(flag, P->d_gbar, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (flag[2] != 0u) {
+        GRAPE_CUDA_TRY(cudaMemset(P->d_gbar, 0, 4 * sizeof(unsigned)));
+        return fail(GRAPE_ETIMEOUT, "a grid barrier of the propagation kernel gave up waiting");
+    }
+    return GRAPE_OK;
+}
+
+grape_status grape_problem_kernel(grape_problem_t P, int32_t *kind) {
+    if (!P || !kind) return fail(GRAPE_EINVAL, "NULL argument");
+    *kind = P->grid ? 2 : ((P->variant & 2) ? 0 : 1);
     return GRAPE_OK;
 }
 
@@ -1067,7 +1158,10 @@ grape_status grape_forward(grape_problem_t P, const double *u, double *F, double
         GRAPE_CUDA_TRY(cudaMemcpyAsync(F, P->d_F, sizeof(double), cudaMemcpyDeviceToHost, s));
         sync = true;
     }
-    if (sync) GRAPE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (sync) {
+        GRAPE_CUDA_TRY(cudaStreamSynchronize(s));
+        if (P->grid) return grape_problem_status(P);
+    }
     return GRAPE_OK;
 }
 
@@ -1104,7 +1198,10 @@ grape_status grape_gradient(grape_problem_t P, const double *u, double *F, doubl
                                        cudaMemcpyDeviceToHost, s));
         sync = true;
     }
-    if (sync) GRAPE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (sync) {
+        GRAPE_CUDA_TRY(cudaStreamSynchronize(s));
+        if (P->grid) return grape_problem_status(P);
+    }
     return GRAPE_OK;
 }
 

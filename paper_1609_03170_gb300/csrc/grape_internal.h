@@ -64,7 +64,14 @@ struct PropArgs {
     int cu;                             // upper-triangle entries per CTA
     int maxwin;                         // largest window (entries) of the cluster
     int rt_rows;                        // rows of the largest push table
+    // grid kernel (state windows in global memory, one grid barrier per stage)
+    void *gbuf;                         // [2][n_states][d*d] stage-input buffers
+    unsigned *gbar;                     // [0] arrivals, [1] generation, [2] error flag
+    int ce;                             // entries (state, upper entry) per CTA
+    long long spin_limit;               // polls of the grid barrier before it gives up
 };
+
+#define GRAPE_GRID_THREADS 512
 
 // Layout of the Hermitian kernel's table (ints), for a cluster of ncl CTAs:
 //   [4k + 0..3]            u0, u1 (owned upper-triangle range), wr0, nrows of CTA k
@@ -104,7 +111,11 @@ struct TraceArgs {
     cudaError_t grape_launch_cost_##SUFFIX(const void *rho, const void *sigma, int n_states,    \
                                            int d2, double *F, cudaStream_t stream);             \
     cudaError_t grape_launch_to_double_##SUFFIX(const void *src, double2 *dst, size_t n,        \
-                                                cudaStream_t stream);
+                                                cudaStream_t stream);                           \
+    cudaError_t grape_launch_grid_##SUFFIX(const PropArgs &p, int nblocks, int variant,         \
+                                           size_t smem, cudaStream_t stream);                   \
+    cudaError_t grape_prepare_grid_##SUFFIX(int variant, size_t smem_total, size_t smem,        \
+                                            int *max_blocks);
 
 GRAPE_DECLARE_LAUNCHERS(f64)
 GRAPE_DECLARE_LAUNCHERS(df)

@@ -538,6 +538,220 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
         store_herm<Num>(x_out + soff, d, rc[u - u0].x, rc[u - u0].y, xs[u - u0]);
 }
 
+// ---------------------------------------------------------------------------
+// Grid kernel for states too large for a cluster's shared memory: one
+// cooperative grid of CTAs (at most one per SM) shares all states' upper
+// triangles in contiguous chunks; the stage inputs live as full matrices in
+// global memory (L2-resident; read with ld.global.cg so stale L1 lines are
+// never used), every upper entry written together with its conjugate
+// mirror; a grid barrier separates RK stages.  The barrier's wait is
+// bounded: after spin_limit polls it raises the error flag and every CTA
+// leaves its loop, so a fault cannot hang the GPU.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// returns false when the barrier gave up (error flag set)
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, long long limit,
+                                             int *abort_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned gen = ld_acquire_gpu(&bar[1]);
+        const unsigned old = atom_add_acq_rel_gpu(&bar[0], 1u);
+        if (old == nblocks - 1) {
+            bar[0] = 0u;                        // ordered before the release below
+            st_release_gpu(&bar[1], gen + 1u);
+        } else {
+            long long it = 0;
+            while (ld_acquire_gpu(&bar[1]) == gen) {
+                if (ld_acquire_gpu(&bar[2]) != 0u || ++it > limit) {
+                    atomicExch(&bar[2], 1u);
+                    *abort_flag = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+    }
+    __syncthreads();
+    return *abort_flag == 0;
+}
+
+template <class Num, bool REALJ>
+__device__ __forceinline__ typename Num::val lindblad_g_at(const typename Num::store_t *cur, int i,
+                                                           int j, int d, const PropTables &t,
+                                                           const typename Num::store_t *A,
+                                                           const typename Num::store_t *vL,
+                                                           const typename Num::store_t *vR) {
+    typename Num::acc w = Num::acc_zero();
+#pragma unroll 1
+    for (int b = 0; b < t.nb; ++b) {
+        const int o = t.off[b], r = i + o, c = j + o;
+        if (r >= 0 && r < d) Num::mac(w, Num::load(A[b * d + i]), Num::load(__ldcg(&cur[(size_t)r * d + j])));
+        if (c >= 0 && c < d)
+            Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(__ldcg(&cur[(size_t)i * d + c])));
+    }
+    w = Num::acc_minus_i(w);
+#pragma unroll 1
+    for (int q = 0; q < t.nt; ++q) {
+        const int r = i + t.joL[q], c = j + t.joR[q];
+        if (r < 0 || r >= d || c < 0 || c >= d) continue;
+        const typename Num::val zv = Num::load(__ldcg(&cur[(size_t)r * d + c]));
+        if (REALJ) {
+            const typename Num::real_t cf =
+                Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j])));
+            Num::mac_real(w, cf, zv);
+        } else {
+            Num::mac(w, Num::mul_conjb(Num::load(vL[q * d + i]), Num::load(vR[q * d + j])), zv);
+        }
+    }
+    return Num::done(w);
+}
+
+// Shared memory: xs, as [ce]; bands [2][nb][d]; vL, vR [nt][d];
+// ent [ce] (int4: row, column, state); 12 RK coefficients.
+template <class Num, bool REALJ>
+__global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const PropArgs p) {
+    using S = typename Num::store_t;
+    using V = typename Num::val;
+    using R = typename Num::real_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int abort_flag;
+    const int d = p.d;
+    const size_t d2 = (size_t)d * d;
+    const int nbd = p.tab.nb * d;
+    S *xs = reinterpret_cast<S *>(smem_raw);
+    S *as = xs + p.ce;
+    S *bands = as + p.ce;
+    S *vL = bands + 2 * nbd;
+    S *vR = vL + p.tab.nt * d;
+    int4 *ent = reinterpret_cast<int4 *>(vR + p.tab.nt * d);
+    R *cg = reinterpret_cast<R *>(ent + p.ce);
+    R *ca = cg + 4;
+    R *cb = cg + 8;
+    S *gb0 = static_cast<S *>(p.gbuf);
+    S *gb1 = gb0 + (size_t)p.n_states * d2;
+    const S *x_in = static_cast<const S *>(p.x_in);
+    S *x_out = static_cast<S *>(p.x_out);
+    S *stage_store = static_cast<S *>(p.stage_store);
+    S *bound_store = static_cast<S *>(p.bound_store);
+    const long long NU = (long long)d * (d + 1) / 2;
+    const long long E = NU * p.n_states;
+    const long long e0 = (long long)blockIdx.x * p.ce;
+    const long long e1 = min(E, e0 + p.ce);
+    const int nth = blockDim.x;
+    const unsigned nblocks = gridDim.x;
+
+    if (threadIdx.x == 0) abort_flag = 0;
+    for (int i = threadIdx.x; i < p.tab.nt * d; i += nth) {
+        vL[i] = Num::store(Num::from_double2(__ldg(&p.tab.vL[i])));
+        vR[i] = Num::store(Num::from_double2(__ldg(&p.tab.vR[i])));
+    }
+    if (threadIdx.x < 4) {
+        cg[threadIdx.x] = Num::real_const(p.g[threadIdx.x]);
+        ca[threadIdx.x] = Num::real_const(p.a[threadIdx.x]);
+        cb[threadIdx.x] = Num::real_const(p.b[threadIdx.x]);
+    }
+    const long long nsub = p.sub_end - p.sub_begin;
+    long long n_first = p.reverse ? p.sub_end - 1 : p.sub_begin;
+    if (nsub <= 0) n_first = p.sub_begin;
+    int jcur = (int)(n_first / p.n_rk);
+    build_bands<Num>(bands, p, jcur);
+    __syncthreads();   // coefficients, tables and bands are read below
+    for (long long e = e0 + threadIdx.x; e < e1; e += nth) {
+        const int st = (int)(e / NU);
+        const long long u = e - (long long)st * NU;
+        const double b2 = 2.0 * d + 1.0;
+        int i = (int)floor(0.5 * (b2 - sqrt(b2 * b2 - 8.0 * (double)u)));
+        i = max(0, min(d - 1, i));
+        while (i > 0 && (long long)i * d - (long long)i * (i - 1) / 2 > u) --i;
+        while (i + 1 < d && (long long)(i + 1) * d - (long long)(i + 1) * i / 2 <= u) ++i;
+        const int j = i + (int)(u - ((long long)i * d - (long long)i * (i - 1) / 2));
+        ent[e - e0] = make_int4(i, j, st, 0);
+        const V x = Num::load(x_in[(size_t)st * d2 + (size_t)i * d + j]);
+        xs[e - e0] = Num::store(x);
+        store_herm<Num>(gb0 + (size_t)st * d2, d, i, j, Num::store(Num::scale(cg[0], x)));
+    }
+    if (!grid_barrier(p.gbar, nblocks, p.spin_limit, &abort_flag)) return;
+
+    const bool unit_g = (p.g[1] == 1.0 && p.g[2] == 1.0 && p.g[3] == 1.0);
+    int tb = 0;
+    for (long long it = 0; it < nsub; ++it) {
+        const long long n = p.reverse ? p.sub_end - 1 - it : p.sub_begin + it;
+        const long long tidx = p.reverse ? n + 1 : n;
+        if (bound_store && ((tidx - p.sub_begin) % p.bound_step) == 0) {
+            S *dst = bound_store + (size_t)((tidx - p.sub_begin) / p.bound_step) * p.n_states * d2;
+            for (long long e = e0 + threadIdx.x; e < e1; e += nth) {
+                const int4 q = ent[e - e0];
+                store_herm<Num>(dst + (size_t)q.z * d2, d, q.x, q.y, xs[e - e0]);
+            }
+        }
+        const S *A = bands + tb * nbd;
+        bool flip = false;
+#pragma unroll 1
+        for (int s = 0; s < 4; ++s) {
+            const S *cur = (s & 1) ? gb1 : gb0;
+            S *nxt = (s & 1) ? gb0 : gb1;
+            S *stg = nullptr;
+            if (stage_store)
+                stg = stage_store + (size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states * d2;
+            const R as_ = ca[s];
+#pragma unroll 1
+            for (long long e = e0 + threadIdx.x; e < e1; e += nth) {
+                const int li = (int)(e - e0);
+                const int4 q = ent[li];
+                const S *cs = cur + (size_t)q.z * d2;
+                const V w = lindblad_g_at<Num, REALJ>(cs, q.x, q.y, d, p.tab, A, vL, vR);
+                if (stg) store_herm<Num>(stg + (size_t)q.z * d2, d, q.x, q.y, __ldcg(&cs[(size_t)q.x * d + q.y]));
+                const V x = Num::load(xs[li]);
+                const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
+                V z;
+                if (s < 3) {
+                    as[li] = Num::store(acc);
+                    z = unit_g ? Num::axpy(cb[s + 1], w, x) : Num::lin2(cg[s + 1], x, cb[s + 1], w);
+                } else {
+                    xs[li] = Num::store(acc);
+                    z = Num::scale(cg[0], acc);
+                }
+                store_herm<Num>(nxt + (size_t)q.z * d2, d, q.x, q.y, Num::store(z));
+            }
+            if (s == 3 && it + 1 < nsub) {
+                const long long nn = p.reverse ? n - 1 : n + 1;
+                const int jn = (int)(nn / p.n_rk);
+                if (jn != jcur) {
+                    build_bands<Num>(bands + (tb ^ 1) * nbd, p, jn);
+                    jcur = jn;
+                    flip = true;
+                }
+            }
+            if (!grid_barrier(p.gbar, nblocks, p.spin_limit, &abort_flag)) return;
+        }
+        if (flip) tb ^= 1;
+    }
+    const long long tend = p.reverse ? p.sub_begin : p.sub_end;
+    if (bound_store && ((tend - p.sub_begin) % p.bound_step) == 0) {
+        S *dst = bound_store + (size_t)((tend - p.sub_begin) / p.bound_step) * p.n_states * d2;
+        for (long long e = e0 + threadIdx.x; e < e1; e += nth) {
+            const int4 q = ent[e - e0];
+            store_herm<Num>(dst + (size_t)q.z * d2, d, q.x, q.y, xs[e - e0]);
+        }
+    }
+    for (long long e = e0 + threadIdx.x; e < e1; e += nth) {
+        const int4 q = ent[e - e0];
+        store_herm<Num>(x_out + (size_t)q.z * d2, d, q.x, q.y, xs[e - e0]);
+    }
+}
+
 template <class Num>
 __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
     using S = typename Num::store_t;
@@ -694,6 +908,45 @@ cudaError_t clusters_t(int threads, size_t smem, int ncl, int n_blocks, int *clu
     return cudaOccupancyMaxActiveClusters(clusters, prop_kernel<Num, REALJ>, &cfg);
 }
 
+template <class Num, bool REALJ>
+cudaError_t launch_grid_t(const PropArgs &p, int nblocks, size_t smem, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3(GRAPE_GRID_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, prop_g_kernel<Num, REALJ>, p);
+}
+
+template <class Num>
+cudaError_t launch_grid(const PropArgs &p, int nblocks, int variant, size_t smem, cudaStream_t s) {
+    return (variant & 1) ? launch_grid_t<Num, true>(p, nblocks, smem, s)
+                         : launch_grid_t<Num, false>(p, nblocks, smem, s);
+}
+
+// prepares the grid kernel and returns how many CTAs of it fit on the device at once
+template <class Num>
+cudaError_t prepare_grid(int variant, size_t smem_total, size_t smem, int *max_blocks) {
+    cudaError_t e = (variant & 1) ? prepare_kernel(prop_g_kernel<Num, true>, smem_total, 1)
+                                  : prepare_kernel(prop_g_kernel<Num, false>, smem_total, 1);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = (variant & 1) ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prop_g_kernel<Num, true>,
+                                                                      GRAPE_GRID_THREADS, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prop_g_kernel<Num, false>,
+                                                                      GRAPE_GRID_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *max_blocks = per_sm * sms;
+    return cudaSuccess;
+}
+
 // `variant` bit 0: the jump tables are real; bit 1: Hermitian (upper-triangle) kernel.
 #define GRAPE_VARIANT_DISPATCH(FN, ...)                                   \
     switch (variant & 3) {                                                \
@@ -770,4 +1023,12 @@ cudaError_t launch_to_double(const void *src, double2 *dst, size_t n, cudaStream
     cudaError_t grape_launch_to_double_##SUFFIX(const void *src, double2 *dst, size_t n,        \
                                                 cudaStream_t s) {                               \
         return grape_k::launch_to_double<NUM>(src, dst, n, s);                                  \
+    }                                                                                           \
+    cudaError_t grape_launch_grid_##SUFFIX(const PropArgs &p, int nblocks, int variant,         \
+                                           size_t smem, cudaStream_t s) {                       \
+        return grape_k::launch_grid<NUM>(p, nblocks, variant, smem, s);                         \
+    }                                                                                           \
+    cudaError_t grape_prepare_grid_##SUFFIX(int variant, size_t smem_total, size_t smem,        \
+                                            int *max_blocks) {                                  \
+        return grape_k::prepare_grid<NUM>(variant, smem_total, smem, max_blocks);               \
     }

@@ -164,6 +164,14 @@ class GrapeProblem:
     def gradient_launches(self) -> int:
         return _lib.grape_gradient_launches(self._h)
 
+    def kernel(self) -> str:
+        """hermitian-cluster, full-cluster or grid."""
+        return _lib.grape_problem_kernel(self._h)
+
+    def status(self) -> None:
+        """Raise GrapeError(GRAPE_ETIMEOUT) if a grid barrier gave up."""
+        _lib.grape_problem_status(self._h)
+
     def set_profiling(self, on: bool = True) -> None:
         _lib.grape_set_profiling(self._h, on)
 
