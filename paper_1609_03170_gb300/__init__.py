@@ -12,6 +12,14 @@ from ._lib import (GRAPE_GRAD_EXACT, GRAPE_GRAD_FIRST_ORDER, GRAPE_PREC_DF64, GR
                    grape_gradient, grape_problem_create, grape_problem_destroy)
 from .problem import BandModel, BandOp, GrapeBatch, GrapeProblem, band_model
 
+
+def __getattr__(name):
+    # torch is imported only when the autograd front end is used
+    if name in ("GrapeFunction", "grape_phi"):
+        from . import autograd
+        return getattr(autograd, name)
+    raise AttributeError(name)
+
 __all__ = ["GRAPE_GRAD_EXACT", "GRAPE_GRAD_FIRST_ORDER", "GRAPE_PREC_DF64", "GRAPE_PREC_FP64",
            "GrapeError", "GrapeProblem", "GrapeBatch",
            "BandModel", "BandOp", "band_model", "grape_forward", "grape_gradient",
