@@ -193,6 +193,50 @@ grape_status grape_batch_gradient(grape_batch_t batch, const double *const *u, d
 grape_status grape_batch_info(grape_batch_t batch, int32_t *n_lanes, size_t *scratch_bytes,
                               int32_t *launches);
 
+/* ---- Serving: pulse optimisations with continuous batching ----
+ * A job maximises Phi of one problem with projected L-BFGS (the paper
+ * optimises with BFGS, Sec. 2.1, Eq. update) over the box
+ * u_min <= u <= u_max, starting from u0.  Each iteration is one gradient
+ * evaluation at a trial point followed by one L-BFGS step on the device
+ * (decrease of -Phi accepts the point, otherwise the step is halved).  The
+ * server keeps every job's controls, gradient and L-BFGS history on the
+ * device; a worker thread admits queued jobs whenever a slot is free and
+ * their gradient storage fits the memory budget, runs each admitted job on
+ * its own stream and launches its next iteration as soon as the previous one
+ * completes, so iterations of different jobs overlap.  A job's result does
+ * not depend on the other jobs (deterministic kernels). */
+typedef struct grape_server *grape_server_t;
+
+typedef struct {
+    int32_t max_iters;   /* gradient evaluations (e.g. 50) */
+    int32_t lbfgs_m;     /* curvature pairs kept (1..64, e.g. 10) */
+    double u_min, u_max; /* box on every control amplitude */
+    double step0;        /* first step: largest control change of the first move */
+    double tol;          /* stop when max |P(u - grad) - u| <= tol (0: use max_iters) */
+} grape_opt_params;
+
+typedef struct {
+    int32_t evaluations; /* gradient evaluations the job used */
+    double queued_us;    /* submit -> admission */
+    double latency_us;   /* submit -> result */
+} grape_job_info;
+
+/* hbm_budget_bytes = 0 uses 60% of the free device memory; max_slots jobs
+ * run at once.  Starts the worker thread (device = the current device). */
+grape_status grape_server_create(size_t hbm_budget_bytes, int32_t max_slots, grape_server_t *out);
+/* Runs the jobs already admitted to completion, drops queued ones, joins the
+ * worker.  Problems must outlive their jobs; a problem serves one job at a
+ * time (jobs of a busy problem wait in the queue). */
+grape_status grape_server_destroy(grape_server_t server);
+/* Queues a job (u0: host, n_slices x n_controls; it is copied). */
+grape_status grape_submit(grape_server_t server, grape_problem_t problem, const double *u0,
+                          const grape_opt_params *params, uint64_t *ticket);
+/* Waits up to timeout_us for the job; GRAPE_ENOTREADY while it runs.  On
+ * completion copies the best controls (host) and Phi there, fills info (all
+ * three nullable) and forgets the ticket. */
+grape_status grape_poll(grape_server_t server, uint64_t ticket, int64_t timeout_us, double *u_out,
+                        double *F_out, grape_job_info *info);
+
 /* Kernel launches one grape_gradient call makes (for launch accounting);
  * -1 before the first gradient call has fixed the segment plan. */
 int32_t grape_gradient_launches(grape_problem_t problem);

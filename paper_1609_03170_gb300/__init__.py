@@ -10,7 +10,7 @@ from . import _lib
 from ._lib import (GRAPE_GRAD_EXACT, GRAPE_GRAD_FIRST_ORDER, GRAPE_PREC_DF64, GRAPE_PREC_FP64,
                    GrapeError, grape_forward,
                    grape_gradient, grape_problem_create, grape_problem_destroy)
-from .problem import BandModel, BandOp, GrapeBatch, GrapeProblem, band_model
+from .problem import BandModel, BandOp, GrapeBatch, GrapeProblem, GrapeServer, band_model
 
 
 def __getattr__(name):
@@ -21,6 +21,6 @@ def __getattr__(name):
     raise AttributeError(name)
 
 __all__ = ["GRAPE_GRAD_EXACT", "GRAPE_GRAD_FIRST_ORDER", "GRAPE_PREC_DF64", "GRAPE_PREC_FP64",
-           "GrapeError", "GrapeProblem", "GrapeBatch",
+           "GrapeError", "GrapeProblem", "GrapeBatch", "GrapeServer",
            "BandModel", "BandOp", "band_model", "grape_forward", "grape_gradient",
            "grape_problem_create", "grape_problem_destroy"]

@@ -37,6 +37,15 @@ class grape_problem_desc(ctypes.Structure):
                 ("precision", c_int32)]
 
 
+class grape_opt_params(ctypes.Structure):
+    _fields_ = [("max_iters", c_int32), ("lbfgs_m", c_int32), ("u_min", c_double),
+                ("u_max", c_double), ("step0", c_double), ("tol", c_double)]
+
+
+class grape_job_info(ctypes.Structure):
+    _fields_ = [("evaluations", c_int32), ("queued_us", c_double), ("latency_us", c_double)]
+
+
 class GrapeError(RuntimeError):
     def __init__(self, status, where, msg):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
@@ -49,7 +58,8 @@ EXPORTS = ["grape_problem_create", "grape_problem_destroy", "grape_forward", "gr
            "grape_problem_memory", "grape_problem_geometry", "grape_set_profiling",
            "grape_phase_times", "grape_gradient_launches", "grape_gradient_static",
            "grape_batch_create", "grape_batch_destroy", "grape_batch_gradient", "grape_batch_info",
-           "grape_problem_kernel", "grape_problem_status",
+           "grape_problem_kernel", "grape_problem_status", "grape_server_create",
+           "grape_server_destroy", "grape_submit", "grape_poll",
            "grape_last_error", "grape_version"]
 
 
@@ -76,6 +86,16 @@ def load(build_if_missing: bool = True):
     lib.grape_forward.restype = c_int32
     lib.grape_gradient.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.grape_gradient.restype = c_int32
+    lib.grape_server_create.argtypes = [c_size_t, c_int32, P(c_void_p)]
+    lib.grape_server_create.restype = c_int32
+    lib.grape_server_destroy.argtypes = [c_void_p]
+    lib.grape_server_destroy.restype = c_int32
+    lib.grape_submit.argtypes = [c_void_p, c_void_p, P(c_double), P(grape_opt_params),
+                                 P(ctypes.c_uint64)]
+    lib.grape_submit.restype = c_int32
+    lib.grape_poll.argtypes = [c_void_p, ctypes.c_uint64, ctypes.c_int64, P(c_double),
+                               P(c_double), P(grape_job_info)]
+    lib.grape_poll.restype = c_int32
     lib.grape_problem_kernel.argtypes = [c_void_p, P(c_int32)]
     lib.grape_problem_kernel.restype = c_int32
     lib.grape_problem_status.argtypes = [c_void_p]
@@ -139,6 +159,35 @@ def grape_gradient_static(h, u_ptr: int, F_ptr: int, grad_ptr: int, stream_ptr: 
     array (no device allocation); u, F and grad must be device pointers."""
     check(load().grape_gradient_static(h, u_ptr or None, F_ptr or None, grad_ptr or None,
                                        stream_ptr or None), "grape_gradient_static")
+
+
+def grape_server_create(budget_bytes: int = 0, max_slots: int = 16):
+    srv = c_void_p()
+    check(load().grape_server_create(int(budget_bytes), int(max_slots), ctypes.byref(srv)),
+          "grape_server_create")
+    return srv
+
+
+def grape_server_destroy(srv) -> None:
+    check(load().grape_server_destroy(srv), "grape_server_destroy")
+
+
+def grape_submit(srv, problem_handle, u0, params: grape_opt_params) -> int:
+    t = ctypes.c_uint64()
+    check(load().grape_submit(srv, problem_handle, u0.ctypes.data_as(P(c_double)),
+                              ctypes.byref(params), ctypes.byref(t)), "grape_submit")
+    return int(t.value)
+
+
+def grape_poll(srv, ticket: int, timeout_us: int, u_out, F_out, info: grape_job_info) -> bool:
+    """True when the job is done (results written), False while it runs."""
+    st = load().grape_poll(srv, ctypes.c_uint64(ticket), ctypes.c_int64(int(timeout_us)),
+                           u_out.ctypes.data_as(P(c_double)), F_out.ctypes.data_as(P(c_double)),
+                           ctypes.byref(info))
+    if st == GRAPE_ENOTREADY:
+        return False
+    check(st, "grape_poll")
+    return True
 
 
 KERNEL_NAMES = {0: "hermitian-cluster", 1: "full-cluster", 2: "grid"}

@@ -12,7 +12,12 @@
 #include "grape_num.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
 #include <complex>
 #include <cstdlib>
 #include <cstring>
@@ -245,6 +250,27 @@ struct grape_problem {
         }
         return e;
     }
+    std::vector<void *> grad_allocs;   // gradient storage, released between served jobs
+    size_t grad_bytes = 0;
+    void *alloc_grad(size_t n) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(n, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        grad_allocs.push_back(p);
+        grad_bytes += n;
+        bytes += n;
+        return p;
+    }
+    void release_grad() {
+        for (void *p : grad_allocs) cudaFree(p);
+        grad_allocs.clear();
+        bytes -= grad_bytes;
+        grad_bytes = 0;
+        d_Y = d_K = d_ckpt = nullptr;
+        seg = nseg = 0;
+    }
     std::vector<void *> allocs;
     void *alloc(size_t n) {
         void *p = nullptr;
@@ -261,6 +287,7 @@ struct grape_problem {
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
         if (s2) cudaStreamDestroy(s2);
+        for (void *p : grad_allocs) cudaFree(p);
         for (auto &m : marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
         for (auto e : event_pool) cudaEventDestroy(e);
         for (void *p : allocs) cudaFree(p);
@@ -675,7 +702,7 @@ int gradient_launch_count(const grape_problem *P, int seg, int nseg) {
     return n;
 }
 
-grape_status plan_gradient(grape_problem *P) {
+grape_status plan_gradient(grape_problem *P, size_t budget_override = 0) {
     if (P->nseg > 0) return GRAPE_OK;
     size_t free_b = 0, total_b = 0;
     GRAPE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
@@ -684,7 +711,7 @@ grape_status plan_gradient(grape_problem *P) {
         const double v = std::atof(env);
         if (v > 0.0 && v <= 0.95) frac = v;
     }
-    const size_t budget = (size_t)(frac * (double)free_b);
+    const size_t budget = budget_override ? budget_override : (size_t)(frac * (double)free_b);
     long long seg;
     if (P->ckpt_stride > 0) {
         seg = std::min<long long>(P->ckpt_stride, P->n_slices);
@@ -697,12 +724,12 @@ grape_status plan_gradient(grape_problem *P) {
     const size_t mat = P->d2 * sizeof(double2) * P->ns;
     const size_t per = (P->mode == GRAPE_GRAD_EXACT) ? (size_t)seg * P->n_rk * 4 * mat
                                                     : (size_t)(seg + 1) * mat;
-    P->d_Y = static_cast<double2 *>(P->alloc(per));
-    P->d_K = static_cast<double2 *>(P->alloc(per));
+    P->d_Y = static_cast<double2 *>(P->alloc_grad(per));
+    P->d_K = static_cast<double2 *>(P->alloc_grad(per));
     if (!P->d_Y || !P->d_K) return fail(GRAPE_ENOMEM, "cudaMalloc failed for gradient storage");
     const int nseg = (int)((P->n_slices + seg - 1) / seg);
     if (nseg > 1) {
-        P->d_ckpt = static_cast<double2 *>(P->alloc((size_t)(nseg + 1) * mat));
+        P->d_ckpt = static_cast<double2 *>(P->alloc_grad((size_t)(nseg + 1) * mat));
         if (!P->d_ckpt) return fail(GRAPE_ENOMEM, "cudaMalloc failed for checkpoints");
     }
     P->seg = (int)seg;
@@ -1564,6 +1591,350 @@ grape_status grape_batch_gradient(grape_batch_t B, const double *const *u, doubl
     GRAPE_CUDA_TRY(cudaGraphInstantiate(&B->exec, graph, 0));
     B->key = key;
     return launch();
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving: pulse optimisations (projected L-BFGS on the device) admitted by
+// device memory and run with continuous batching.  Every admitted job owns a
+// stream; a worker thread launches a job's next iteration (one gradient
+// evaluation plus one L-BFGS step) as soon as its previous iteration has
+// completed, and admits queued jobs whenever slots and memory free up, so
+// iterations of different jobs overlap on the GPU.
+struct ServerJob {
+    uint64_t ticket = 0;
+    grape_problem *P = nullptr;
+    grape_opt_params prm{};
+    int n = 0;
+    std::vector<double> u0;
+    double *d_arena = nullptr;        // u, g, ut, dir, S, Y, rho, alpha, F, G
+    LbfgsState *d_state = nullptr;
+    LbfgsState *h_state = nullptr;    // pinned copy read by the worker
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    size_t footprint = 0;             // device bytes the job holds
+    size_t reserved = 0;              // budget reserved for it at admission
+    LbfgsArgs args{};
+    int phase = 0;                    // 0 queued, 1 running, 2 done, 3 failed
+    grape_status err = GRAPE_OK;
+    std::string err_msg;
+    std::vector<double> u_out;
+    double F_out = 0.0;
+    int evals = 0;
+    std::chrono::steady_clock::time_point t_submit, t_start, t_done;
+};
+
+struct grape_server {
+    int device = 0;
+    size_t budget = 0;
+    int max_slots = 1;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ServerJob *> queue;
+    std::vector<ServerJob *> active;
+    std::map<uint64_t, ServerJob *> jobs;
+    size_t reserved = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+    ~grape_server() {
+        for (auto &kv : jobs) delete kv.second;
+    }
+};
+
+namespace {
+
+size_t lbfgs_bytes(int n, int m) { return ((size_t)(6 + 2 * m) * n + 2 * m + 2) * sizeof(double); }
+
+// Allocate the job's device state and plan its gradient storage within its
+// share of the budget.  Called by the worker thread with the device current.
+grape_status start_job(grape_server *S, ServerJob *j) {
+    grape_problem *P = j->P;
+    const int n = j->n, m = j->prm.lbfgs_m;
+    const size_t share = S->budget / std::max(1, S->max_slots);
+    const size_t lb = lbfgs_bytes(n, m);
+    grape_status st = plan_gradient(P, share > lb ? share - lb : 1);
+    if (st != GRAPE_OK) return st;
+    if (cudaMalloc(&j->d_arena, lb) != cudaSuccess || cudaMalloc(&j->d_state, sizeof(LbfgsState)) != cudaSuccess ||
+        cudaMallocHost(&j->h_state, sizeof(LbfgsState)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GRAPE_ENOMEM, "job allocation failed");
+    }
+    double *a = j->d_arena;
+    LbfgsArgs &A = j->args;
+    A.state = j->d_state;
+    A.n = n;
+    A.m = m;
+    A.max_evals = j->prm.max_iters;
+    A.u_min = j->prm.u_min;
+    A.u_max = j->prm.u_max;
+    A.tol = j->prm.tol;
+    A.step0 = j->prm.step0;
+    A.u = a; a += n;
+    A.g = a; a += n;
+    A.ut = a; a += n;
+    A.dir = a; a += n;
+    A.S = a; a += (size_t)m * n;
+    A.Y = a; a += (size_t)m * n;
+    A.rho = a; a += m;
+    A.alpha = a; a += m;
+    double *Fd = a; a += 2;
+    double *Gd = a;
+    A.F = Fd;
+    A.G = Gd;
+    LbfgsState init{};
+    init.step = 1.0;
+    init.gamma = 1.0;
+    *j->h_state = init;
+    GRAPE_CUDA_TRY(cudaMemcpyAsync(j->d_state, j->h_state, sizeof(LbfgsState), cudaMemcpyHostToDevice, j->stream));
+    GRAPE_CUDA_TRY(cudaMemcpyAsync(A.ut, j->u0.data(), n * sizeof(double), cudaMemcpyHostToDevice, j->stream));
+    GRAPE_CUDA_TRY(cudaStreamSynchronize(j->stream));   // u0 and the pinned state may be reused
+    j->footprint = lb + P->grad_bytes;
+    return GRAPE_OK;
+}
+
+// one iteration: gradient evaluation at ut, then one L-BFGS step
+grape_status launch_iteration(ServerJob *j) {
+    grape_problem *P = j->P;
+    GradScratch S;
+    S.Y = P->d_Y;
+    S.K = P->d_K;
+    S.ckpt = P->d_ckpt;
+    S.x = P->d_x;
+    S.mu = P->d_mu;
+    S.seg = P->seg;
+    S.nseg = P->nseg;
+    S.s2 = P->s2;
+    S.ev = P->ev;
+    grape_status st = run_gradient(P, j->args.ut, const_cast<double *>(j->args.F),
+                                   const_cast<double *>(j->args.G), j->stream, S);
+    if (st != GRAPE_OK) return st;
+    GRAPE_CUDA_TRY(grape_launch_lbfgs(j->args, j->stream));
+    GRAPE_CUDA_TRY(cudaMemcpyAsync(j->h_state, j->d_state, sizeof(LbfgsState), cudaMemcpyDeviceToHost, j->stream));
+    GRAPE_CUDA_TRY(cudaEventRecord(j->ev, j->stream));
+    return GRAPE_OK;
+}
+
+void free_job_device(ServerJob *j) {
+    if (j->stream) cudaStreamSynchronize(j->stream);
+    if (j->ev) cudaEventDestroy(j->ev);
+    if (j->stream) cudaStreamDestroy(j->stream);
+    if (j->d_arena) cudaFree(j->d_arena);
+    if (j->d_state) cudaFree(j->d_state);
+    if (j->h_state) cudaFreeHost(j->h_state);
+    j->ev = nullptr;
+    j->stream = nullptr;
+    j->d_arena = nullptr;
+    j->d_state = nullptr;
+    j->h_state = nullptr;
+    if (j->P) j->P->release_grad();
+}
+
+bool problem_busy(const grape_server *S, const grape_problem *P) {
+    for (const ServerJob *a : S->active)
+        if (a->P == P) return true;
+    return false;
+}
+
+void server_loop(grape_server *S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<ServerJob *> admit;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->active.empty() && S->queue.empty()) {
+                if (S->stop) break;
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+                continue;
+            }
+            // admission: FIFO while slots are free and the estimated footprint fits
+            while (!S->queue.empty() && (int)(S->active.size() + admit.size()) < S->max_slots) {
+                ServerJob *j = S->queue.front();
+                if (problem_busy(S, j->P)) break;
+                // a grid-kernel job occupies every SM with one cooperative grid: it runs alone
+                bool grid_running = false;
+                for (const ServerJob *a : S->active) grid_running = grid_running || a->P->grid;
+                for (const ServerJob *a : admit) grid_running = grid_running || a->P->grid;
+                if (grid_running) break;
+                if (j->P->grid && !(S->active.empty() && admit.empty())) break;
+                const size_t share = S->budget / std::max(1, S->max_slots);
+                const size_t need = std::min(share, seg_bytes(j->P, j->P->n_slices) + lbfgs_bytes(j->n, j->prm.lbfgs_m));
+                if (S->reserved + need > S->budget && !(S->active.empty() && admit.empty())) break;
+                S->queue.pop_front();
+                S->reserved += need;
+                j->reserved = need;
+                admit.push_back(j);
+            }
+        }
+        for (ServerJob *j : admit) {
+            j->t_start = std::chrono::steady_clock::now();
+            grape_status st = start_job(S, j);
+            if (st == GRAPE_OK) st = launch_iteration(j);
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (st != GRAPE_OK) {
+                j->phase = 3;
+                j->err = st;
+                j->err_msg = g_last_error;
+                S->reserved -= j->reserved;
+                free_job_device(j);
+                j->t_done = std::chrono::steady_clock::now();
+                S->cv_done.notify_all();
+            } else {
+                j->phase = 1;
+                S->active.push_back(j);
+            }
+        }
+        bool progressed = !admit.empty();
+        std::vector<ServerJob *> running;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            running = S->active;
+        }
+        for (ServerJob *j : running) {
+            const cudaError_t q = cudaEventQuery(j->ev);
+            if (q == cudaErrorNotReady) continue;
+            progressed = true;
+            grape_status st = GRAPE_OK;
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                st = fail(GRAPE_ECUDA, std::string("served job: ") + cudaGetErrorString(q));
+            } else if (j->P->grid) {
+                st = grape_problem_status(j->P);
+            }
+            if (st == GRAPE_OK && j->h_state->status == 0) {
+                st = launch_iteration(j);
+                if (st == GRAPE_OK) continue;
+            }
+            // finished (or failed): copy the result out and release the slot
+            if (st == GRAPE_OK) {
+                j->u_out.resize(j->n);
+                cudaMemcpy(j->u_out.data(), j->args.u, j->n * sizeof(double), cudaMemcpyDeviceToHost);
+                j->F_out = -j->h_state->f;
+                j->evals = j->h_state->evals;
+            }
+            free_job_device(j);
+            std::lock_guard<std::mutex> lk(S->mu);
+            j->phase = (st == GRAPE_OK) ? 2 : 3;
+            j->err = st;
+            if (st != GRAPE_OK) j->err_msg = g_last_error;
+            j->t_done = std::chrono::steady_clock::now();
+            S->reserved -= j->reserved;
+            S->active.erase(std::find(S->active.begin(), S->active.end(), j));
+            S->cv_done.notify_all();
+        }
+        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+grape_status grape_server_create(size_t hbm_budget_bytes, int32_t max_slots, grape_server_t *out) {
+    if (!out || max_slots < 1) return fail(GRAPE_EINVAL, "NULL output or max_slots < 1");
+    *out = nullptr;
+    grape_server *S = new grape_server();
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete S;
+        return fail(GRAPE_ECUDA, "no CUDA device");
+    }
+    if (hbm_budget_bytes == 0) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            delete S;
+            return fail(GRAPE_ECUDA, "cudaMemGetInfo failed");
+        }
+        hbm_budget_bytes = (size_t)(0.6 * (double)free_b);
+    }
+    S->budget = hbm_budget_bytes;
+    S->max_slots = max_slots;
+    S->worker = std::thread(server_loop, S);
+    *out = S;
+    return GRAPE_OK;
+}
+
+grape_status grape_server_destroy(grape_server_t S) {
+    if (!S) return GRAPE_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        // queued jobs are dropped; running jobs finish
+        for (ServerJob *j : S->queue) {
+            j->phase = 3;
+            j->err = GRAPE_EINVAL;
+            j->err_msg = "server destroyed";
+        }
+        S->queue.clear();
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    delete S;
+    return GRAPE_OK;
+}
+
+grape_status grape_submit(grape_server_t S, grape_problem_t P, const double *u0,
+                          const grape_opt_params *prm, uint64_t *ticket) {
+    if (!S || !P || !u0 || !prm || !ticket) return fail(GRAPE_EINVAL, "NULL argument");
+    if (P->device != S->device) return fail(GRAPE_EINVAL, "problem on another device");
+    if (P->R < 1) return fail(GRAPE_EINVAL, "problem has no controls");
+    if (prm->max_iters < 1 || prm->lbfgs_m < 1 || prm->lbfgs_m > 64 || !(prm->u_max > prm->u_min) ||
+        !(prm->step0 > 0.0) || prm->tol < 0.0)
+        return fail(GRAPE_EINVAL, "bad optimisation parameters");
+    ServerJob *j = new ServerJob();
+    j->P = P;
+    j->prm = *prm;
+    j->n = P->n_slices * P->R;
+    j->u0.assign(u0, u0 + j->n);
+    for (double &v : j->u0) v = std::min(std::max(v, prm->u_min), prm->u_max);
+    j->t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) {
+            delete j;
+            return fail(GRAPE_EBUSY, "server is shutting down");
+        }
+        j->ticket = S->next_ticket++;
+        S->jobs[j->ticket] = j;
+        S->queue.push_back(j);
+        *ticket = j->ticket;
+    }
+    S->cv_work.notify_all();
+    return GRAPE_OK;
+}
+
+grape_status grape_poll(grape_server_t S, uint64_t ticket, int64_t timeout_us, double *u_out,
+                        double *F_out, grape_job_info *info) {
+    if (!S) return fail(GRAPE_EINVAL, "NULL server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->jobs.find(ticket);
+    if (it == S->jobs.end()) return fail(GRAPE_EINVAL, "unknown ticket");
+    ServerJob *j = it->second;
+    if (j->phase < 2 && timeout_us > 0)
+        S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return j->phase >= 2; });
+    if (j->phase < 2) return GRAPE_ENOTREADY;
+    if (j->phase == 3) {
+        const grape_status e = j->err;
+        const std::string msg = j->err_msg;
+        S->jobs.erase(it);
+        delete j;
+        return fail(e, msg.empty() ? "job failed" : msg);
+    }
+    if (u_out) std::memcpy(u_out, j->u_out.data(), j->n * sizeof(double));
+    if (F_out) *F_out = j->F_out;
+    if (info) {
+        using us = std::chrono::duration<double, std::micro>;
+        info->evaluations = j->evals;
+        info->queued_us = us(j->t_start - j->t_submit).count();
+        info->latency_us = us(j->t_done - j->t_submit).count();
+    }
+    S->jobs.erase(it);
+    delete j;
+    return GRAPE_OK;
 }
 
 }  // extern "C"

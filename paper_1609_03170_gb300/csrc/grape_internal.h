@@ -119,3 +119,28 @@ struct TraceArgs {
 
 GRAPE_DECLARE_LAUNCHERS(f64)
 GRAPE_DECLARE_LAUNCHERS(df)
+
+// ---------------------------------------------------------------------------
+// Device state of one projected L-BFGS optimisation (serving loop).
+struct LbfgsState {
+    double f;        // objective -Phi at the accepted point
+    double step;     // step multiplier along the L-BFGS direction
+    double gamma;    // s.y / y.y of the newest curvature pair
+    double pgnorm;   // max-norm of the projected gradient at the accepted point
+    int evals;       // gradient evaluations consumed
+    int accepted;    // accepted points
+    int hist;        // stored curvature pairs
+    int head;        // next ring slot
+    int status;      // 0 running, 1 evaluation budget used, 2 converged or stalled
+    int pad;
+};
+
+struct LbfgsArgs {
+    LbfgsState *state;
+    int n, m, max_evals;
+    double u_min, u_max, tol, step0;
+    const double *F, *G;                         // gradient evaluation at ut
+    double *u, *g, *ut, *dir, *S, *Y, *rho, *alpha;
+};
+
+cudaError_t grape_launch_lbfgs(const LbfgsArgs &a, cudaStream_t s);

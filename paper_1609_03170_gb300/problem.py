@@ -248,3 +248,46 @@ class GrapeBatch:
         _lib.grape_batch_gradient(self._h, [u.data_ptr() for u in us], F.data_ptr(),
                                   [g.data_ptr() for g in grads], _stream_ptr(stream))
         return F, grads
+
+
+class GrapeServer:
+    """Pulse-optimisation service (grape_server_*): submit jobs, poll results.
+
+    Each job maximises Phi of one GrapeProblem with projected L-BFGS on the
+    device; jobs are admitted by device memory and run with continuous
+    batching (see include/grape.h)."""
+
+    def __init__(self, budget_bytes: int = 0, max_slots: int = 16):
+        self._h = _lib.grape_server_create(budget_bytes, max_slots)
+        self._shapes = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.grape_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, problem: "GrapeProblem", u0, max_iters=50, lbfgs_m=10, u_min=-5.0,
+               u_max=5.0, step0=0.5, tol=0.0) -> int:
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        prm = _lib.grape_opt_params(int(max_iters), int(lbfgs_m), float(u_min), float(u_max),
+                                    float(step0), float(tol))
+        t = _lib.grape_submit(self._h, problem.handle, u0, prm)
+        self._shapes[t] = u0.shape
+        return t
+
+    def poll(self, ticket: int, timeout_s: float = 0.0):
+        """None while the job runs, else (u_best, Phi, evaluations, queued_s, latency_s)."""
+        shape = self._shapes[ticket]
+        u = np.zeros(shape)
+        F = np.zeros(1)
+        info = _lib.grape_job_info()
+        if not _lib.grape_poll(self._h, ticket, int(timeout_s * 1e6), u, F, info):
+            return None
+        del self._shapes[ticket]
+        return u, float(F[0]), int(info.evaluations), info.queued_us * 1e-6, info.latency_us * 1e-6
