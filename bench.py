@@ -11,6 +11,17 @@ libgrape.so kernels.
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs its own copy of
 the problem (replicas, weak scaling) and the time is the max over ranks.
+
+Other workloads (measurement cases of the batched, long-pulse and serving
+forms; not the headline line):
+  --workload batch256  the 256-problem batch in one graph-captured launch,
+                       against one-at-a-time gradients of a sample
+  --workload d600      one checkpointed gradient of the d=600 problem
+                       (N_t = 40000, a checkpoint every 200 slices)
+  --workload serve     a Poisson trace of pulse optimisations (50 projected
+                       L-BFGS iterations each) through the serving loop, with
+                       continuous batching and one job at a time
+  --scale s            multiplies every problem's number of slices
 """
 import argparse
 import hashlib
@@ -22,6 +33,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -43,6 +56,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"],
                     help="kernel arithmetic: double-float on FP32 pipes or native FP64")
+    ap.add_argument("--workload", default="d120", choices=["d120", "batch256", "d600", "serve"])
+    ap.add_argument("--scale", type=float, default=None,
+                    help="slice-count multiplier of the batch256/serve/d600 workloads")
+    ap.add_argument("--jobs", type=int, default=64, help="serve: jobs in the trace")
+    ap.add_argument("--sample", type=int, default=32, help="batch256: one-at-a-time sample")
     return ap.parse_args()
 
 
@@ -203,8 +221,185 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+def _base_line(args, workload, value, unit, ms, extra):
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "df64", "data": "synthetic",
+            "config": {"workload": workload}}
+    line.update(extra)
+    return line
+
+
+def run_batch256(args):
+    import torch
+    import workloads
+    from paper_1609_03170_gb300 import GrapeBatch, GrapeProblem, _lib
+    scale = 0.25 if args.scale is None else args.scale
+    ws = []
+    for i in range(256):
+        nt = workloads.batch_problem(i).n_slices
+        ws.append(workloads.batch_problem(i, n_slices=max(4, int(round(nt * scale)))))
+    probs = [GrapeProblem.from_workload(w) for w in ws]
+    us = [torch.from_numpy(w.u).cuda() for w in ws]
+    stream = torch.cuda.Stream()
+    B = GrapeBatch(probs)
+    F = torch.empty(256, dtype=torch.float64, device="cuda")
+    Gs = [torch.empty((w.n_slices, w.n_controls), dtype=torch.float64, device="cuda") for w in ws]
+    for _ in range(max(1, args.warmup)):
+        B.gradient(us, F=F, grads=Gs, stream=stream)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        B.gradient(us, F=F, grads=Gs, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # one problem at a time on one stream, on a sample (every 256/sample-th
+    # problem); each sampled problem gets its own short-lived handle so that
+    # its gradient storage is freed before the next one
+    idx = list(range(0, 256, max(1, 256 // args.sample)))[:args.sample]
+    Fd = torch.empty(1, dtype=torch.float64, device="cuda")
+    seq_sample_ms = 0.0
+    for i in idx:
+        Pi = GrapeProblem.from_workload(ws[i])
+        _lib.grape_gradient(Pi.handle, us[i].data_ptr(), Fd.data_ptr(), Gs[i].data_ptr(),
+                            stream.cuda_stream)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        _lib.grape_gradient(Pi.handle, us[i].data_ptr(), Fd.data_ptr(), Gs[i].data_ptr(),
+                            stream.cuda_stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        seq_sample_ms += ev0.elapsed_time(ev1)
+        Pi.close()
+    work_all = sum(w.n_slices * w.n_states * w.d ** 2 for w in ws)
+    work_sample = sum(ws[i].n_slices * ws[i].n_states * ws[i].d ** 2 for i in idx)
+    seq_ms = seq_sample_ms * work_all / work_sample
+    lanes, scratch, launches = B.info()
+    print(json.dumps(_base_line(args, "batch256", 256 * 1000.0 / ms, UNIT, ms, {
+        "config": {"workload": "batch256", "problems": 256, "slice_scale": scale,
+                   "d_range": [min(w.d for w in ws), max(w.d for w in ws)],
+                   "slices_range": [min(w.n_slices for w in ws), max(w.n_slices for w in ws)],
+                   "lanes": lanes, "scratch_bytes": scratch},
+        "one_at_a_time": {"sample": len(idx), "sample_ms": seq_sample_ms,
+                          "estimated_ms_all": seq_ms,
+                          "value": 256 * 1000.0 / seq_ms, "unit": UNIT,
+                          "estimate": "sample time scaled by (slices x states x d^2) of all / sample"},
+        "speedup_vs_one_at_a_time": seq_ms / ms,
+        "gpu_launches": launches * args.steps})), flush=True)
+
+
+def run_d600(args):
+    import torch
+    import workloads
+    from paper_1609_03170_gb300 import GrapeProblem
+    scale = 1.0 if args.scale is None else args.scale
+    n = max(2, int(round(40000 * scale)))
+    w = workloads.transmon_resonator_d600(n_slices=n)
+    P = GrapeProblem.from_workload(w, ckpt_stride=200)
+    u = torch.from_numpy(w.u).cuda()
+    P.set_profiling(True)
+    for _ in range(args.warmup):
+        P.gradient(u)
+    torch.cuda.synchronize()
+    P.phase_times()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        F, G = P.gradient(u)
+    torch.cuda.synchronize()
+    s = (time.perf_counter() - t0) / args.steps
+    ph = P.phase_times()
+    P.status()
+    print(json.dumps(_base_line(args, "transmon_resonator_d600", 1.0 / s, UNIT, 1000 * s, {
+        "config": {"workload": "transmon_resonator_d600", "d": 600, "n_slices": n, "n_rk": 4,
+                   "n_states": 1, "ckpt_stride": 200, "kernel": P.kernel(),
+                   "device_bytes": P.memory_bytes()},
+        "phases_ms_per_step": {k: v[0] / args.steps for k, v in ph.items()},
+        "gpu_launches": P.gradient_launches() * args.steps})), flush=True)
+
+
+def serve_trace(n_jobs, scale, rate, seed=1609):
+    """Seeded trace: (arrival time, workload); 88% batch-distribution problems,
+    10% d=120 / N_t=2000 problems, 2% d=300 / N_t=10000 problems (slice
+    counts times `scale`)."""
+    import workloads
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
+    out = []
+    for k in range(n_jobs):
+        r = rng.uniform()
+        if r < 0.88:
+            i = int(rng.integers(0, 256))
+            nt = workloads.batch_problem(i).n_slices
+            w = workloads.batch_problem(i, n_slices=max(4, int(round(nt * scale))))
+        elif r < 0.98:
+            w = workloads.transmon_resonator_d120(n_slices=max(4, int(round(2000 * scale))))
+        else:
+            phys = workloads.Physics(Q=3, N=100, chi=(0.0, 1.0, 2.6), kerr=-0.01, kappa=1.0,
+                                     controls=("res_x", "res_y"))
+            nt = max(4, int(round(10000 * scale)))
+            w = workloads.make("d300", phys, T=0.003 * nt, n_slices=nt, n_rk=4,
+                               states=[(0, 2.0), (1, 2.0 + 1.0j), (2, 1.5j)], u_bound=1.0)
+        out.append((float(t[k]), w))
+    return out
+
+
+def run_serve_once(trace, max_slots):
+    from paper_1609_03170_gb300 import GrapeProblem, GrapeServer
+    probs = [GrapeProblem.from_workload(w) for _, w in trace]
+    srv = GrapeServer(max_slots=max_slots)
+    t0 = time.perf_counter()
+    tickets = []
+    pending = {}
+    results = {}
+    k = 0
+    while len(results) < len(trace):
+        now = time.perf_counter() - t0
+        while k < len(trace) and trace[k][0] <= now:
+            tk = srv.submit(probs[k], trace[k][1].u, max_iters=50, lbfgs_m=10,
+                            u_min=-5.0, u_max=5.0)
+            pending[tk] = k
+            k += 1
+        for tk in list(pending):
+            r = srv.poll(tk, timeout_s=0.0)
+            if r is not None:
+                results[pending.pop(tk)] = r
+        time.sleep(0.0005)
+    makespan = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([results[i][4] for i in range(len(trace))])
+    return {"jobs_per_s": len(trace) / makespan, "makespan_s": makespan,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "max_slots": max_slots,
+            "evaluations": int(sum(results[i][2] for i in range(len(trace))))}
+
+
+def run_serve(args):
+    scale = 0.1 if args.scale is None else args.scale
+    trace = serve_trace(args.jobs, scale, 50.0)
+    batched = run_serve_once(trace, 24)
+    serial = run_serve_once(trace, 1)
+    trace08 = serve_trace(args.jobs, scale, 0.8 * batched["jobs_per_s"], seed=1610)
+    at08 = run_serve_once(trace08, 24)
+    print(json.dumps(_base_line(args, "serve", batched["jobs_per_s"], "jobs/s",
+                                1000 * batched["makespan_s"], {
+        "config": {"workload": "serve", "jobs": args.jobs, "arrivals": "Poisson 50 jobs/s",
+                   "slice_scale": scale, "iterations": 50, "box": 5.0,
+                   "mix": "88% batch-distribution, 10% d=120/N_t=2000, 2% d=300/N_t=10000 "
+                          "(slice counts x scale)"},
+        "continuous_batching": batched, "serial_same_gpu": serial,
+        "at_0.8x_capacity": at08,
+        "throughput_vs_serial": batched["jobs_per_s"] / serial["jobs_per_s"]})), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload != "d120":
+        import torch
+        torch.cuda.set_device(0)
+        {"batch256": run_batch256, "d600": run_d600, "serve": run_serve}[args.workload](args)
+        return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -238,23 +433,31 @@ def main():
     stream.synchronize()
     launches_per_step = P.gradient_launches()
 
-    # ---- device-resident timing (value) ------------------------------------
-    P.set_profiling(True)
-    P.phase_times()
+    # ---- device-resident timing (value), no per-launch events -------------
     clocks = ClockSampler(dev)
     clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
     ev0.record(stream)
     for _ in range(args.steps):
         step_device()
     ev1.record(stream)
     torch.cuda.synchronize()
+    wall_ms = 1000.0 * (time.perf_counter() - t_wall) / args.steps
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
+
+    # ---- per-launch durations of each kernel (CUDA events on the launching
+    # streams), a second pass of the same steps -------------------------------
+    P.set_profiling(True)
+    P.phase_times()
+    for _ in range(args.steps):
+        step_device()
+    torch.cuda.synchronize()
     phases = P.phase_times()
     P.set_profiling(False)
 
@@ -350,6 +553,7 @@ def main():
                 "peak_gbs": hbm_peak, "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
         "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+        "wall_ms_per_step": wall_ms,
         "e2e": {"value": world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(u_host.numel() * 8),
                 "d2h_bytes_per_step": int(F_host.numel() * 8 + G_host.numel() * 8)},
