@@ -354,8 +354,12 @@ def run_serve_once(trace, max_slots):
     pending = {}
     results = {}
     k = 0
+    last_report = 0.0
     while len(results) < len(trace):
         now = time.perf_counter() - t0
+        if now - last_report > 10.0:
+            sys.stderr.write(f"serve slots={max_slots}: {now:.0f} s, submitted {k}, done {len(results)}\n")
+            last_report = now
         while k < len(trace) and trace[k][0] <= now:
             tk = srv.submit(probs[k], trace[k][1].u, max_iters=50, lbfgs_m=10,
                             u_min=-5.0, u_max=5.0)

@@ -181,7 +181,8 @@ grape_status grape_gradient_static(grape_problem_t problem, const double *u, dou
  * must not be used concurrently with it. */
 typedef struct grape_batch *grape_batch_t;
 
-/* n_lanes <= 0 picks 24 (capped at n).  Errors: GRAPE_EINVAL, GRAPE_ENOMEM. */
+/* n_lanes <= 0 picks 24 (capped at n).  Errors: GRAPE_EINVAL (NULL pointers,
+ * a problem listed twice, problems on different devices), GRAPE_ENOMEM. */
 grape_status grape_batch_create(grape_problem_t *problems, int32_t n, int32_t n_lanes,
                                 grape_batch_t *out);
 grape_status grape_batch_destroy(grape_batch_t batch);
@@ -200,8 +201,9 @@ grape_status grape_batch_info(grape_batch_t batch, int32_t *n_lanes, size_t *scr
  * evaluation at a trial point followed by one L-BFGS step on the device
  * (decrease of -Phi accepts the point, otherwise the step is halved).  The
  * server keeps every job's controls, gradient and L-BFGS history on the
- * device; a worker thread admits queued jobs whenever a slot is free and
- * their gradient storage fits the memory budget, runs each admitted job on
+ * device; a worker thread admits queued jobs (in order) whenever a slot is
+ * free, their gradient storage fits the memory budget and the SMs their
+ * clusters need (states x cluster width) are not taken, runs each admitted job on
  * its own stream and launches its next iteration as soon as the previous one
  * completes, so iterations of different jobs overlap.  A job's result does
  * not depend on the other jobs (deterministic kernels). */

@@ -230,9 +230,12 @@ struct grape_problem {
     double2 *d_rho0 = nullptr, *d_sigma = nullptr, *d_x = nullptr, *d_mu = nullptr;
     double2 *d_Y = nullptr, *d_K = nullptr, *d_ckpt = nullptr;
     double2 *d_out = nullptr;        // complex128 staging of rho(T)
+    double *d_part = nullptr;        // per-split partial traces [n_slices][npairs][R]
     double *d_u = nullptr, *d_F = nullptr, *d_G = nullptr;
     size_t bytes = 0;
-    cudaStream_t s2 = nullptr;       // trace kernels overlap the adjoint sweep here
+    cudaStream_t s1 = nullptr;       // high-priority stream the gradient sweeps run on
+    cudaStream_t s2 = nullptr;       // low-priority stream: traces overlap the adjoint sweep
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     static constexpr int kMaxChunks = 16;
     cudaEvent_t ev[kMaxChunks + 2] = {};
     bool profiling = false;
@@ -252,9 +255,16 @@ struct grape_problem {
     }
     std::vector<void *> grad_allocs;   // gradient storage, released between served jobs
     size_t grad_bytes = 0;
+    // Served jobs allocate gradient storage stream-ordered from the server's
+    // pool (no device-wide synchronisation when a job starts or ends).
+    cudaStream_t grad_stream = nullptr;
+    cudaMemPool_t grad_pool = nullptr;
     void *alloc_grad(size_t n) {
         void *p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(n, 16)) != cudaSuccess) {
+        const size_t nb = std::max<size_t>(n, 16);
+        const cudaError_t e = grad_pool ? cudaMallocFromPoolAsync(&p, nb, grad_pool, grad_stream)
+                                        : cudaMalloc(&p, nb);
+        if (e != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
@@ -264,8 +274,13 @@ struct grape_problem {
         return p;
     }
     void release_grad() {
-        for (void *p : grad_allocs) cudaFree(p);
+        for (void *p : grad_allocs) {
+            if (grad_pool) cudaFreeAsync(p, grad_stream);
+            else cudaFree(p);
+        }
         grad_allocs.clear();
+        grad_pool = nullptr;
+        grad_stream = nullptr;
         bytes -= grad_bytes;
         grad_bytes = 0;
         d_Y = d_K = d_ckpt = nullptr;
@@ -287,7 +302,11 @@ struct grape_problem {
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
         if (s2) cudaStreamDestroy(s2);
-        for (void *p : grad_allocs) cudaFree(p);
+        if (s1) cudaStreamDestroy(s1);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (!grad_pool)
+            for (void *p : grad_allocs) cudaFree(p);
         for (auto &m : marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
         for (auto e : event_pool) cudaEventDestroy(e);
         for (void *p : allocs) cudaFree(p);
@@ -661,7 +680,23 @@ struct GradScratch {
     int seg = 0, nseg = 0;
     cudaStream_t s2 = nullptr;   // trace stream; null: traces run on the main stream
     cudaEvent_t *ev = nullptr;   // kMaxChunks + 1 events when s2 is set
+    double *part = nullptr;      // partial traces; null: one CTA per slice
 };
+
+long long trace_pairs(const grape_problem *P) {
+    return (P->mode == GRAPE_GRAD_EXACT) ? (long long)P->n_rk * 4 * P->ns : (long long)P->ns;
+}
+
+// Splits of each slice's trace over CTAs, a constant of the problem (so the
+// summation order, and with it every bit of the gradient, does not depend on
+// how the slices are grouped into launches): each split takes a contiguous
+// range of the slice's stage pairs worth about 2^17 band-element products.
+int trace_splits(const grape_problem *P) {
+    const long long npairs = trace_pairs(P);
+    const long long work = (long long)P->d * P->d * std::max(1, P->trace.ndo);
+    const long long per = std::max<long long>(1, ((1LL << 17) + work - 1) / work);
+    return (int)std::max<long long>(1, (npairs + per - 1) / per);
+}
 
 // stage storage of one segment (Y and K) and the checkpoints, in bytes
 size_t stage_bytes(const grape_problem *P, long long seg) {
@@ -697,7 +732,8 @@ int gradient_launch_count(const grape_problem *P, int seg, int nseg) {
         const long long j0 = (long long)gi * seg;
         const long long j1 = std::min<long long>(P->n_slices, j0 + seg);
         const int nch = adjoint_chunks(P, j0, j1);
-        n += (nseg > 1 ? 1 : 0) + nch + (P->R > 0 ? nch : 0);
+        n += (nseg > 1 ? 1 : 0) + nch;
+        if (P->R > 0) n += nch * (P->trace.nsplit > 1 ? 2 : 1);
     }
     return n;
 }
@@ -859,7 +895,15 @@ grape_status run_gradient(grape_problem *P, const double *ud, double *Fd, double
                 t.npairs = P->ns;
                 t.weight = dt;
             }
+            if (!S.part) t.nsplit = 1;
+            t.part = S.part ? S.part + (size_t)cA * t.nsplit * P->R : nullptr;
             if ((st = timed(P, PH_TRACE, ts, [&] { return k_trace(P, t, ts); })) != GRAPE_OK)
+                return st;
+            if (t.nsplit > 1 &&
+                (st = timed(P, PH_TRACE, ts, [&] {
+                     return P->prec == GRAPE_PREC_FP64 ? grape_launch_trace_finish_f64(t, ts)
+                                                       : grape_launch_trace_finish_df(t, ts);
+                 })) != GRAPE_OK)
                 return st;
         }
         if (P->R > 0 && S.s2) {   // the segment's stage storage is reused next: join s2 into s
@@ -1059,16 +1103,26 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
     if ((st = upload(P, cbv, &cb)) != GRAPE_OK) return bail(st);
     tr.cb_val = cb;
     P->trace = tr;
+    P->trace.nsplit = trace_splits(P);
     P->d_x = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
     P->d_mu = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
     P->d_out = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
+    P->d_part = static_cast<double *>(
+        P->alloc((size_t)P->n_slices * P->trace.nsplit * std::max(P->R, 1) * sizeof(double)));
     P->d_u = static_cast<double *>(P->alloc((size_t)P->n_slices * std::max(P->R, 1) * sizeof(double)));
     P->d_F = static_cast<double *>(P->alloc(sizeof(double)));
     P->d_G = static_cast<double *>(P->alloc((size_t)P->n_slices * std::max(P->R, 1) * sizeof(double)));
-    if (!P->d_x || !P->d_mu || !P->d_out || !P->d_u || !P->d_F || !P->d_G) return bail(fail(GRAPE_ENOMEM, "cudaMalloc failed"));
-    if (cudaStreamCreateWithFlags(&P->s2, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        return bail(fail(GRAPE_ECUDA, "cudaStreamCreate failed"));
+    if (!P->d_x || !P->d_mu || !P->d_out || !P->d_part || !P->d_u || !P->d_F || !P->d_G) return bail(fail(GRAPE_ENOMEM, "cudaMalloc failed"));
+    {
+        int prio_low = 0, prio_high = 0;
+        cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+        if (cudaStreamCreateWithPriority(&P->s1, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&P->s2, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(GRAPE_ECUDA, "cudaStreamCreate failed"));
+        }
     }
     for (auto &e : P->ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
@@ -1211,10 +1265,19 @@ grape_status grape_gradient(grape_problem_t P, const double *u, double *F, doubl
     S.mu = P->d_mu;
     S.seg = P->seg;
     S.nseg = P->nseg;
-    S.s2 = P->s2;
     S.ev = P->ev;
-    if ((st = run_gradient(P, ud, f_dev ? F : P->d_F, g_dev ? grad : P->d_G, s, S)) != GRAPE_OK)
+    S.part = P->d_part;
+    bool overlap = true;
+    if (const char *env = std::getenv("GRAPE_TRACE_OVERLAP")) overlap = std::atoi(env) != 0;
+    S.s2 = overlap ? P->s2 : nullptr;
+    // the sweeps run on the problem's high-priority stream, ordered after and
+    // before the caller's stream; the traces on its low-priority stream
+    GRAPE_CUDA_TRY(cudaEventRecord(P->ev_fork, s));
+    GRAPE_CUDA_TRY(cudaStreamWaitEvent(P->s1, P->ev_fork, 0));
+    if ((st = run_gradient(P, ud, f_dev ? F : P->d_F, g_dev ? grad : P->d_G, P->s1, S)) != GRAPE_OK)
         return st;
+    GRAPE_CUDA_TRY(cudaEventRecord(P->ev_join, P->s1));
+    GRAPE_CUDA_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
     bool sync = false;
     if (!f_dev) {
         GRAPE_CUDA_TRY(cudaMemcpyAsync(F, P->d_F, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1347,6 +1410,8 @@ grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F
         else { b.bound_store = K; b.bound_step = P->n_rk; }
         GRAPE_CUDA_TRY(k_prop(P, b, s));
         TraceArgs t = P->trace;
+        t.nsplit = 1;
+        t.part = nullptr;
         t.n_rows = (int)(j1 - j0);
         t.G = grad + (size_t)j0 * P->R;
         if (exact) {
@@ -1418,6 +1483,8 @@ grape_status grape_batch_create(grape_problem_t *problems, int32_t n, int32_t n_
     for (int i = 0; i < n; ++i) {
         if (!problems[i]) return fail(GRAPE_EINVAL, "NULL problem in batch");
         if (problems[i]->device != dev) return fail(GRAPE_EINVAL, "batch problems on different devices");
+        for (int k = 0; k < i; ++k)
+            if (problems[k] == problems[i]) return fail(GRAPE_EINVAL, "a problem appears twice in the batch");
     }
     DeviceGuard g(dev);
     grape_batch *B = new grape_batch();
@@ -1490,6 +1557,7 @@ grape_status grape_batch_create(grape_problem_t *problems, int32_t n, int32_t n_
             S.nseg = (int)((P->n_slices + segs[t] - 1) / segs[t]);
             S.s2 = nullptr;      // lanes already run concurrently: traces stay on the lane
             S.ev = nullptr;
+            S.part = P->d_part;
         }
     }
     B->lanes.resize(B->n_lanes);
@@ -1611,6 +1679,7 @@ struct ServerJob {
     double *d_arena = nullptr;        // u, g, ut, dir, S, Y, rho, alpha, F, G
     LbfgsState *d_state = nullptr;
     LbfgsState *h_state = nullptr;    // pinned copy read by the worker
+    int pinned_slot = -1;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     size_t footprint = 0;             // device bytes the job holds
@@ -1627,8 +1696,13 @@ struct ServerJob {
 
 struct grape_server {
     int device = 0;
+    int n_sms = 0;                      // streaming multiprocessors of the device
+    int sms_in_use = 0;                 // SM demand of the admitted jobs
     size_t budget = 0;
     int max_slots = 1;
+    cudaMemPool_t pool = nullptr;       // device memory of the admitted jobs
+    LbfgsState *pinned = nullptr;       // max_slots status words read by the worker
+    std::vector<int> free_pinned;       // worker-owned
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<ServerJob *> queue;
@@ -1654,15 +1728,26 @@ grape_status start_job(grape_server *S, ServerJob *j) {
     const int n = j->n, m = j->prm.lbfgs_m;
     const size_t share = S->budget / std::max(1, S->max_slots);
     const size_t lb = lbfgs_bytes(n, m);
+    if (cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GRAPE_ECUDA, "job stream creation failed");
+    }
+    if (P->nseg == 0) {            // stream-ordered gradient storage from the server pool
+        P->grad_pool = S->pool;
+        P->grad_stream = j->stream;
+    }
     grape_status st = plan_gradient(P, share > lb ? share - lb : 1);
     if (st != GRAPE_OK) return st;
-    if (cudaMalloc(&j->d_arena, lb) != cudaSuccess || cudaMalloc(&j->d_state, sizeof(LbfgsState)) != cudaSuccess ||
-        cudaMallocHost(&j->h_state, sizeof(LbfgsState)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(&j->d_arena), lb, S->pool, j->stream) != cudaSuccess ||
+        cudaMallocFromPoolAsync(reinterpret_cast<void **>(&j->d_state), sizeof(LbfgsState), S->pool,
+                                j->stream) != cudaSuccess || S->free_pinned.empty()) {
         cudaGetLastError();
         return fail(GRAPE_ENOMEM, "job allocation failed");
     }
+    j->pinned_slot = S->free_pinned.back();
+    S->free_pinned.pop_back();
+    j->h_state = S->pinned + j->pinned_slot;
     double *a = j->d_arena;
     LbfgsArgs &A = j->args;
     A.state = j->d_state;
@@ -1707,8 +1792,9 @@ grape_status launch_iteration(ServerJob *j) {
     S.mu = P->d_mu;
     S.seg = P->seg;
     S.nseg = P->nseg;
-    S.s2 = P->s2;
+    S.s2 = nullptr;                  // served jobs overlap each other, not their traces
     S.ev = P->ev;
+    S.part = P->d_part;
     grape_status st = run_gradient(P, j->args.ut, const_cast<double *>(j->args.F),
                                    const_cast<double *>(j->args.G), j->stream, S);
     if (st != GRAPE_OK) return st;
@@ -1718,19 +1804,29 @@ grape_status launch_iteration(ServerJob *j) {
     return GRAPE_OK;
 }
 
-void free_job_device(ServerJob *j) {
-    if (j->stream) cudaStreamSynchronize(j->stream);
+// Releases a finished job's device state without synchronising the device:
+// frees are ordered on the job's stream.
+void free_job_device(grape_server *S, ServerJob *j) {
+    if (j->stream) {
+        if (j->d_arena) cudaFreeAsync(j->d_arena, j->stream);
+        if (j->d_state) cudaFreeAsync(j->d_state, j->stream);
+        if (j->P && j->P->grad_stream == j->stream) j->P->release_grad();
+        cudaStreamSynchronize(j->stream);   // this stream only
+    }
     if (j->ev) cudaEventDestroy(j->ev);
     if (j->stream) cudaStreamDestroy(j->stream);
-    if (j->d_arena) cudaFree(j->d_arena);
-    if (j->d_state) cudaFree(j->d_state);
-    if (j->h_state) cudaFreeHost(j->h_state);
+    if (j->pinned_slot >= 0) S->free_pinned.push_back(j->pinned_slot);
+    j->pinned_slot = -1;
     j->ev = nullptr;
     j->stream = nullptr;
     j->d_arena = nullptr;
     j->d_state = nullptr;
     j->h_state = nullptr;
-    if (j->P) j->P->release_grad();
+}
+
+int job_sm_demand(const grape_server *S, const ServerJob *j) {
+    const grape_problem *P = j->P;
+    return P->grid ? S->n_sms : std::max(1, P->ns * P->ncl);
 }
 
 bool problem_busy(const grape_server *S, const grape_problem *P) {
@@ -1760,11 +1856,16 @@ void server_loop(grape_server *S) {
                 for (const ServerJob *a : admit) grid_running = grid_running || a->P->grid;
                 if (grid_running) break;
                 if (j->P->grid && !(S->active.empty() && admit.empty())) break;
+                // SM demand: every initial state's cluster needs its own SMs; running
+                // more than fits only makes the clusters wait for free GPCs
+                const int dem = job_sm_demand(S, j);
+                if (S->sms_in_use + dem > S->n_sms && !(S->active.empty() && admit.empty())) break;
                 const size_t share = S->budget / std::max(1, S->max_slots);
                 const size_t need = std::min(share, seg_bytes(j->P, j->P->n_slices) + lbfgs_bytes(j->n, j->prm.lbfgs_m));
                 if (S->reserved + need > S->budget && !(S->active.empty() && admit.empty())) break;
                 S->queue.pop_front();
                 S->reserved += need;
+                S->sms_in_use += dem;
                 j->reserved = need;
                 admit.push_back(j);
             }
@@ -1779,7 +1880,8 @@ void server_loop(grape_server *S) {
                 j->err = st;
                 j->err_msg = g_last_error;
                 S->reserved -= j->reserved;
-                free_job_device(j);
+                S->sms_in_use -= job_sm_demand(S, j);
+                free_job_device(S, j);
                 j->t_done = std::chrono::steady_clock::now();
                 S->cv_done.notify_all();
             } else {
@@ -1811,17 +1913,20 @@ void server_loop(grape_server *S) {
             // finished (or failed): copy the result out and release the slot
             if (st == GRAPE_OK) {
                 j->u_out.resize(j->n);
-                cudaMemcpy(j->u_out.data(), j->args.u, j->n * sizeof(double), cudaMemcpyDeviceToHost);
+                cudaMemcpyAsync(j->u_out.data(), j->args.u, j->n * sizeof(double), cudaMemcpyDeviceToHost,
+                                j->stream);
+                cudaStreamSynchronize(j->stream);
                 j->F_out = -j->h_state->f;
                 j->evals = j->h_state->evals;
             }
-            free_job_device(j);
+            free_job_device(S, j);
             std::lock_guard<std::mutex> lk(S->mu);
             j->phase = (st == GRAPE_OK) ? 2 : 3;
             j->err = st;
             if (st != GRAPE_OK) j->err_msg = g_last_error;
             j->t_done = std::chrono::steady_clock::now();
             S->reserved -= j->reserved;
+            S->sms_in_use -= job_sm_demand(S, j);
             S->active.erase(std::find(S->active.begin(), S->active.end(), j));
             S->cv_done.notify_all();
         }
@@ -1853,6 +1958,20 @@ grape_status grape_server_create(size_t hbm_budget_bytes, int32_t max_slots, gra
     }
     S->budget = hbm_budget_bytes;
     S->max_slots = max_slots;
+    cudaDeviceGetAttribute(&S->n_sms, cudaDevAttrMultiProcessorCount, S->device);
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = S->device;
+    if (cudaMemPoolCreate(&S->pool, &props) != cudaSuccess ||
+        cudaMallocHost(&S->pinned, sizeof(LbfgsState) * max_slots) != cudaSuccess) {
+        cudaGetLastError();
+        delete S;
+        return fail(GRAPE_ECUDA, "server pool creation failed");
+    }
+    unsigned long long keep = ~0ull;   // freed job memory stays in the pool for the next job
+    cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    for (int i = max_slots - 1; i >= 0; --i) S->free_pinned.push_back(i);
     S->worker = std::thread(server_loop, S);
     *out = S;
     return GRAPE_OK;
@@ -1873,6 +1992,12 @@ grape_status grape_server_destroy(grape_server_t S) {
     }
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
+    {
+        DeviceGuard g(S->device);
+        cudaDeviceSynchronize();
+        if (S->pool) cudaMemPoolDestroy(S->pool);
+        if (S->pinned) cudaFreeHost(S->pinned);
+    }
     delete S;
     return GRAPE_OK;
 }

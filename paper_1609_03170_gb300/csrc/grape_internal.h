@@ -98,6 +98,10 @@ struct TraceArgs {
     int n_rows;
     double weight;
     double *G;                  // [n_rows][R]
+    // nsplit > 1: each row's pairs are split over nsplit CTAs writing
+    // part[row][split][R]; trace_finish_kernel adds the splits in order
+    int nsplit;
+    double *part;
 };
 
 // Launchers, one set per number type: _f64 native FP64, _df double-float.
@@ -108,6 +112,7 @@ struct TraceArgs {
     cudaError_t grape_max_active_clusters_##SUFFIX(int threads, int variant, size_t smem,       \
                                                    int ncl, int n_blocks, int *clusters);      \
     cudaError_t grape_launch_trace_##SUFFIX(const TraceArgs &p, cudaStream_t stream);          \
+    cudaError_t grape_launch_trace_finish_##SUFFIX(const TraceArgs &p, cudaStream_t stream);   \
     cudaError_t grape_launch_cost_##SUFFIX(const void *rho, const void *sigma, int n_states,    \
                                            int d2, double *F, cudaStream_t stream);             \
     cudaError_t grape_launch_to_double_##SUFFIX(const void *src, double2 *dst, size_t n,        \

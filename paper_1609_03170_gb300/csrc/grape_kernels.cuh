@@ -757,7 +757,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
     using S = typename Num::store_t;
     extern __shared__ __align__(16) unsigned char tsmem[];
     S *hv = reinterpret_cast<S *>(tsmem);            // [ncb][d] control band values
-    const int row = blockIdx.x;
+    const int nsplit = max(1, p.nsplit);
+    const int row = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
+    const long long q0 = (long long)split * p.npairs / nsplit;
+    const long long q1 = (long long)(split + 1) * p.npairs / nsplit;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int d = p.d;
     const size_t d2 = (size_t)d * d;
@@ -771,7 +774,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
     const S *Yb = static_cast<const S *>(p.Y);
 
 #pragma unroll 1
-    for (long long q = 0; q < p.npairs; ++q) {
+    for (long long q = q0; q < q1; ++q) {
         const size_t moff = ((size_t)row * p.npairs + q) * d2;
         const S *K = Kb + moff;
         const S *Y = Yb + moff;
@@ -812,9 +815,21 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
                 for (int w = 0; w < nwarps; ++w) t += red[c][w];
                 s += t;
             }
-            p.G[(size_t)row * p.R + k] = p.weight * (-2.0 * s);
+            const double v = p.weight * (-2.0 * s);
+            if (nsplit == 1) p.G[(size_t)row * p.R + k] = v;
+            else p.part[((size_t)row * nsplit + split) * p.R + k] = v;
         }
     }
+}
+
+// G[row][k] = sum over the row's splits, in split order (deterministic)
+static __global__ void __launch_bounds__(256) trace_finish_kernel(const TraceArgs p) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= p.n_rows * p.R) return;
+    const int row = idx / p.R, k = idx - row * p.R;
+    double s = 0.0;
+    for (int sp = 0; sp < p.nsplit; ++sp) s += p.part[((size_t)row * p.nsplit + sp) * p.R + k];
+    p.G[(size_t)row * p.R + k] = s;
 }
 
 template <class Num>
@@ -980,7 +995,14 @@ cudaError_t launch_trace(const TraceArgs &p, cudaStream_t s) {
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    trace_kernel<Num><<<p.n_rows, 256, smem, s>>>(p);
+    trace_kernel<Num><<<p.n_rows * max(1, p.nsplit), 256, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_trace_finish(const TraceArgs &p, cudaStream_t s) {
+    if (p.n_rows <= 0 || p.nsplit <= 1) return cudaSuccess;
+    const int n = p.n_rows * p.R;
+    trace_finish_kernel<<<(n + 255) / 256, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -1015,6 +1037,9 @@ cudaError_t launch_to_double(const void *src, double2 *dst, size_t n, cudaStream
     }                                                                                           \
     cudaError_t grape_launch_trace_##SUFFIX(const TraceArgs &p, cudaStream_t s) {               \
         return grape_k::launch_trace<NUM>(p, s);                                                \
+    }                                                                                           \
+    cudaError_t grape_launch_trace_finish_##SUFFIX(const TraceArgs &p, cudaStream_t s) {        \
+        return grape_k::launch_trace_finish(p, s);                                              \
     }                                                                                           \
     cudaError_t grape_launch_cost_##SUFFIX(const void *rho, const void *sigma, int n_states,    \
                                            int d2, double *F, cudaStream_t s) {                 \
