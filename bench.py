@@ -61,6 +61,7 @@ def parse():
                     help="slice-count multiplier of the batch256/serve/d600 workloads")
     ap.add_argument("--jobs", type=int, default=64, help="serve: jobs in the trace")
     ap.add_argument("--sample", type=int, default=32, help="batch256: one-at-a-time sample")
+    ap.add_argument("--lanes", type=int, default=0, help="batch256: concurrent lanes (0 = automatic)")
     return ap.parse_args()
 
 
@@ -234,7 +235,7 @@ def run_batch256(args):
     import torch
     import workloads
     from paper_1609_03170_gb300 import GrapeBatch, GrapeProblem, _lib
-    scale = 0.25 if args.scale is None else args.scale
+    scale = 1.0 if args.scale is None else args.scale
     ws = []
     for i in range(256):
         nt = workloads.batch_problem(i).n_slices
@@ -242,24 +243,14 @@ def run_batch256(args):
     probs = [GrapeProblem.from_workload(w) for w in ws]
     us = [torch.from_numpy(w.u).cuda() for w in ws]
     stream = torch.cuda.Stream()
-    B = GrapeBatch(probs)
-    F = torch.empty(256, dtype=torch.float64, device="cuda")
-    Gs = [torch.empty((w.n_slices, w.n_controls), dtype=torch.float64, device="cuda") for w in ws]
-    for _ in range(max(1, args.warmup)):
-        B.gradient(us, F=F, grads=Gs, stream=stream)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        B.gradient(us, F=F, grads=Gs, stream=stream)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
     # one problem at a time on one stream, on a sample (every 256/sample-th
-    # problem); each sampled problem gets its own short-lived handle so that
-    # its gradient storage is freed before the next one
+    # problem), before the batch takes its lane storage; each sampled problem
+    # gets its own short-lived handle so that its gradient storage is freed
+    # before the next one
     idx = list(range(0, 256, max(1, 256 // args.sample)))[:args.sample]
     Fd = torch.empty(1, dtype=torch.float64, device="cuda")
+    Gs = [torch.empty((w.n_slices, w.n_controls), dtype=torch.float64, device="cuda") for w in ws]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     seq_sample_ms = 0.0
     for i in idx:
         Pi = GrapeProblem.from_workload(ws[i])
@@ -273,6 +264,27 @@ def run_batch256(args):
         torch.cuda.synchronize()
         seq_sample_ms += ev0.elapsed_time(ev1)
         Pi.close()
+    own = [p.geometry()[:2] for p in probs]
+    t0 = time.perf_counter()
+    B = GrapeBatch(probs, n_lanes=args.lanes)    # tunes the tile per d bucket
+    tune_s = time.perf_counter() - t0
+    tiles = {}
+    for w, p, o in zip(ws, probs, own):
+        b = f"d{32 * ((w.d - 1) // 32) + 1}-{32 * ((w.d - 1) // 32 + 1)}"
+        tiles.setdefault(b, set()).add(p.geometry()[:2])
+    tiles = {b: sorted(f"{c}x{t}" for c, t in v) for b, v in sorted(tiles.items())}
+    F = torch.empty(256, dtype=torch.float64, device="cuda")
+    Gs = [torch.empty((w.n_slices, w.n_controls), dtype=torch.float64, device="cuda") for w in ws]
+    for _ in range(max(1, args.warmup)):
+        B.gradient(us, F=F, grads=Gs, stream=stream)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        B.gradient(us, F=F, grads=Gs, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
     work_all = sum(w.n_slices * w.n_states * w.d ** 2 for w in ws)
     work_sample = sum(ws[i].n_slices * ws[i].n_states * ws[i].d ** 2 for i in idx)
     seq_ms = seq_sample_ms * work_all / work_sample
@@ -281,7 +293,8 @@ def run_batch256(args):
         "config": {"workload": "batch256", "problems": 256, "slice_scale": scale,
                    "d_range": [min(w.d for w in ws), max(w.d for w in ws)],
                    "slices_range": [min(w.n_slices for w in ws), max(w.n_slices for w in ws)],
-                   "lanes": lanes, "scratch_bytes": scratch},
+                   "lanes": lanes, "scratch_bytes": scratch,
+                   "tiles_cluster_x_threads": tiles, "batch_create_s": tune_s},
         "one_at_a_time": {"sample": len(idx), "sample_ms": seq_sample_ms,
                           "estimated_ms_all": seq_ms,
                           "value": 256 * 1000.0 / seq_ms, "unit": UNIT,

@@ -125,6 +125,18 @@ grape_status grape_problem_memory(grape_problem_t problem, size_t *bytes);
 grape_status grape_problem_geometry(grape_problem_t problem, int32_t *cluster,
                                     int32_t *threads, int32_t *elems_per_thread);
 
+/* Sets the propagation tile of a cluster-kernel problem: the cluster width
+ * (1, 2, 4, 8 or 16 CTAs per initial state, each CTA owning an equal share
+ * of the state's entries) and the threads per CTA (a multiple of 32 in
+ * [64, 512]).  Every entry is computed by the same arithmetic whatever CTA
+ * or thread owns it, so results do not change, bit for bit; only speed and
+ * the SMs a call occupies do (narrow tiles leave room for other problems,
+ * see grape_batch_create).  Errors: GRAPE_EINVAL (values out of range, a
+ * grid-kernel problem, or a tile whose state window does not fit in shared
+ * memory or of which no cluster can be resident; the tile is unchanged),
+ * GRAPE_ECUDA. */
+grape_status grape_problem_set_tile(grape_problem_t problem, int32_t cluster, int32_t threads);
+
 /* Which propagation kernel the problem runs on: 0 = Hermitian cluster kernel
  * (upper triangle, states in distributed shared memory), 1 = full-matrix
  * cluster kernel, 2 = grid kernel (states in global memory, one cooperative
@@ -170,7 +182,14 @@ grape_status grape_gradient_static(grape_problem_t problem, const double *u, dou
 
 /* ---- Batching: many problems of different sizes in one graph launch ----
  * (the batched form of the hot path; the paper evaluates one problem at a
- * time).  The problems are spread over n_lanes concurrent streams, longest
+ * time).  grape_batch_create first tunes the propagation tile per bucket of
+ * d (32 wide): for the bucket's largest problem it times every tile that
+ * fits (cluster width x threads per CTA, see grape_problem_set_tile) on a
+ * few slices of forward propagation run as concurrent copies, as many as
+ * can be resident at once, and sets the tile of highest throughput on the
+ * bucket's problems (their own tiles come back at grape_batch_destroy;
+ * GRAPE_BATCH_TUNE=0 skips the tuning).  The problems are then spread over
+ * n_lanes concurrent streams, longest
  * first to the least loaded lane; each lane owns stage storage sized for its
  * largest problem (with checkpoint segments that keep every lane within an
  * equal share of 60% of the free device memory) and runs its problems one
@@ -181,7 +200,9 @@ grape_status grape_gradient_static(grape_problem_t problem, const double *u, dou
  * must not be used concurrently with it. */
 typedef struct grape_batch *grape_batch_t;
 
-/* n_lanes <= 0 picks 24 (capped at n).  Errors: GRAPE_EINVAL (NULL pointers,
+/* n_lanes <= 0 picks the work-weighted mean number of copies of the
+ * batch's problems that can be resident at once (at least 8, at most 128,
+ * capped at n).  Errors: GRAPE_EINVAL (NULL pointers,
  * a problem listed twice, problems on different devices), GRAPE_ENOMEM. */
 grape_status grape_batch_create(grape_problem_t *problems, int32_t n, int32_t n_lanes,
                                 grape_batch_t *out);

@@ -55,7 +55,7 @@ class GrapeError(RuntimeError):
 _lib = None
 
 EXPORTS = ["grape_problem_create", "grape_problem_destroy", "grape_forward", "grape_gradient",
-           "grape_problem_memory", "grape_problem_geometry", "grape_set_profiling",
+           "grape_problem_memory", "grape_problem_geometry", "grape_problem_set_tile", "grape_set_profiling",
            "grape_phase_times", "grape_gradient_launches", "grape_gradient_static",
            "grape_batch_create", "grape_batch_destroy", "grape_batch_gradient", "grape_batch_info",
            "grape_problem_kernel", "grape_problem_status", "grape_server_create",
@@ -114,6 +114,8 @@ def load(build_if_missing: bool = True):
     lib.grape_problem_memory.restype = c_int32
     lib.grape_problem_geometry.argtypes = [c_void_p, P(c_int32), P(c_int32), P(c_int32)]
     lib.grape_problem_geometry.restype = c_int32
+    lib.grape_problem_set_tile.argtypes = [c_void_p, c_int32, c_int32]
+    lib.grape_problem_set_tile.restype = c_int32
     lib.grape_set_profiling.argtypes = [c_void_p, c_int32]
     lib.grape_set_profiling.restype = c_int32
     lib.grape_phase_times.argtypes = [c_void_p, P(c_double), P(c_int32)]
@@ -241,6 +243,10 @@ def grape_problem_geometry(h):
     check(load().grape_problem_geometry(h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(e)),
           "grape_problem_geometry")
     return int(c.value), int(t.value), int(e.value)
+
+
+def grape_problem_set_tile(h, cluster: int, threads: int) -> None:
+    check(load().grape_problem_set_tile(h, int(cluster), int(threads)), "grape_problem_set_tile")
 
 
 def grape_set_profiling(h, on: bool) -> None:

@@ -14,8 +14,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <complex>
@@ -214,6 +216,9 @@ struct grape_problem {
     int ncl = 1, threads = GRAPE_PROP_THREADS, chunk = 0, halo = 0, win = 0, reach = 0;
     int variant = 0;                 // bit 0 = real jump tables, bit 1 = Hermitian kernel
     int hb = 0, cu = 0, maxwin = 0, htab_len = 0, rt_rows = 0;   // Hermitian kernel geometry
+    int omax = 0;                    // largest band offset of either Lindbladian
+    int hb_h = 0;                    // lower entries the Hermitian stencil reads
+    std::map<int, int *> htabs;      // Hermitian tables per cluster width
     bool grid = false;               // grid kernel (state windows in global memory)
     int nblocks = 0, ce = 0;         // its CTAs and entries per CTA
     long long spin_limit = 1LL << 22;   // grid-barrier polls (~0.3 s) before giving up
@@ -398,54 +403,90 @@ double2 encode(const grape_problem *P, cplx v) {
     return out;
 }
 
-grape_status choose_geometry(grape_problem *P, int omax) {
-    int max_smem = 0;
-    GRAPE_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+int max_smem_optin(const grape_problem *P) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
+
+// True when at least one cluster of `ncl` CTAs of `threads` threads and
+// `smem` bytes of dynamic shared memory can be resident.
+bool cluster_fits(const grape_problem *P, int variant, int threads, size_t smem, int ncl) {
+    int clusters = 0;
+    const cudaError_t e =
+        P->prec == GRAPE_PREC_FP64
+            ? grape_max_active_clusters_f64(threads, variant, smem, ncl, ncl * P->ns, &clusters)
+            : grape_max_active_clusters_df(threads, variant, smem, ncl, ncl * P->ns, &clusters);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return clusters >= 1;
+}
+
+// Full-matrix cluster kernel with `ncl` CTAs of `threads` threads per state:
+// sets the geometry, or GRAPE_EINVAL when the tile does not fit.
+grape_status plan_full(grape_problem *P, int ncl, int threads) {
+    const int max_smem = max_smem_optin(P);
     const long long d2 = (long long)P->d2;
-    P->halo = omax * (P->d + 1);
+    const int halo = P->omax * (P->d + 1);
     const int nb = std::max(P->tab[0].nb, P->tab[1].nb), nt = std::max(P->tab[0].nt, P->tab[1].nt);
-    int start = std::min(16, pow2ceil((d2 + 1023) / 1024));
+    const int chunk = (int)((d2 + ncl - 1) / ncl);
+    const int win = chunk + 2 * halo;
+    // windows, base values and accumulators, bands, jump tables (16 B each),
+    // the (row, column) table of the owned entries and 12 RK coefficients
+    const size_t smem = ((size_t)2 * win + 2 * (size_t)chunk + 2 * (size_t)nb * P->d +
+                         2 * (size_t)nt * P->d) * sizeof(double2) +
+                        (size_t)chunk * sizeof(int2) + 12 * sizeof(double);
+    const int variant = P->variant & 1;
+    if (smem + 1024 > (size_t)max_smem)   // keep room for static shared memory
+        return fail(GRAPE_EINVAL, "state window does not fit in shared memory");
+    if (!cluster_fits(P, variant, threads, smem, ncl))
+        return fail(GRAPE_EINVAL, "no cluster of this shape can be resident");
+    P->variant = variant;
+    P->ncl = ncl;
+    P->halo = halo;
+    P->chunk = chunk;
+    P->win = win;
+    P->smem = smem;
+    P->threads = threads;
+    P->reach = (ncl > 1) ? (halo + chunk - 1) / chunk : 0;
+    return GRAPE_OK;
+}
+
+// Preferred width first, then wider, then narrower (bounded search).
+int candidate_widths(int start, int *widths) {
+    int nw = 0;
+    for (int c = start; c <= 16; c *= 2) widths[nw++] = c;
+    for (int c = start / 2; c >= 1; c /= 2) widths[nw++] = c;
+    return nw;
+}
+
+int env_cluster(int start) {
     if (const char *env = std::getenv("GRAPE_CLUSTER")) {
         const int v = std::atoi(env);
-        if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) start = v;
+        if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) return v;
     }
-    cudaError_t e = P->prec == GRAPE_PREC_FP64 ? grape_prepare_prop_f64(P->variant, (size_t)max_smem, 16)
-                                               : grape_prepare_prop_df(P->variant, (size_t)max_smem, 16);
+    return start;
+}
+
+grape_status choose_geometry(grape_problem *P) {
+    const long long d2 = (long long)P->d2;
+    const int start = env_cluster(std::min(16, pow2ceil((d2 + 1023) / 1024)));
+    cudaError_t e = P->prec == GRAPE_PREC_FP64
+                        ? grape_prepare_prop_f64(P->variant & 1, (size_t)max_smem_optin(P), 16)
+                        : grape_prepare_prop_df(P->variant & 1, (size_t)max_smem_optin(P), 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(GRAPE_ECUDA, std::string("prop kernel attributes: ") + cudaGetErrorString(e));
     }
-    // candidate cluster widths: the preferred one and wider, then narrower (bounded search)
-    int widths[8], nw = 0;
-    for (int c = start; c <= 16; c *= 2) widths[nw++] = c;
-    for (int c = start / 2; c >= 1; c /= 2) widths[nw++] = c;
-    for (int wi = 0; wi < nw; ++wi) {
-        const int ncl = widths[wi];
-        const int chunk = (int)((d2 + ncl - 1) / ncl);
-        const int win = chunk + 2 * P->halo;
-        // windows, base values and accumulators, bands, jump tables (16 B each),
-        // the (row, column) table of the owned entries and 12 RK coefficients
-        const size_t smem = ((size_t)2 * win + 2 * (size_t)chunk + 2 * (size_t)nb * P->d +
-                             2 * (size_t)nt * P->d) * sizeof(double2) +
-                            (size_t)chunk * sizeof(int2) + 12 * sizeof(double);
-        if (smem + 1024 > (size_t)max_smem) continue;   // keep room for static shared memory
-        int clusters = 0;
-        e = P->prec == GRAPE_PREC_FP64
-                ? grape_max_active_clusters_f64(GRAPE_PROP_THREADS, P->variant, smem, ncl, ncl * P->ns, &clusters)
-                : grape_max_active_clusters_df(GRAPE_PROP_THREADS, P->variant, smem, ncl, ncl * P->ns, &clusters);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        if (clusters < 1) continue;
-        P->ncl = ncl;
-        P->chunk = chunk;
-        P->win = win;
-        P->smem = smem;
-        P->threads = GRAPE_PROP_THREADS;
-        P->reach = (ncl > 1) ? (P->halo + chunk - 1) / chunk : 0;
-        return GRAPE_OK;
-    }
+    int widths[8];
+    const int nw = candidate_widths(start, widths);
+    for (int wi = 0; wi < nw; ++wi)
+        if (plan_full(P, widths[wi], GRAPE_PROP_THREADS) == GRAPE_OK) return GRAPE_OK;
     return fail(GRAPE_EINVAL, "problem too large for the cluster propagation kernel "
                               "(state window does not fit in shared memory)");
 }
@@ -516,63 +557,64 @@ std::vector<int> hermitian_table(int d, int ncl, int omax, int hb, int *maxwin, 
     return tab;
 }
 
-grape_status choose_geometry_h(grape_problem *P, int omax, int hb) {
-    int max_smem = 0;
-    GRAPE_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
-    const int d = P->d;
-    const long long NU = (long long)d * (d + 1) / 2;
+// Hermitian cluster kernel with `ncl` CTAs of `threads` threads per state:
+// sets the geometry, or GRAPE_EINVAL when the tile does not fit.  Tables
+// are kept per width (a captured graph may still use an earlier one).
+grape_status plan_h(grape_problem *P, int ncl, int threads) {
+    const int max_smem = max_smem_optin(P);
+    const int d = P->d, hb = P->hb_h;
     const int nb = std::max(P->tab[0].nb, P->tab[1].nb), nt = std::max(P->tab[0].nt, P->tab[1].nt);
-    int start = std::min(16, pow2ceil((NU + 511) / 512));
-    if (const char *env = std::getenv("GRAPE_CLUSTER")) {
-        const int v = std::atoi(env);
-        if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16) start = v;
+    int maxwin = 0, cu = 0, rt_rows = 0;
+    const std::vector<int> tab = hermitian_table(d, ncl, P->omax, hb, &maxwin, &cu, &rt_rows);
+    if (maxwin >= 32768) return fail(GRAPE_EINVAL, "state window too large for 16-bit addresses");
+    const size_t smem = ((size_t)2 * maxwin + 2 * (size_t)cu + 2 * (size_t)nb * d +
+                         2 * (size_t)nt * d) * sizeof(double2) +
+                        (size_t)cu * sizeof(int2) + 12 * sizeof(double) + tab.size() * sizeof(int) +
+                        (size_t)rt_rows * (ncl + 1) * sizeof(uint32_t) +
+                        (size_t)cu * (2 * nb + nt + 1) * sizeof(short);
+    const int variant = (P->variant & 1) | 2;
+    if (smem + 1024 > (size_t)max_smem) return fail(GRAPE_EINVAL, "state window does not fit in shared memory");
+    if (!cluster_fits(P, variant, threads, smem, ncl))
+        return fail(GRAPE_EINVAL, "no cluster of this shape can be resident");
+    auto it = P->htabs.find(ncl);
+    if (it == P->htabs.end()) {
+        int *dt = nullptr;
+        grape_status st = upload(P, tab, &dt);
+        if (st != GRAPE_OK) return st;
+        it = P->htabs.emplace(ncl, dt).first;
     }
-    const int variant = P->variant | 2;
-    cudaError_t e = P->prec == GRAPE_PREC_FP64 ? grape_prepare_prop_f64(variant, (size_t)max_smem, 16)
-                                               : grape_prepare_prop_df(variant, (size_t)max_smem, 16);
+    P->d_htab = it->second;
+    P->variant = variant;
+    P->ncl = ncl;
+    P->cu = cu;
+    P->maxwin = maxwin;
+    P->hb = hb;
+    P->htab_len = (int)tab.size();
+    P->rt_rows = rt_rows;
+    P->smem = smem;
+    P->threads = threads;
+    P->chunk = cu;
+    P->halo = 0;
+    P->win = maxwin;
+    P->reach = 0;
+    return GRAPE_OK;
+}
+
+grape_status choose_geometry_h(grape_problem *P) {
+    const long long NU = (long long)P->d * (P->d + 1) / 2;
+    const int start = env_cluster(std::min(16, pow2ceil((NU + 511) / 512)));
+    const int variant = (P->variant & 1) | 2;
+    cudaError_t e = P->prec == GRAPE_PREC_FP64 ? grape_prepare_prop_f64(variant, (size_t)max_smem_optin(P), 16)
+                                               : grape_prepare_prop_df(variant, (size_t)max_smem_optin(P), 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(GRAPE_ECUDA, std::string("hermitian kernel attributes: ") + cudaGetErrorString(e));
     }
-    int widths[8], nw = 0;
-    for (int c = start; c <= 16; c *= 2) widths[nw++] = c;
-    for (int c = start / 2; c >= 1; c /= 2) widths[nw++] = c;
+    int widths[8];
+    const int nw = candidate_widths(start, widths);
     for (int wi = 0; wi < nw; ++wi) {
-        const int ncl = widths[wi];
-        int maxwin = 0, cu = 0, rt_rows = 0;
-        const std::vector<int> tab = hermitian_table(d, ncl, omax, hb, &maxwin, &cu, &rt_rows);
-        if (maxwin >= 32768) continue;   // neighbour addresses are 16-bit
-        const size_t smem = ((size_t)2 * maxwin + 2 * (size_t)cu + 2 * (size_t)nb * d +
-                             2 * (size_t)nt * d) * sizeof(double2) +
-                            (size_t)cu * sizeof(int2) + 12 * sizeof(double) + tab.size() * sizeof(int) +
-                            (size_t)rt_rows * (ncl + 1) * sizeof(uint32_t) +
-                            (size_t)cu * (2 * nb + nt + 1) * sizeof(short);
-        if (smem + 1024 > (size_t)max_smem) continue;
-        int clusters = 0;
-        e = P->prec == GRAPE_PREC_FP64
-                ? grape_max_active_clusters_f64(GRAPE_PROP_THREADS, variant, smem, ncl, ncl * P->ns, &clusters)
-                : grape_max_active_clusters_df(GRAPE_PROP_THREADS, variant, smem, ncl, ncl * P->ns, &clusters);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        if (clusters < 1) continue;
-        grape_status st = upload(P, tab, &P->d_htab);
-        if (st != GRAPE_OK) return st;
-        P->variant = variant;
-        P->ncl = ncl;
-        P->cu = cu;
-        P->maxwin = maxwin;
-        P->hb = hb;
-        P->htab_len = (int)tab.size();
-        P->rt_rows = rt_rows;
-        P->smem = smem;
-        P->threads = GRAPE_PROP_THREADS;
-        P->chunk = cu;
-        P->halo = 0;
-        P->win = maxwin;
-        P->reach = 0;
-        return GRAPE_OK;
+        const grape_status st = plan_h(P, widths[wi], GRAPE_PROP_THREADS);
+        if (st == GRAPE_OK || st != GRAPE_EINVAL) return st;
     }
     return fail(GRAPE_EINVAL, "problem too large for the Hermitian cluster kernel");
 }
@@ -1081,13 +1123,15 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
     bool herm = kern == "auto" || kern == "cluster";
     if (const char *env = std::getenv("GRAPE_HERMITIAN")) herm = herm && std::atoi(env) != 0;
     bool placed = false;
+    P->omax = omax;
+    P->hb_h = hb;
     if (kern != "grid" && herm) {
-        st = choose_geometry_h(P, omax, hb);
+        st = choose_geometry_h(P);
         if (st != GRAPE_OK && st != GRAPE_EINVAL) return bail(st);
         placed = (st == GRAPE_OK);
     }
     if (kern != "grid" && !placed) {
-        st = choose_geometry(P, omax);
+        st = choose_geometry(P);
         if (st != GRAPE_OK && st != GRAPE_EINVAL) return bail(st);
         placed = (st == GRAPE_OK);
     }
@@ -1153,6 +1197,17 @@ grape_status grape_problem_geometry(grape_problem_t P, int32_t *cluster, int32_t
     if (threads) *threads = P->threads;
     if (ept) *ept = (P->chunk + P->threads - 1) / P->threads;
     return GRAPE_OK;
+}
+
+grape_status grape_problem_set_tile(grape_problem_t P, int32_t cluster, int32_t threads) {
+    if (!P) return fail(GRAPE_EINVAL, "NULL problem");
+    if (!(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8 || cluster == 16))
+        return fail(GRAPE_EINVAL, "cluster width must be 1, 2, 4, 8 or 16");
+    if (threads < 64 || threads > GRAPE_PROP_THREADS || threads % 32 != 0)
+        return fail(GRAPE_EINVAL, "threads per CTA must be a multiple of 32 in [64, 512]");
+    if (P->grid) return fail(GRAPE_EINVAL, "the grid kernel has no tile to set");
+    DeviceGuard g(P->device);
+    return (P->variant & 2) ? plan_h(P, cluster, threads) : plan_full(P, cluster, threads);
 }
 
 grape_status grape_problem_status(grape_problem_t P) {
@@ -1449,6 +1504,8 @@ struct grape_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<const void *> key;             // pointers the graph was captured with
+    std::vector<int2> own_tile;                // (width, threads) before tuning; x = 0: unchanged
+    std::vector<double> copies;                // per problem: copies of it resident at once
     ~grape_batch() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -1463,6 +1520,143 @@ struct grape_batch {
 };
 
 namespace {
+
+// Clusters of the problem's current tile that can be resident at once.
+int resident_clusters(const grape_problem *P) {
+    int clusters = 0;
+    const cudaError_t e =
+        P->prec == GRAPE_PREC_FP64
+            ? grape_max_active_clusters_f64(P->threads, P->variant, P->smem, P->ncl, P->ncl * P->ns, &clusters)
+            : grape_max_active_clusters_df(P->threads, P->variant, P->smem, P->ncl, P->ncl * P->ns, &clusters);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return std::max(1, clusters);
+}
+
+// Tile autotuner.  Problems are grouped into buckets of d (32 wide).  For
+// each bucket the largest problem stands in for the rest: for every tile
+// (cluster width x threads per CTA) that fits it, a forward propagation of
+// a few slices runs as C concurrent copies, C = the copies whose clusters
+// can be resident at once (at most kMaxCopies), and the tile with the most
+// slices per second over all copies wins.  It is then set on every problem
+// of the bucket it fits (results do not depend on the tile).
+constexpr int kMaxCopies = 64;
+constexpr int kProbeSlices = 32;
+
+grape_status tune_batch(grape_batch *B) {
+    const int n = (int)B->probs.size();
+    B->own_tile.assign(n, make_int2(0, 0));
+    B->copies.assign(n, 1.0);
+    std::map<int, std::vector<int>> buckets;
+    for (int i = 0; i < n; ++i)
+        if (!B->probs[i]->grid) buckets[(B->probs[i]->d - 1) / 32].push_back(i);
+    if (buckets.empty()) return GRAPE_OK;
+    size_t out_bytes = 16, u_bytes = 16;
+    for (auto &kv : buckets)
+        for (int i : kv.second) {
+            const grape_problem *P = B->probs[i];
+            out_bytes = std::max(out_bytes, (size_t)kMaxCopies * P->ns * P->d2 * sizeof(double2));
+            u_bytes = std::max(u_bytes, (size_t)kProbeSlices * std::max(P->R, 1) * sizeof(double));
+        }
+    void *out = nullptr, *u = nullptr;
+    std::vector<cudaStream_t> ss(kMaxCopies, nullptr);
+    std::vector<cudaEvent_t> done(kMaxCopies, nullptr);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&] {
+        for (auto x : ss) if (x) cudaStreamDestroy(x);
+        for (auto x : done) if (x) cudaEventDestroy(x);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (out) cudaFree(out);
+        if (u) cudaFree(u);
+    };
+    if (cudaMalloc(&out, out_bytes) != cudaSuccess || cudaMalloc(&u, u_bytes) != cudaSuccess ||
+        cudaMemset(u, 0, u_bytes) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(GRAPE_ENOMEM, "tile tuner: probe buffers");
+    }
+    for (int k = 0; k < kMaxCopies; ++k)
+        if (cudaStreamCreateWithFlags(&ss[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            return fail(GRAPE_ECUDA, "tile tuner: streams");
+        }
+    // C copies of P's first kProbeSlices slices; milliseconds of the wave
+    auto probe = [&](grape_problem *P, int C, float *ms) -> grape_status {
+        PropArgs a = base_args(P, 0, static_cast<const double *>(u));
+        a.sub_begin = 0;
+        a.sub_end = (long long)std::min(kProbeSlices, P->n_slices) * P->n_rk;
+        a.x_in = P->d_rho0;
+        GRAPE_CUDA_TRY(cudaEventRecord(e0, ss[0]));
+        for (int k = 0; k < C; ++k) {
+            if (k) GRAPE_CUDA_TRY(cudaStreamWaitEvent(ss[k], e0, 0));
+            a.x_out = static_cast<double2 *>(out) + (size_t)k * P->ns * P->d2;
+            GRAPE_CUDA_TRY(k_prop(P, a, ss[k]));
+            GRAPE_CUDA_TRY(cudaEventRecord(done[k], ss[k]));
+            GRAPE_CUDA_TRY(cudaStreamWaitEvent(ss[0], done[k], 0));
+        }
+        GRAPE_CUDA_TRY(cudaEventRecord(e1, ss[0]));
+        GRAPE_CUDA_TRY(cudaEventSynchronize(e1));
+        GRAPE_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+        return GRAPE_OK;
+    };
+    static const int kThreads[3] = {128, 256, 512};
+    grape_status st = GRAPE_OK;
+    for (auto &kv : buckets) {
+        std::vector<int> &idx = kv.second;
+        int rep = idx[0];
+        for (int i : idx) {
+            const grape_problem *a = B->probs[i], *b = B->probs[rep];
+            if (a->d > b->d || (a->d == b->d && a->ns > b->ns)) rep = i;
+        }
+        grape_problem *R = B->probs[rep];
+        const int2 own = make_int2(R->ncl, R->threads);
+        double best = -1.0;
+        int2 tile = own;
+        for (int w = 1; w <= 16 && st == GRAPE_OK; w *= 2)
+            for (int t : kThreads) {
+                const grape_status ps = grape_problem_set_tile(R, w, t);
+                if (ps == GRAPE_EINVAL) continue;
+                if (ps != GRAPE_OK) { st = ps; break; }
+                const int C = std::max(1, std::min(kMaxCopies, resident_clusters(R) / R->ns));
+                float ms = 0.0f, ms2 = 0.0f;
+                if ((st = probe(R, C, &ms)) != GRAPE_OK || (st = probe(R, C, &ms2)) != GRAPE_OK) break;
+                const double rate = C / (double)std::max(1e-3f, std::min(ms, ms2));
+                if (std::getenv("GRAPE_TUNE_LOG"))
+                    std::fprintf(stderr, "tile d=%d states=%d cluster=%d threads=%d copies=%d ms=%.3f rate=%.1f\n",
+                                 R->d, R->ns, w, t, C, std::min(ms, ms2), rate);
+                if (rate > best) { best = rate; tile = make_int2(w, t); }
+            }
+        if (st == GRAPE_OK) st = grape_problem_set_tile(R, own.x, own.y);   // back before the sweep below
+        if (st != GRAPE_OK) break;
+        for (int i : idx) {
+            grape_problem *P = B->probs[i];
+            const int2 mine = make_int2(P->ncl, P->threads);
+            if (tile.x == mine.x && tile.y == mine.y) {
+                B->copies[i] = std::max(1, std::min(kMaxCopies, resident_clusters(P) / P->ns));
+                continue;
+            }
+            const grape_status ps = grape_problem_set_tile(P, tile.x, tile.y);
+            if (ps == GRAPE_OK) B->own_tile[i] = mine;
+            else if (ps != GRAPE_EINVAL) { st = ps; break; }
+            B->copies[i] = std::max(1, std::min(kMaxCopies, resident_clusters(P) / P->ns));
+        }
+        if (st != GRAPE_OK) break;
+    }
+    cudaDeviceSynchronize();
+    cleanup();
+    return st;
+}
+
+void restore_tiles(grape_batch *B) {
+    for (size_t i = 0; i < B->own_tile.size(); ++i)
+        if (B->own_tile[i].x > 0) grape_problem_set_tile(B->probs[i], B->own_tile[i].x, B->own_tile[i].y);
+}
 
 // rough device time of one gradient, for the longest-first lane assignment
 double gradient_cost(const grape_problem *P) {
@@ -1488,10 +1682,35 @@ grape_status grape_batch_create(grape_problem_t *problems, int32_t n, int32_t n_
     }
     DeviceGuard g(dev);
     grape_batch *B = new grape_batch();
-    auto bail = [&](grape_status s) { delete B; return s; };
+    auto bail = [&](grape_status s) { restore_tiles(B); delete B; return s; };
     B->device = dev;
     B->probs.assign(problems, problems + n);
-    B->n_lanes = std::max(1, std::min<int>(n_lanes > 0 ? n_lanes : 24, n));
+    bool tune = true;
+    if (const char *env = std::getenv("GRAPE_BATCH_TUNE")) tune = std::atoi(env) != 0;
+    if (tune) {
+        const grape_status st = tune_batch(B);
+        if (st != GRAPE_OK) return bail(st);
+    } else {
+        B->own_tile.assign(n, make_int2(0, 0));
+        B->copies.assign(n, 1.0);
+        for (int i = 0; i < n; ++i)
+            if (!B->probs[i]->grid)
+                B->copies[i] = std::max(1, std::min(kMaxCopies, resident_clusters(B->probs[i]) / B->probs[i]->ns));
+    }
+    // lanes: as many as problems of the mix can run at once (work-weighted
+    // mean of the resident copies), at least 8
+    int lanes = n_lanes;
+    if (lanes <= 0) {
+        double wsum = 0.0, csum = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double c = gradient_cost(B->probs[i]);
+            wsum += c;
+            csum += c * B->copies[i];
+        }
+        lanes = std::max(8, (int)std::lround(wsum > 0.0 ? csum / wsum : 8.0));
+        lanes = std::min(lanes, 128);
+    }
+    B->n_lanes = std::max(1, std::min<int>(lanes, n));
     // longest-first assignment to the least loaded lane
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
@@ -1583,6 +1802,7 @@ grape_status grape_batch_create(grape_problem_t *problems, int32_t n, int32_t n_
 grape_status grape_batch_destroy(grape_batch_t B) {
     if (!B) return GRAPE_OK;
     DeviceGuard g(B->device);
+    restore_tiles(B);
     delete B;
     return GRAPE_OK;
 }

@@ -161,6 +161,11 @@ class GrapeProblem:
     def geometry(self):
         return _lib.grape_problem_geometry(self._h)
 
+    def set_tile(self, cluster: int, threads: int) -> None:
+        """Cluster width and threads per CTA of the propagation kernel
+        (results do not change, bit for bit)."""
+        _lib.grape_problem_set_tile(self._h, cluster, threads)
+
     def gradient_launches(self) -> int:
         return _lib.grape_gradient_launches(self._h)
 

@@ -116,3 +116,8 @@ def test_create_without_gpu_reports_cuda_error():
     with pytest.raises(_lib.GrapeError) as e:
         problem.GrapeProblem.from_workload(w)
     assert e.value.status in (_lib.GRAPE_ECUDA, _lib.GRAPE_ENOMEM)
+
+
+def test_set_tile_validates_on_the_host():
+    lib = _lib.load()
+    assert lib.grape_problem_set_tile(None, 4, 128) == _lib.GRAPE_EINVAL

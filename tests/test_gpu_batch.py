@@ -37,6 +37,37 @@ def test_batch_equals_individual_gradients(torch_cuda, lanes):
             assert np.array_equal(Gs[i].cpu().numpy(), Gr)
 
 
+def test_tuner_sets_fitting_tiles_and_restores_them(torch_cuda, monkeypatch):
+    """The tuner gives problems of one d bucket the same tile, results keep
+    every bit, and destroying the batch gives each problem its own tile back."""
+    from paper_1609_03170_gb300 import GrapeBatch, GrapeProblem
+    ws = batch_workloads(8, [10, 17])
+    probs = [GrapeProblem.from_workload(w) for w in ws]
+    own = [p.geometry()[:2] for p in probs]
+    refs = [p.gradient(w.u) for p, w in zip(probs, ws)]
+    B = GrapeBatch(probs)
+    tiles = [p.geometry()[:2] for p in probs]
+    buckets = {}
+    for w, t, o in zip(ws, tiles, own):
+        if t != o:                                  # a tuned problem carries its bucket's tile
+            buckets.setdefault((w.d - 1) // 32, set()).add(t)
+    assert all(len(v) == 1 for v in buckets.values())
+    lanes, _, _ = B.info()
+    assert 1 <= lanes <= len(probs)
+    us = [torch_cuda.from_numpy(w.u).cuda() for w in ws]
+    F, Gs = B.gradient(us)
+    torch_cuda.cuda.synchronize()
+    for i, (Fr, Gr) in enumerate(refs):
+        assert F[i].item() == Fr and np.array_equal(Gs[i].cpu().numpy(), Gr)
+        assert probs[i].gradient(ws[i].u)[0] == Fr          # alone, on the tuned tile
+    B.close()
+    assert [p.geometry()[:2] for p in probs] == own
+    monkeypatch.setenv("GRAPE_BATCH_TUNE", "0")
+    B2 = GrapeBatch(probs)
+    assert [p.geometry()[:2] for p in probs] == own
+    B2.close()
+
+
 def test_batch_replay_sees_new_values_and_recaptures_new_pointers(torch_cuda):
     from paper_1609_03170_gb300 import GrapeBatch, GrapeProblem
     ws = batch_workloads(5, [12, 30])

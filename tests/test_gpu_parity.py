@@ -132,6 +132,53 @@ def test_cluster_width_does_not_change_bits(gp, prec, herm):
         assert np.array_equal(G, out[0][1])
 
 
+@pytest.mark.parametrize("herm", KERNELS)
+@pytest.mark.parametrize("prec", PRECS)
+def test_tile_does_not_change_bits(gp, prec, herm):
+    """Cluster width and threads per CTA only move entries between CTAs and
+    threads: every (width, threads) tile gives the same bits."""
+    w = workloads.transmon_resonator_d120(n_slices=6)
+    with with_cluster(16, herm):
+        P = gp.GrapeProblem.from_workload(w, precision=prec)
+    F0, G0 = P.gradient(w.u)
+    r0 = P.forward(w.u)[1]
+    for c, t in ((8, 128), (16, 64), (16, 256), (8, 512)):
+        P.set_tile(c, t)
+        assert P.geometry()[:2] == (c, t)
+        F, G = P.gradient(w.u)
+        assert F == F0 and np.array_equal(G, G0)
+        assert np.array_equal(P.forward(w.u)[1], r0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_single_cta_tiles_match_oracle(gp, prec):
+    """d=20 with one CTA per state and 64 or 96 threads (several entries per
+    thread, a ragged last pass) against the C oracle."""
+    w = workloads.qubit_resonator_d20(n_slices=40)
+    F_ref, G_ref, r_ref, _ = sparse.run_workload(w, threads=2)
+    P = gp.GrapeProblem.from_workload(w, precision=prec)
+    for c, t in ((1, 64), (1, 96), (2, 160)):
+        P.set_tile(c, t)
+        F, r = P.forward(w.u)
+        assert rel(r, r_ref) < TOL
+        F2, G = P.gradient(w.u)
+        assert abs(F2 - F_ref) < TOL * abs(F_ref) and rel(G, G_ref) < TOL
+
+
+def test_set_tile_rejects_bad_tiles(gp):
+    w = workloads.transmon_resonator_d120(n_slices=4)
+    P = gp.GrapeProblem.from_workload(w)
+    before = P.geometry()
+    for c, t in ((3, 128), (4, 100), (4, 1024), (4, 32)):
+        with pytest.raises(gp._lib.GrapeError) as e:
+            P.set_tile(c, t)
+        assert e.value.status == gp._lib.GRAPE_EINVAL
+    with pytest.raises(gp._lib.GrapeError) as e:   # 7260 entries in one CTA do not fit shared memory
+        P.set_tile(1, 512)
+    assert e.value.status == gp._lib.GRAPE_EINVAL
+    assert P.geometry() == before
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_hermitian_and_full_kernels_agree(gp, prec):
     """The upper-triangle kernel mirrors the lower triangle instead of
