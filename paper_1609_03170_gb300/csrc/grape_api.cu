@@ -566,8 +566,8 @@ grape_status plan_h(grape_problem *P, int ncl, int threads) {
     const int nb = std::max(P->tab[0].nb, P->tab[1].nb), nt = std::max(P->tab[0].nt, P->tab[1].nt);
     int maxwin = 0, cu = 0, rt_rows = 0;
     const std::vector<int> tab = hermitian_table(d, ncl, P->omax, hb, &maxwin, &cu, &rt_rows);
-    if (maxwin >= 32768) return fail(GRAPE_EINVAL, "state window too large for 16-bit addresses");
-    const size_t smem = ((size_t)2 * maxwin + 2 * (size_t)cu + 2 * (size_t)nb * d +
+    if (maxwin >= 32767) return fail(GRAPE_EINVAL, "state window too large for 16-bit addresses");
+    const size_t smem = ((size_t)2 * (maxwin + 1) + 2 * (size_t)cu + 2 * (size_t)nb * d +
                          2 * (size_t)nt * d) * sizeof(double2) +
                         (size_t)cu * sizeof(int2) + 12 * sizeof(double) + tab.size() * sizeof(int) +
                         (size_t)rt_rows * (ncl + 1) * sizeof(uint32_t) +

@@ -304,18 +304,18 @@ __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::s
                                                            const typename Num::store_t *A,
                                                            const typename Num::store_t *vL,
                                                            const typename Num::store_t *vR) {
+    // neighbours outside the matrix point at the window's zero slot, so
+    // every term is accumulated without a branch (adding 0 changes no bit)
     typename Num::acc w = Num::acc_zero();
 #pragma unroll 1
     for (int b = 0; b < t.nb; ++b) {
-        const int aL = nb_ad[2 * b], aR = nb_ad[2 * b + 1];
-        if (aL >= 0) Num::mac(w, Num::load(A[b * d + i]), Num::load(cur[aL]));
-        if (aR >= 0) Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[aR]));
+        Num::mac(w, Num::load(A[b * d + i]), Num::load(cur[nb_ad[2 * b]]));
+        Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[nb_ad[2 * b + 1]]));
     }
     w = Num::acc_minus_i(w);
 #pragma unroll 1
     for (int q = 0; q < t.nt; ++q) {
         const int aJ = nb_ad[2 * t.nb + q];
-        if (aJ < 0) continue;
         if (REALJ) {
             const typename Num::real_t cf =
                 Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j])));
@@ -347,7 +347,8 @@ __device__ __forceinline__ void hpush_pre(const uint32_t *rowtab, int rstride, i
     for (int t = 1; t <= n; ++t) st_cluster_addr(e[t] + boff + (uint32_t)c * (uint32_t)sizeof(S), v);
 }
 
-// Shared memory: buf0, buf1 [maxwin]; xs, as [cu]; bands [2][nb][d];
+// Shared memory: buf0, buf1 [maxwin + 1] (the last entry of each stays zero);
+// xs, as [cu]; bands [2][nb][d];
 // vL, vR [nt][d]; rc [cu] (int2); 12 RK coefficients; htab copy (ints);
 // row push table [rt_rows][ncl + 1] (u32); neighbour addresses [cu][ns + 1] (i16).
 template <class Num, bool REALJ>
@@ -358,9 +359,10 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int d = p.d, d2 = d * d;
     const int nbd = p.tab.nb * d;
+    const int wst = p.maxwin + 1;                // window stride; slot maxwin is the zero slot
     S *buf0 = reinterpret_cast<S *>(smem_raw);
-    S *buf1 = buf0 + p.maxwin;
-    S *xs = buf1 + p.maxwin;
+    S *buf1 = buf0 + wst;
+    S *xs = buf1 + wst;
     S *as = xs + p.cu;
     S *bands = as + p.cu;
     S *vL = bands + 2 * nbd;
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
 
     for (int i = threadIdx.x; i < p.htab_len; i += nth) tab[i] = __ldg(&p.htab[i]);
     const V vzero = Num::zero();
-    for (int i = threadIdx.x; i < 2 * p.maxwin; i += nth) buf0[i] = Num::store(vzero);
+    for (int i = threadIdx.x; i < 2 * wst; i += nth) buf0[i] = Num::store(vzero);
     for (int i = threadIdx.x; i < p.tab.nt * d; i += nth) {
         vL[i] = Num::store(Num::from_double2(__ldg(&p.tab.vL[i])));
         vR[i] = Num::store(Num::from_double2(__ldg(&p.tab.vR[i])));
@@ -420,15 +422,16 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
         short *na = nbad + (size_t)(u - u0) * nstride;
         const int own = ofs[i - wr0] + (j - cs_of(i, hb));
         na[ns] = (short)own;
+        const short zs = (short)p.maxwin;
         for (int b = 0; b < p.tab.nb; ++b) {
             const int o = p.tab.off[b], r = i + o, c = j + o;
-            na[2 * b] = (short)((r >= 0 && r < d) ? ofs[r - wr0] + (j - cs_of(r, hb)) : -1);
-            na[2 * b + 1] = (short)((c >= 0 && c < d) ? own + o : -1);
+            na[2 * b] = (r >= 0 && r < d) ? (short)(ofs[r - wr0] + (j - cs_of(r, hb))) : zs;
+            na[2 * b + 1] = (c >= 0 && c < d) ? (short)(own + o) : zs;
         }
         for (int q = 0; q < p.tab.nt; ++q) {
             const int r = i + p.tab.joL[q], c = j + p.tab.joR[q];
             na[2 * p.tab.nb + q] =
-                (short)((r >= 0 && r < d && c >= 0 && c < d) ? ofs[r - wr0] + (c - cs_of(r, hb)) : -1);
+                (r >= 0 && r < d && c >= 0 && c < d) ? (short)(ofs[r - wr0] + (c - cs_of(r, hb))) : zs;
         }
     }
     // push targets of the rows this CTA writes: its own rows and, for the
@@ -461,7 +464,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
         e[0] = (uint32_t)n;
     }
     cluster_sync_all();   // every CTA runs, windows zeroed, tables built
-    const uint32_t boff1 = (uint32_t)(p.maxwin * (int)sizeof(S));
+    const uint32_t boff1 = (uint32_t)(wst * (int)sizeof(S));
 
     for (int u = u0 + threadIdx.x; u < u1; u += nth) {
         const int2 ij = rc[u - u0];

@@ -37,20 +37,38 @@ __device__ __forceinline__ ff fast_two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);
     return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
-__device__ __forceinline__ ff ff_add(ff a, ff b) {       // accurate sum
-    ff s = two_sum(a.h, b.h);
-    const ff t = two_sum(a.l, b.l);
-    s.l = __fadd_rn(s.l, t.h);
-    s = fast_two_sum(s.h, s.l);
-    s.l = __fadd_rn(s.l, t.l);
-    return fast_two_sum(s.h, s.l);
-}
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
     const float p = __fmul_rn(a.h, b.h);
     float e = __fmaf_rn(a.h, b.h, -p);
     e = __fmaf_rn(a.h, b.l, e);
     e = __fmaf_rn(a.l, b.h, e);
     return fast_two_sum(p, e);
+}
+// x + s*w: the product's high part is exact (FMA) and its error joins the
+// cross terms and the low parts, renormalised once.  One TwoSum instead of
+// the accurate sum's two: the error is about 2^-47 (|x| + |s w|), an
+// absolute bound on the scale of the operands, which is what the
+// propagation needs (its tolerances are relative to the largest entry).
+__device__ __forceinline__ ff ff_axpy(ff s, ff w, ff x) {
+    const float p = __fmul_rn(s.h, w.h);
+    float e = __fmaf_rn(s.h, w.h, -p);
+    e = __fmaf_rn(s.h, w.l, e);
+    e = __fmaf_rn(s.l, w.h, e);
+    const ff t = two_sum(x.h, p);
+    return fast_two_sum(t.h, __fadd_rn(t.l, __fadd_rn(x.l, e)));
+}
+// g*x + b*w, same error model
+__device__ __forceinline__ ff ff_lin2(ff g, ff x, ff b, ff w) {
+    const float p = __fmul_rn(g.h, x.h);
+    float e = __fmaf_rn(g.h, x.h, -p);
+    e = __fmaf_rn(g.h, x.l, e);
+    e = __fmaf_rn(g.l, x.h, e);
+    const float q = __fmul_rn(b.h, w.h);
+    float f = __fmaf_rn(b.h, w.h, -q);
+    f = __fmaf_rn(b.h, w.l, f);
+    f = __fmaf_rn(b.l, w.h, f);
+    const ff t = two_sum(p, q);
+    return fast_two_sum(t.h, __fadd_rn(t.l, __fadd_rn(e, f)));
 }
 __host__ __device__ __forceinline__ ff ff_from_double(double x) {
     const float h = (float)x;
@@ -182,10 +200,10 @@ struct NumF {
         lacc_fma(w.im, c.h, c.l, b.im.h, b.im.l);
     }
     static __device__ __forceinline__ val axpy(real_t s, val w, val x) {
-        return {ff_add(x.re, ff_mul(s, w.re)), ff_add(x.im, ff_mul(s, w.im))};
+        return {ff_axpy(s, w.re, x.re), ff_axpy(s, w.im, x.im)};
     }
     static __device__ __forceinline__ val lin2(real_t g, val x, real_t b, val w) {
-        return {ff_add(ff_mul(g, x.re), ff_mul(b, w.re)), ff_add(ff_mul(g, x.im), ff_mul(b, w.im))};
+        return {ff_lin2(g, x.re, b, w.re), ff_lin2(g, x.im, b, w.im)};
     }
     static __device__ __forceinline__ val scale(real_t s, val a) {
         return {ff_mul(s, a.re), ff_mul(s, a.im)};
