@@ -216,6 +216,7 @@ struct grape_problem {
     int ncl = 1, threads = GRAPE_PROP_THREADS, chunk = 0, halo = 0, win = 0, reach = 0;
     int variant = 0;                 // bit 0 = real jump tables, bit 1 = Hermitian kernel
     int hb = 0, cu = 0, maxwin = 0, htab_len = 0, rt_rows = 0;   // Hermitian kernel geometry
+    int fold = 0;                    // Hermitian kernel: own-entry coefficients cached in shared memory
     int omax = 0;                    // largest band offset of either Lindbladian
     int hb_h = 0;                    // lower entries the Hermitian stencil reads
     std::map<int, int *> htabs;      // Hermitian tables per cluster width
@@ -342,10 +343,14 @@ grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
         t->off[b] = h.off[b];
         t->off_row[b] = h.off[b] * d;
     }
+    t->b0 = -1;
+    for (int b = 0; b < t->nb; ++b)
+        if (h.off[b] == 0) t->b0 = b;
     for (int q = 0; q < t->nt; ++q) {
         t->jflat[q] = h.oL[q] * d + h.oR[q];
         t->joL[q] = h.oL[q];
         t->joR[q] = h.oR[q];
+        if (h.oL[q] == 0 && h.oR[q] == 0) t->jdiag |= 1 << q;
     }
     auto cvt = [](const std::vector<cplx> &v) {
         std::vector<double2> o(v.size());
@@ -573,9 +578,18 @@ grape_status plan_h(grape_problem *P, int ncl, int threads) {
                         (size_t)rt_rows * (ncl + 1) * sizeof(uint32_t) +
                         (size_t)cu * (2 * nb + nt + 1) * sizeof(short);
     const int variant = (P->variant & 1) | 2;
-    if (smem + 1024 > (size_t)max_smem) return fail(GRAPE_EINVAL, "state window does not fit in shared memory");
-    if (!cluster_fits(P, variant, threads, smem, ncl))
-        return fail(GRAPE_EINVAL, "no cluster of this shape can be resident");
+    // own-entry coefficients cached per slice (16 B per owned entry) when the
+    // table fits, else recomputed every stage: the same values either way
+    bool fold = true;
+    if (const char *env = std::getenv("GRAPE_FOLD")) fold = std::atoi(env) != 0;
+    const size_t smem_fold = smem + (size_t)cu * sizeof(double2);
+    fold = fold && smem_fold + 1024 <= (size_t)max_smem && cluster_fits(P, variant, threads, smem_fold, ncl);
+    const size_t use = fold ? smem_fold : smem;
+    if (!fold) {
+        if (use + 1024 > (size_t)max_smem) return fail(GRAPE_EINVAL, "state window does not fit in shared memory");
+        if (!cluster_fits(P, variant, threads, use, ncl))
+            return fail(GRAPE_EINVAL, "no cluster of this shape can be resident");
+    }
     auto it = P->htabs.find(ncl);
     if (it == P->htabs.end()) {
         int *dt = nullptr;
@@ -591,7 +605,8 @@ grape_status plan_h(grape_problem *P, int ncl, int threads) {
     P->hb = hb;
     P->htab_len = (int)tab.size();
     P->rt_rows = rt_rows;
-    P->smem = smem;
+    P->smem = use;
+    P->fold = fold ? 1 : 0;
     P->threads = threads;
     P->chunk = cu;
     P->halo = 0;
@@ -699,6 +714,7 @@ PropArgs base_args(const grape_problem *P, int dir, const double *u) {
     a.cu = P->cu;
     a.maxwin = P->maxwin;
     a.rt_rows = P->rt_rows;
+    a.fold = (P->variant & 2) ? P->fold : 0;
     a.gbuf = P->d_gbuf;
     a.gbar = P->d_gbar;
     a.ce = P->ce;

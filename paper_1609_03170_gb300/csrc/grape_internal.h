@@ -25,6 +25,8 @@ struct PropTables {
     int jflat[GRAPE_MAXT];      // oL_t * d + oR_t
     int joL[GRAPE_MAXT];        // oL_t
     int joR[GRAPE_MAXT];        // oR_t
+    int b0;                     // index of the offset-0 band, -1 if none
+    int jdiag;                  // bit t set: jump term t has oL_t = oR_t = 0
     const double2 *A0;          // [nb][d]
     const double2 *Ak;          // [R][nb][d]
     const double2 *vL;          // [nt][d]
@@ -64,6 +66,7 @@ struct PropArgs {
     int cu;                             // upper-triangle entries per CTA
     int maxwin;                         // largest window (entries) of the cluster
     int rt_rows;                        // rows of the largest push table
+    int fold;                           // Hermitian kernel: own-entry coefficients folded (D table)
     // grid kernel (state windows in global memory, one grid barrier per stage)
     void *gbuf;                         // [2][n_states][d*d] stage-input buffers
     unsigned *gbar;                     // [0] arrivals, [1] generation, [2] error flag

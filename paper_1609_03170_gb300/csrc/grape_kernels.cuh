@@ -297,24 +297,49 @@ __device__ __forceinline__ void st_cluster_addr(uint32_t addr, float4 v) { st_re
 // window addresses nb_ad: [2 b] = (i + o_b, j), [2 b + 1] = (i, j + o_b),
 // [2 nb + q] = (i + oL_q, j + oR_q); -1 where the neighbour lies outside the
 // matrix (its coefficient is zero there).
+// D_ij = -i (A_0[i] - conj(A_0[j])) + sum over jump terms with both offsets
+// 0 of vL_t[i] conj(vR_t[j]): the coefficient of X_ij itself in W_ij
+template <class Num, bool REALJ>
+__device__ __forceinline__ typename Num::val diag_coef(int i, int j, int d, const PropTables &t,
+                                                       const typename Num::store_t *A,
+                                                       const typename Num::store_t *vL,
+                                                       const typename Num::store_t *vR) {
+    typename Num::val c = Num::zero();
+    if (t.b0 >= 0) c = Num::minus_i(Num::sub_conj(Num::load(A[t.b0 * d + i]), Num::load(A[t.b0 * d + j])));
+    for (int q = 0; q < t.nt; ++q) {
+        if (!((t.jdiag >> q) & 1)) continue;
+        if (REALJ)
+            c = Num::add_real(c, Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j]))));
+        else
+            c = Num::add(c, Num::mul_conjb(Num::load(vL[q * d + i]), Num::load(vR[q * d + j])));
+    }
+    return c;
+}
+
 template <class Num, bool REALJ>
 __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::store_t *cur,
                                                            const short *nb_ad, int i, int j, int d,
                                                            const PropTables &t,
                                                            const typename Num::store_t *A,
                                                            const typename Num::store_t *vL,
-                                                           const typename Num::store_t *vR) {
+                                                           const typename Num::store_t *vR,
+                                                           const typename Num::val dij) {
     // neighbours outside the matrix point at the window's zero slot, so
-    // every term is accumulated without a branch (adding 0 changes no bit)
+    // every term is accumulated without a branch (adding 0 changes no bit).
+    // The terms on the entry itself - the offset-0 band and the jump terms
+    // with both offsets 0 - come as one coefficient D_ij (diag_coef).
     typename Num::acc w = Num::acc_zero();
 #pragma unroll 1
     for (int b = 0; b < t.nb; ++b) {
+        if (b == t.b0) continue;
         Num::mac(w, Num::load(A[b * d + i]), Num::load(cur[nb_ad[2 * b]]));
         Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[nb_ad[2 * b + 1]]));
     }
     w = Num::acc_minus_i(w);
+    Num::mac(w, dij, Num::load(cur[nb_ad[2 * t.nb + t.nt]]));
 #pragma unroll 1
     for (int q = 0; q < t.nt; ++q) {
+        if ((t.jdiag >> q) & 1) continue;
         const int aJ = nb_ad[2 * t.nb + q];
         if (REALJ) {
             const typename Num::real_t cf =
@@ -325,7 +350,7 @@ __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::s
                      Num::load(cur[aJ]));
         }
     }
-    return Num::done(w);
+    return Num::raw(w);
 }
 
 // full-matrix store of upper entry (i, j) and its conjugate mirror
@@ -348,7 +373,7 @@ __device__ __forceinline__ void hpush_pre(const uint32_t *rowtab, int rstride, i
 }
 
 // Shared memory: buf0, buf1 [maxwin + 1] (the last entry of each stays zero);
-// xs, as [cu]; bands [2][nb][d];
+// xs, as [cu]; D [cu] when p.fold; bands [2][nb][d];
 // vL, vR [nt][d]; rc [cu] (int2); 12 RK coefficients; htab copy (ints);
 // row push table [rt_rows][ncl + 1] (u32); neighbour addresses [cu][ns + 1] (i16).
 template <class Num, bool REALJ>
@@ -364,7 +389,8 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     S *buf1 = buf0 + wst;
     S *xs = buf1 + wst;
     S *as = xs + p.cu;
-    S *bands = as + p.cu;
+    S *Dt = as + p.cu;                           // [cu] own-entry coefficients when p.fold
+    S *bands = Dt + (p.fold ? p.cu : 0);
     S *vL = bands + 2 * nbd;
     S *vR = vL + p.tab.nt * d;
     int2 *rc = reinterpret_cast<int2 *>(vR + p.tab.nt * d);
@@ -479,6 +505,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
 
     const bool unit_g = (p.g[1] == 1.0 && p.g[2] == 1.0 && p.g[3] == 1.0);   // forward RK4
     int tb = 0;
+    bool dfresh = true;                          // D table to (re)build for this slice
     for (long long it = 0; it < nsub; ++it) {
         const long long n = p.reverse ? p.sub_end - 1 - it : p.sub_begin + it;
         const long long tidx = p.reverse ? n + 1 : n;
@@ -502,7 +529,16 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                 const int li = u - u0;
                 const int2 ij = rc[li];
                 const short *na = nbad + (size_t)li * nstride;
-                const V w = lindblad_h_at<Num, REALJ>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR);
+                // own-entry coefficient: cached per slice (the entry is thread-private,
+                // so no barrier is needed) or recomputed when there is no room
+                V dij;
+                if (p.fold) {
+                    if (s == 0 && dfresh) Dt[li] = Num::store(diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR));
+                    dij = Num::load(Dt[li]);
+                } else {
+                    dij = diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR);
+                }
+                const V w = lindblad_h_at<Num, REALJ>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij);
                 if (st) store_herm<Num>(st, d, ij.x, ij.y, cur[na[ns]]);   // the stage input itself
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
@@ -530,6 +566,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
             cluster_sync_all();
         }
         if (flip) tb ^= 1;
+        dfresh = flip;
     }
     const long long tend = p.reverse ? p.sub_begin : p.sub_end;
     if (bound_store && ((tend - p.sub_begin) % p.bound_step) == 0) {
@@ -596,17 +633,21 @@ __device__ __forceinline__ typename Num::val lindblad_g_at(const typename Num::s
                                                            const typename Num::store_t *A,
                                                            const typename Num::store_t *vL,
                                                            const typename Num::store_t *vR) {
+    // same terms in the same order as lindblad_h_at (identical bits)
     typename Num::acc w = Num::acc_zero();
 #pragma unroll 1
     for (int b = 0; b < t.nb; ++b) {
+        if (b == t.b0) continue;
         const int o = t.off[b], r = i + o, c = j + o;
         if (r >= 0 && r < d) Num::mac(w, Num::load(A[b * d + i]), Num::load(__ldcg(&cur[(size_t)r * d + j])));
         if (c >= 0 && c < d)
             Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(__ldcg(&cur[(size_t)i * d + c])));
     }
     w = Num::acc_minus_i(w);
+    Num::mac(w, diag_coef<Num, REALJ>(i, j, d, t, A, vL, vR), Num::load(__ldcg(&cur[(size_t)i * d + j])));
 #pragma unroll 1
     for (int q = 0; q < t.nt; ++q) {
+        if ((t.jdiag >> q) & 1) continue;
         const int r = i + t.joL[q], c = j + t.joR[q];
         if (r < 0 || r >= d || c < 0 || c >= d) continue;
         const typename Num::val zv = Num::load(__ldcg(&cur[(size_t)r * d + c]));
@@ -618,7 +659,7 @@ __device__ __forceinline__ typename Num::val lindblad_g_at(const typename Num::s
             Num::mac(w, Num::mul_conjb(Num::load(vL[q * d + i]), Num::load(vR[q * d + j])), zv);
         }
     }
-    return Num::done(w);
+    return Num::raw(w);
 }
 
 // Shared memory: xs, as [ce]; bands [2][nb][d]; vL, vR [nt][d];

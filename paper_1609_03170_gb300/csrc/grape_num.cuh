@@ -70,6 +70,11 @@ __device__ __forceinline__ ff ff_lin2(ff g, ff x, ff b, ff w) {
     const ff t = two_sum(p, q);
     return fast_two_sum(t.h, __fadd_rn(t.l, __fadd_rn(e, f)));
 }
+// a + b with one TwoSum (same error model as ff_axpy)
+__device__ __forceinline__ ff ff_sum(ff a, ff b) {
+    const ff t = two_sum(a.h, b.h);
+    return fast_two_sum(t.h, __fadd_rn(t.l, __fadd_rn(a.l, b.l)));
+}
 __host__ __device__ __forceinline__ ff ff_from_double(double x) {
     const float h = (float)x;
     return {h, (float)(x - (double)h)};
@@ -122,7 +127,12 @@ struct NumD {
         c.im = fma(a.im, b.re, fma(-a.re, b.im, c.im));
     }
     static __device__ __forceinline__ val done(acc c) { return {c.re, c.im}; }
+    static __device__ __forceinline__ val raw(acc c) { return {c.re, c.im}; }
     static __device__ __forceinline__ acc acc_minus_i(acc c) { return {c.im, -c.re}; }
+    // a - conj(b), a + b, a + c (c real)
+    static __device__ __forceinline__ val sub_conj(val a, val b) { return {a.re - b.re, a.im + b.im}; }
+    static __device__ __forceinline__ val add(val a, val b) { return {a.re + b.re, a.im + b.im}; }
+    static __device__ __forceinline__ val add_real(val a, real_t c) { return {a.re + c, a.im}; }
     // a * conj(b)
     static __device__ __forceinline__ val mul_conjb(val a, val b) {
         return {fma(a.re, b.re, a.im * b.im), fma(a.im, b.re, -a.re * b.im)};
@@ -183,7 +193,15 @@ struct NumF {
         lacc_fms(c.im, a.re.h, a.re.l, b.im.h, b.im.l);
     }
     static __device__ __forceinline__ val done(acc c) { return {lacc_done(c.re), lacc_done(c.im)}; }
+    // the accumulator's pairs as they stand (the low parts not renormalised;
+    // consumers that multiply keep every cross term, so nothing is lost)
+    static __device__ __forceinline__ val raw(acc c) { return {{c.re.h, c.re.l}, {c.im.h, c.im.l}}; }
     static __device__ __forceinline__ acc acc_minus_i(acc c) { return {c.im, {-c.re.h, -c.re.l}}; }
+    static __device__ __forceinline__ val sub_conj(val a, val b) {
+        return {ff_sum(a.re, {-b.re.h, -b.re.l}), ff_sum(a.im, b.im)};
+    }
+    static __device__ __forceinline__ val add(val a, val b) { return {ff_sum(a.re, b.re), ff_sum(a.im, b.im)}; }
+    static __device__ __forceinline__ val add_real(val a, real_t c) { return {ff_sum(a.re, c), a.im}; }
     static __device__ __forceinline__ val mul_conjb(val a, val b) {
         acc c = acc_zero();
         mac_conjb(c, a, b);

@@ -151,6 +151,22 @@ def test_tile_does_not_change_bits(gp, prec, herm):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_cached_and_recomputed_own_coefficients_agree(gp, prec):
+    """The coefficient of X_ij itself (offset-0 band and both-offsets-0 jump
+    terms) is cached per slice when shared memory allows and recomputed every
+    stage otherwise: the same values, so the same bits (d=120 has a
+    dephasing jump, so both parts of the coefficient are exercised)."""
+    w = workloads.transmon_resonator_d120(n_slices=7)
+    P1 = gp.GrapeProblem.from_workload(w, precision=prec)
+    with with_env(GRAPE_FOLD=0):
+        P0 = gp.GrapeProblem.from_workload(w, precision=prec)
+    F1, G1 = P1.gradient(w.u)
+    F0, G0 = P0.gradient(w.u)
+    assert F1 == F0 and np.array_equal(G1, G0)
+    assert np.array_equal(P1.forward(w.u)[1], P0.forward(w.u)[1])
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_single_cta_tiles_match_oracle(gp, prec):
     """d=20 with one CTA per state and 64 or 96 threads (several entries per
     thread, a ragged last pass) against the C oracle."""
