@@ -224,7 +224,11 @@ grape_status grape_batch_info(grape_batch_t batch, int32_t *n_lanes, size_t *scr
  * server keeps every job's controls, gradient and L-BFGS history on the
  * device; a worker thread admits queued jobs (in order) whenever a slot is
  * free, their gradient storage fits the memory budget and the SMs their
- * clusters need (states x cluster width) are not taken, runs each admitted job on
+ * clusters need (states x cluster width) are not taken - a job admitted
+ * while others run or wait is first moved to the narrowest cluster width its
+ * state fits (grape_problem_set_tile; results unchanged), widened again
+ * between iterations when nothing waits and SMs are free, and given its own
+ * tile back when it ends (GRAPE_SERVER_ELASTIC=0 keeps tiles) - runs each admitted job on
  * its own stream and launches its next iteration as soon as the previous one
  * completes, so iterations of different jobs overlap.  A job's result does
  * not depend on the other jobs (deterministic kernels). */

@@ -327,6 +327,10 @@ grape_status upload(grape_problem *P, const std::vector<T> &h, T **out) {
     if (!*out) return fail(GRAPE_ENOMEM, "cudaMalloc failed for a problem table");
     if (!h.empty())
         GRAPE_CUDA_TRY(cudaMemcpy(*out, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    // a copy from pageable memory may return before its DMA lands, and the
+    // kernels run on non-blocking streams that do not wait for the legacy
+    // stream: wait for it here
+    GRAPE_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
     return GRAPE_OK;
 }
 
@@ -667,6 +671,7 @@ grape_status choose_geometry_grid(grape_problem *P) {
     P->d_gbar = static_cast<unsigned *>(P->alloc(4 * sizeof(unsigned)));
     if (!P->d_gbuf || !P->d_gbar) return fail(GRAPE_ENOMEM, "cudaMalloc failed for the grid kernel buffers");
     GRAPE_CUDA_TRY(cudaMemset(P->d_gbar, 0, 4 * sizeof(unsigned)));
+    GRAPE_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));   // before non-blocking streams use it
     if (const char *env = std::getenv("GRAPE_SPIN_LIMIT")) P->spin_limit = std::atoll(env);
     P->grid = true;
     P->nblocks = nblocks;
@@ -1235,6 +1240,7 @@ grape_status grape_problem_status(grape_problem_t P) {
     GRAPE_CUDA_TRY(cudaMemcpy(flag, P->d_gbar, sizeof(flag), cudaMemcpyDeviceToHost));
     if (flag[2] != 0u) {
         GRAPE_CUDA_TRY(cudaMemset(P->d_gbar, 0, 4 * sizeof(unsigned)));
+        GRAPE_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
         return fail(GRAPE_ETIMEOUT, "a grid barrier of the propagation kernel gave up waiting");
     }
     return GRAPE_OK;
@@ -1589,7 +1595,8 @@ grape_status tune_batch(grape_batch *B) {
         if (u) cudaFree(u);
     };
     if (cudaMalloc(&out, out_bytes) != cudaSuccess || cudaMalloc(&u, u_bytes) != cudaSuccess ||
-        cudaMemset(u, 0, u_bytes) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaMemset(u, 0, u_bytes) != cudaSuccess || cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess ||
         cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
@@ -1927,6 +1934,8 @@ struct ServerJob {
     std::vector<double> u_out;
     double F_out = 0.0;
     int evals = 0;
+    int sm_demand = 0;                // SMs its clusters take (counted at admission)
+    int2 own_tile = {0, 0};           // the problem's tile before admission narrowed it (x = 0: kept)
     std::chrono::steady_clock::time_point t_submit, t_start, t_done;
 };
 
@@ -1934,6 +1943,7 @@ struct grape_server {
     int device = 0;
     int n_sms = 0;                      // streaming multiprocessors of the device
     int sms_in_use = 0;                 // SM demand of the admitted jobs
+    bool elastic = true;                // narrow the tiles of jobs admitted next to others
     size_t budget = 0;
     int max_slots = 1;
     cudaMemPool_t pool = nullptr;       // device memory of the admitted jobs
@@ -2060,6 +2070,31 @@ void free_job_device(grape_server *S, ServerJob *j) {
     j->h_state = nullptr;
 }
 
+// Between iterations of a narrowed job, with nothing waiting: the widest
+// cluster up to its own that the free SMs hold (the GPU drains at the end of
+// a burst; the last jobs should not stay narrow on an idle device).
+void widen_job_tile(grape_server *S, ServerJob *j) {
+    if (j->own_tile.x <= 0) return;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->queue.empty()) return;
+    const int spare = S->n_sms - S->sms_in_use + j->sm_demand;
+    for (int w = j->own_tile.x; w > j->P->ncl; w /= 2) {
+        if (j->P->ns * w > spare) continue;
+        const int t = (w == j->own_tile.x) ? j->own_tile.y : j->P->threads;
+        if (grape_problem_set_tile(j->P, w, t) != GRAPE_OK) continue;
+        const int dem = j->P->ns * w;
+        S->sms_in_use += dem - j->sm_demand;
+        j->sm_demand = dem;
+        if (w == j->own_tile.x) j->own_tile = make_int2(0, 0);
+        return;
+    }
+}
+
+void restore_job_tile(ServerJob *j) {
+    if (j->own_tile.x > 0) grape_problem_set_tile(j->P, j->own_tile.x, j->own_tile.y);
+    j->own_tile = make_int2(0, 0);
+}
+
 int job_sm_demand(const grape_server *S, const ServerJob *j) {
     const grape_problem *P = j->P;
     return P->grid ? S->n_sms : std::max(1, P->ns * P->ncl);
@@ -2092,17 +2127,32 @@ void server_loop(grape_server *S) {
                 for (const ServerJob *a : admit) grid_running = grid_running || a->P->grid;
                 if (grid_running) break;
                 if (j->P->grid && !(S->active.empty() && admit.empty())) break;
+                // elastic tiles: a job that shares the GPU runs on the narrowest
+                // cluster its state fits (fewer SMs for longer; results unchanged)
+                const bool alone = S->active.empty() && admit.empty();
+                int2 own = make_int2(0, 0);
+                if (S->elastic && S->max_slots > 1 && !j->P->grid && (!alone || S->queue.size() > 1)) {
+                    const int2 cur = make_int2(j->P->ncl, j->P->threads);
+                    for (int w = 1; w < cur.x; w *= 2)
+                        if (grape_problem_set_tile(j->P, w, GRAPE_PROP_THREADS) == GRAPE_OK) {
+                            own = cur;
+                            break;
+                        }
+                }
+                auto undo = [&] { if (own.x > 0) grape_problem_set_tile(j->P, own.x, own.y); };
                 // SM demand: every initial state's cluster needs its own SMs; running
                 // more than fits only makes the clusters wait for free GPCs
                 const int dem = job_sm_demand(S, j);
-                if (S->sms_in_use + dem > S->n_sms && !(S->active.empty() && admit.empty())) break;
+                if (S->sms_in_use + dem > S->n_sms && !alone) { undo(); break; }
                 const size_t share = S->budget / std::max(1, S->max_slots);
                 const size_t need = std::min(share, seg_bytes(j->P, j->P->n_slices) + lbfgs_bytes(j->n, j->prm.lbfgs_m));
-                if (S->reserved + need > S->budget && !(S->active.empty() && admit.empty())) break;
+                if (S->reserved + need > S->budget && !alone) { undo(); break; }
                 S->queue.pop_front();
                 S->reserved += need;
                 S->sms_in_use += dem;
                 j->reserved = need;
+                j->sm_demand = dem;
+                j->own_tile = own;
                 admit.push_back(j);
             }
         }
@@ -2116,8 +2166,9 @@ void server_loop(grape_server *S) {
                 j->err = st;
                 j->err_msg = g_last_error;
                 S->reserved -= j->reserved;
-                S->sms_in_use -= job_sm_demand(S, j);
+                S->sms_in_use -= j->sm_demand;
                 free_job_device(S, j);
+                restore_job_tile(j);
                 j->t_done = std::chrono::steady_clock::now();
                 S->cv_done.notify_all();
             } else {
@@ -2143,6 +2194,7 @@ void server_loop(grape_server *S) {
                 st = grape_problem_status(j->P);
             }
             if (st == GRAPE_OK && j->h_state->status == 0) {
+                widen_job_tile(S, j);
                 st = launch_iteration(j);
                 if (st == GRAPE_OK) continue;
             }
@@ -2156,13 +2208,14 @@ void server_loop(grape_server *S) {
                 j->evals = j->h_state->evals;
             }
             free_job_device(S, j);
+            restore_job_tile(j);
             std::lock_guard<std::mutex> lk(S->mu);
             j->phase = (st == GRAPE_OK) ? 2 : 3;
             j->err = st;
             if (st != GRAPE_OK) j->err_msg = g_last_error;
             j->t_done = std::chrono::steady_clock::now();
             S->reserved -= j->reserved;
-            S->sms_in_use -= job_sm_demand(S, j);
+            S->sms_in_use -= j->sm_demand;
             S->active.erase(std::find(S->active.begin(), S->active.end(), j));
             S->cv_done.notify_all();
         }
@@ -2195,6 +2248,7 @@ grape_status grape_server_create(size_t hbm_budget_bytes, int32_t max_slots, gra
     S->budget = hbm_budget_bytes;
     S->max_slots = max_slots;
     cudaDeviceGetAttribute(&S->n_sms, cudaDevAttrMultiProcessorCount, S->device);
+    if (const char *env = std::getenv("GRAPE_SERVER_ELASTIC")) S->elastic = std::atoi(env) != 0;
     cudaMemPoolProps props = {};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;

@@ -63,12 +63,15 @@ def test_results_alone_equal_results_in_the_mix(gp):
     for P, w in zip(probs, ws):
         alone.append(wait(srv, srv.submit(P, w.u, max_iters=6)))
     srv.close()
+    own = [P.geometry() for P in probs]
     srv = gp.GrapeServer(max_slots=8)
     tickets = [srv.submit(P, w.u, max_iters=6) for P, w in zip(probs, ws)]
     mix = [wait(srv, t) for t in tickets]
     srv.close()
+    # jobs sharing the GPU ran on narrowed tiles: the same bits, tiles given back
     for a, b in zip(alone, mix):
         assert np.array_equal(a[0], b[0]) and a[1] == b[1] and a[2] == b[2]
+    assert [P.geometry() for P in probs] == own
 
 
 def test_memory_budget_queues_jobs(gp):
