@@ -80,6 +80,16 @@ def dist_init(n_gpus):
     return rank, world, dist
 
 
+def max_over_ranks(dist, values):
+    """Element-wise maximum over all ranks: the job takes as long as its
+    slowest rank."""
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(values, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
 def workload():
     import workloads
     return workloads.transmon_resonator_d120()
@@ -495,9 +505,7 @@ def main():
     clk = clocks.stop()
 
     if dist:
-        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
+        ms, e2e_s = max_over_ranks(dist, [ms, e2e_s])
     if rank != 0:
         dist.destroy_process_group()
         return

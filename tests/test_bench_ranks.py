@@ -1,0 +1,53 @@
+"""bench.py's multi-rank plumbing on the CPU: two gloo ranks launched the way
+torchrun launches them (RANK / WORLD_SIZE / MASTER_* in the environment)."""
+import os
+import socket
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+RANK_SCRIPT = r"""
+import io, contextlib, json, os, sys
+sys.path.insert(0, os.getcwd())
+import bench
+rank, world, dist = bench.dist_init(2)
+assert dist is not None and dist.get_backend() == "gloo"
+# each rank reports its own step time; the job's time is the slowest rank's
+mine = [10.0 + rank, 5.0 - rank]
+both = bench.max_over_ranks(dist, mine)
+out = io.StringIO()
+class A: steps = 1; warmup = 0; gpus = world
+with contextlib.redirect_stdout(out):
+    if rank != 0:
+        bench.run_reference(A, rank, world)      # other ranks exit without work
+dist.barrier()
+dist.destroy_process_group()
+print(json.dumps({"rank": rank, "world": world, "max": both, "ref_out": out.getvalue()}))
+"""
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_two_gloo_ranks_take_the_max_and_only_rank0_reports():
+    import json
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE="2",
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), CUDA_VISIBLE_DEVICES="")
+        procs.append(subprocess.Popen([sys.executable, "-c", RANK_SCRIPT], cwd=ROOT, env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        o, e = p.communicate(timeout=240)
+        assert p.returncode == 0, e
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    for r in outs:
+        assert r["world"] == 2
+        assert r["max"] == [11.0, 5.0]
+    assert outs[1]["ref_out"] == ""
