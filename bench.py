@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"],
                     help="kernel arithmetic: double-float on FP32 pipes or native FP64")
-    ap.add_argument("--workload", default="d120", choices=["d120", "batch256", "d600", "serve"])
+    ap.add_argument("--workload", default="d120", choices=["d120", "d20", "batch256", "d600", "serve"])
     ap.add_argument("--scale", type=float, default=None,
                     help="slice-count multiplier of the batch256/serve/d600 workloads")
     ap.add_argument("--jobs", type=int, default=64, help="serve: jobs in the trace")
@@ -342,6 +342,48 @@ def run_d600(args):
         "gpu_launches": P.gradient_launches() * args.steps})), flush=True)
 
 
+def run_d20(args):
+    """The small qubit-resonator problem (d=20, N_t=200): gradient evaluations
+    per second on the device and of the plain-C oracle on the host."""
+    import torch
+    import workloads
+    from oracle import sparse
+    from paper_1609_03170_gb300 import GrapeProblem, _lib
+    w = workloads.qubit_resonator_d20()
+    P = GrapeProblem.from_workload(w)
+    stream = torch.cuda.Stream()
+    u = torch.from_numpy(w.u).cuda()
+    F = torch.empty(1, dtype=torch.float64, device="cuda")
+    G = torch.empty((w.n_slices, w.n_controls), dtype=torch.float64, device="cuda")
+
+    def step():
+        _lib.grape_gradient(P.handle, u.data_ptr(), F.data_ptr(), G.data_ptr(), stream.cuda_stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    stream.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    sparse.build()
+    sparse.run_workload(w, threads=w.n_states)
+    t0 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        sparse.run_workload(w, threads=w.n_states)
+    cpu = reps / (time.perf_counter() - t0)
+    print(json.dumps(_base_line(args, "qubit_resonator_d20", 1000.0 / ms, UNIT, ms, {
+        "config": {"workload": "qubit_resonator_d20", "d": 20, "n_slices": 200, "n_rk": 4,
+                   "n_states": 2, "cluster": P.geometry()[0], "l2": "inputs fit in L2 (small case)"},
+        "cpu_baseline": {"value": cpu, "unit": UNIT, "cores": w.n_states, "kind": "oracle",
+                         "sample": "the whole d=20 problem, 5 gradient evaluations"},
+        "gpu_launches": P.gradient_launches() * args.steps})), flush=True)
+
+
 def serve_trace(n_jobs, scale, rate, seed=1609):
     """Seeded trace: (arrival time, workload); 88% batch-distribution problems,
     10% d=120 / N_t=2000 problems, 2% d=300 / N_t=10000 problems (slice
@@ -425,7 +467,8 @@ def main():
     if args.workload != "d120":
         import torch
         torch.cuda.set_device(0)
-        {"batch256": run_batch256, "d600": run_d600, "serve": run_serve}[args.workload](args)
+        {"batch256": run_batch256, "d600": run_d600, "serve": run_serve,
+         "d20": run_d20}[args.workload](args)
         return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":
