@@ -18,6 +18,8 @@ Modules
              block-matrix Frechet derivatives for exact gradients
   sparse     ctypes front end of grape_oracle.c, the same algorithm in plain C
              with sparse operators, for sizes the dense code cannot reach
+  filter     Gaussian filtering of the controls and its chain rule (App. A)
+  lbfgs      projected L-BFGS steps of the serving optimiser
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants, brute force and independent formulations.
