@@ -117,6 +117,40 @@ grape_status grape_forward(grape_problem_t problem, const double *u, double *F,
 grape_status grape_gradient(grape_problem_t problem, const double *u, double *F,
                             double *grad, void *stream);
 
+/* ---- Gaussian filtering of the controls (App. A, transfer matrix of the
+ * erf form; chain rule for the gradient) ----
+ * The n_steps piecewise-constant controls u (length Dt each) become n_sub
+ * subpixel amplitudes s (length dt each) - the slices a problem propagates:
+ *   s[n][k]  = sum_j T_k[n][j] u[j][k],
+ *   T_k[n][j] = (erf(w0_k (n dt - j Dt) / 2) - erf(w0_k (n dt - (j+1) Dt) / 2)) / 2
+ * with 0-based n, j and w0_k = wB_k / sqrt(-ln(1/sqrt 2)) for a 3 dB bandwidth
+ * wB_k of control k.  grape_filter_adjoint applies the transpose,
+ *   g_u[j][k] = sum_n T_k[n][j] g_s[n][k],
+ * which turns dPhi/ds into dPhi/du.  u, s, g_s, g_u are device float64 arrays,
+ * row-major [index][control]; omega0 is a host array of n_controls values.
+ * Both run on `stream` in FP64 (one thread per output, only the band of
+ * terms that can be non-zero: erf saturates to +-1 exactly).  Errors:
+ * GRAPE_EINVAL (NULL or host data pointers, n_steps or n_sub < 1,
+ * n_controls outside [1, 8], Dt, dt or an omega0 not positive and finite),
+ * GRAPE_ECUDA. */
+grape_status grape_filter_apply(int32_t n_steps, int32_t n_sub, int32_t n_controls, double Dt,
+                                double dt, const double *omega0, const double *u, double *s,
+                                void *stream);
+grape_status grape_filter_adjoint(int32_t n_steps, int32_t n_sub, int32_t n_controls, double Dt,
+                                  double dt, const double *omega0, const double *g_s, double *g_u,
+                                  void *stream);
+
+/* Phi and dPhi/du for n_steps filtered controls u [n_steps][n_controls]: the
+ * problem's n_slices are the subpixels (dt = T / n_slices, Dt = T / n_steps),
+ * s = filter(u) is propagated by grape_gradient and its gradient is mapped
+ * back through the transposed filter into grad [n_steps][n_controls].  u, F
+ * and grad may be host or device memory (host results are ready on return);
+ * omega0: host, one value per control.  The problem keeps the subpixel
+ * buffers (allocated on the first call).  Errors as grape_gradient and
+ * grape_filter_apply. */
+grape_status grape_gradient_filtered(grape_problem_t problem, int32_t n_steps, const double *omega0,
+                                     const double *u, double *F, double *grad, void *stream);
+
 /* Device memory the problem holds, in bytes (tables plus stage storage). */
 grape_status grape_problem_memory(grape_problem_t problem, size_t *bytes);
 

@@ -55,6 +55,7 @@ class GrapeError(RuntimeError):
 _lib = None
 
 EXPORTS = ["grape_problem_create", "grape_problem_destroy", "grape_forward", "grape_gradient",
+           "grape_filter_apply", "grape_filter_adjoint", "grape_gradient_filtered",
            "grape_problem_memory", "grape_problem_geometry", "grape_problem_set_tile", "grape_set_profiling",
            "grape_phase_times", "grape_gradient_launches", "grape_gradient_static",
            "grape_batch_create", "grape_batch_destroy", "grape_batch_gradient", "grape_batch_info",
@@ -86,6 +87,13 @@ def load(build_if_missing: bool = True):
     lib.grape_forward.restype = c_int32
     lib.grape_gradient.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.grape_gradient.restype = c_int32
+    for name in ("grape_filter_apply", "grape_filter_adjoint"):
+        getattr(lib, name).argtypes = [c_int32, c_int32, c_int32, c_double, c_double, P(c_double),
+                                       c_void_p, c_void_p, c_void_p]
+        getattr(lib, name).restype = c_int32
+    lib.grape_gradient_filtered.argtypes = [c_void_p, c_int32, P(c_double), c_void_p, c_void_p,
+                                            c_void_p, c_void_p]
+    lib.grape_gradient_filtered.restype = c_int32
     lib.grape_server_create.argtypes = [c_size_t, c_int32, P(c_void_p)]
     lib.grape_server_create.restype = c_int32
     lib.grape_server_destroy.argtypes = [c_void_p]
@@ -154,6 +162,34 @@ def grape_forward(h, u_ptr: int, F_ptr: int, rhoT_ptr: int, stream_ptr: int) -> 
 def grape_gradient(h, u_ptr: int, F_ptr: int, grad_ptr: int, stream_ptr: int) -> None:
     check(load().grape_gradient(h, u_ptr or None, F_ptr or None, grad_ptr or None,
                                 stream_ptr or None), "grape_gradient")
+
+
+def _omega0(omega0, n):
+    w = (c_double * n)()
+    vals = list(omega0) if hasattr(omega0, "__len__") else [omega0] * n
+    if len(vals) != n:
+        raise ValueError(f"omega0 needs {n} values")
+    for k, v in enumerate(vals):
+        w[k] = float(v)
+    return w
+
+
+def grape_filter_apply(n_steps, n_sub, n_controls, Dt, dt, omega0, u_ptr, s_ptr, stream_ptr):
+    check(load().grape_filter_apply(n_steps, n_sub, n_controls, Dt, dt, _omega0(omega0, n_controls),
+                                    u_ptr or None, s_ptr or None, stream_ptr or None),
+          "grape_filter_apply")
+
+
+def grape_filter_adjoint(n_steps, n_sub, n_controls, Dt, dt, omega0, gs_ptr, gu_ptr, stream_ptr):
+    check(load().grape_filter_adjoint(n_steps, n_sub, n_controls, Dt, dt, _omega0(omega0, n_controls),
+                                      gs_ptr or None, gu_ptr or None, stream_ptr or None),
+          "grape_filter_adjoint")
+
+
+def grape_gradient_filtered(h, n_steps, n_controls, omega0, u_ptr, F_ptr, grad_ptr, stream_ptr):
+    check(load().grape_gradient_filtered(h, n_steps, _omega0(omega0, n_controls), u_ptr or None,
+                                         F_ptr or None, grad_ptr or None, stream_ptr or None),
+          "grape_gradient_filtered")
 
 
 def grape_gradient_static(h, u_ptr: int, F_ptr: int, grad_ptr: int, stream_ptr: int) -> None:

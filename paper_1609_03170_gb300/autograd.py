@@ -52,3 +52,24 @@ class GrapeFunction(torch.autograd.Function):
 def grape_phi(u, problem, fused=True):
     """Phi(u) with autograd support (see GrapeFunction)."""
     return GrapeFunction.apply(u, problem, fused)
+
+
+class FilterFunction(torch.autograd.Function):
+    """s = T u for a GaussianFilter (App. A); backward applies the transposed
+    filter, the chain rule of the paper's filtered gradient."""
+
+    @staticmethod
+    def forward(ctx, u, filt):
+        if not (u.is_cuda and u.dtype == torch.float64):
+            raise TypeError("u must be a float64 CUDA tensor of shape (n_steps, n_controls)")
+        ctx.filt = filt
+        return filt.apply(u, stream=torch.cuda.current_stream(u.device))
+
+    @staticmethod
+    def backward(ctx, g_s):
+        return ctx.filt.adjoint(g_s, stream=torch.cuda.current_stream(g_s.device)), None
+
+
+def gaussian_filter(u, filt):
+    """Differentiable Gaussian filtering of the controls u (n_steps x R)."""
+    return FilterFunction.apply(u, filt)

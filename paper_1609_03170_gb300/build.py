@@ -16,7 +16,8 @@ SRC = os.path.join(PKG, "csrc")
 INC = os.path.join(ROOT, "include")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgrape.so")
-SOURCES = ["grape_kernels_df.cu", "grape_kernels_f64.cu", "grape_api.cu", "grape_lbfgs.cu"]
+SOURCES = ["grape_kernels_df.cu", "grape_kernels_f64.cu", "grape_api.cu", "grape_lbfgs.cu",
+           "grape_filter.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -17,7 +17,6 @@
 #include <cstdio>
 #include <condition_variable>
 #include <deque>
-#include <map>
 #include <mutex>
 #include <thread>
 #include <complex>
@@ -237,6 +236,10 @@ struct grape_problem {
     double2 *d_Y = nullptr, *d_K = nullptr, *d_ckpt = nullptr;
     double2 *d_out = nullptr;        // complex128 staging of rho(T)
     double *d_part = nullptr;        // per-split partial traces [n_slices][npairs][R]
+    // filtered gradients: subpixel controls and their gradient [n_slices][R],
+    // staged controls and gradient [n_steps][R] for host pointers
+    double *d_fs = nullptr, *d_fgs = nullptr, *d_fu = nullptr, *d_fgu = nullptr;
+    int f_steps = 0;
     double *d_u = nullptr, *d_F = nullptr, *d_G = nullptr;
     size_t bytes = 0;
     cudaStream_t s1 = nullptr;       // high-priority stream the gradient sweeps run on
@@ -1319,6 +1322,92 @@ grape_status grape_forward(grape_problem_t P, const double *u, double *F, double
     if (sync) {
         GRAPE_CUDA_TRY(cudaStreamSynchronize(s));
         if (P->grid) return grape_problem_status(P);
+    }
+    return GRAPE_OK;
+}
+
+namespace {
+
+grape_status filter_args(int32_t N, int32_t M, int32_t R, double Dt, double dt, const double *omega0,
+                         FilterArgs *a) {
+    if (N < 1 || M < 1) return fail(GRAPE_EINVAL, "filter: n_steps and n_sub must be >= 1");
+    if (R < 1 || R > GRAPE_MAXR) return fail(GRAPE_EINVAL, "filter: n_controls must be in [1, 8]");
+    if (!(Dt > 0.0) || !(dt > 0.0) || !std::isfinite(Dt) || !std::isfinite(dt))
+        return fail(GRAPE_EINVAL, "filter: Dt and dt must be positive and finite");
+    if (!omega0) return fail(GRAPE_EINVAL, "filter: omega0 is NULL");
+    std::memset(a, 0, sizeof(*a));
+    a->N = N;
+    a->M = M;
+    a->R = R;
+    a->Dt = Dt;
+    a->dt = dt;
+    for (int k = 0; k < R; ++k) {
+        if (!(omega0[k] > 0.0) || !std::isfinite(omega0[k]))
+            return fail(GRAPE_EINVAL, "filter: omega0 must be positive and finite");
+        a->w0[k] = omega0[k];
+    }
+    return GRAPE_OK;
+}
+
+grape_status filter_call(int32_t N, int32_t M, int32_t R, double Dt, double dt, const double *omega0,
+                         const double *in, double *out, bool adjoint, void *stream) {
+    FilterArgs a;
+    grape_status st = filter_args(N, M, R, Dt, dt, omega0, &a);
+    if (st != GRAPE_OK) return st;
+    if (!is_device_ptr(in) || !is_device_ptr(out))
+        return fail(GRAPE_EINVAL, "filter: input and output must be device memory");
+    a.in = in;
+    a.out = out;
+    GRAPE_CUDA_TRY(grape_launch_filter(a, adjoint, static_cast<cudaStream_t>(stream)));
+    return GRAPE_OK;
+}
+
+}  // namespace
+
+grape_status grape_filter_apply(int32_t n_steps, int32_t n_sub, int32_t n_controls, double Dt, double dt,
+                                const double *omega0, const double *u, double *s, void *stream) {
+    return filter_call(n_steps, n_sub, n_controls, Dt, dt, omega0, u, s, false, stream);
+}
+
+grape_status grape_filter_adjoint(int32_t n_steps, int32_t n_sub, int32_t n_controls, double Dt, double dt,
+                                  const double *omega0, const double *g_s, double *g_u, void *stream) {
+    return filter_call(n_steps, n_sub, n_controls, Dt, dt, omega0, g_s, g_u, true, stream);
+}
+
+grape_status grape_gradient_filtered(grape_problem_t P, int32_t n_steps, const double *omega0,
+                                     const double *u, double *F, double *grad, void *stream) {
+    if (!P || !u || !F || !grad) return fail(GRAPE_EINVAL, "NULL problem, u, F or grad");
+    if (P->R < 1) return fail(GRAPE_EINVAL, "filtered gradient: the problem has no controls");
+    DeviceGuard g(P->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FilterArgs a;
+    grape_status st = filter_args(n_steps, P->n_slices, P->R, P->T / n_steps, P->T / P->n_slices, omega0, &a);
+    if (st != GRAPE_OK) return st;
+    const size_t sub_b = (size_t)P->n_slices * P->R * sizeof(double);
+    const size_t step_b = (size_t)n_steps * P->R * sizeof(double);
+    if (!P->d_fs) {
+        P->d_fs = static_cast<double *>(P->alloc(sub_b));
+        P->d_fgs = static_cast<double *>(P->alloc(sub_b));
+        if (!P->d_fs || !P->d_fgs) return fail(GRAPE_ENOMEM, "cudaMalloc failed for filtered controls");
+    }
+    const bool u_dev = is_device_ptr(u), g_dev = is_device_ptr(grad);
+    if ((!u_dev || !g_dev) && P->f_steps < n_steps) {
+        P->d_fu = static_cast<double *>(P->alloc(step_b));
+        P->d_fgu = static_cast<double *>(P->alloc(step_b));
+        if (!P->d_fu || !P->d_fgu) return fail(GRAPE_ENOMEM, "cudaMalloc failed for staged controls");
+        P->f_steps = n_steps;
+    }
+    if (!u_dev) GRAPE_CUDA_TRY(cudaMemcpyAsync(P->d_fu, u, step_b, cudaMemcpyHostToDevice, s));
+    a.in = u_dev ? u : P->d_fu;
+    a.out = P->d_fs;
+    GRAPE_CUDA_TRY(grape_launch_filter(a, false, s));
+    if ((st = grape_gradient(P, P->d_fs, F, P->d_fgs, stream)) != GRAPE_OK) return st;
+    a.in = P->d_fgs;
+    a.out = g_dev ? grad : P->d_fgu;
+    GRAPE_CUDA_TRY(grape_launch_filter(a, true, s));
+    if (!g_dev) {
+        GRAPE_CUDA_TRY(cudaMemcpyAsync(grad, P->d_fgu, step_b, cudaMemcpyDeviceToHost, s));
+        GRAPE_CUDA_TRY(cudaStreamSynchronize(s));
     }
     return GRAPE_OK;
 }

@@ -152,3 +152,14 @@ struct LbfgsArgs {
 };
 
 cudaError_t grape_launch_lbfgs(const LbfgsArgs &a, cudaStream_t s);
+
+// Gaussian control filter (App. A): `in` -> `out`, row-major [index][control];
+// forward: N controls -> M subpixels, adjoint: M subpixel gradients -> N.
+struct FilterArgs {
+    int N, M, R;
+    double Dt, dt;                      // control and subpixel lengths
+    double w0[GRAPE_MAXR];              // reference bandwidth per control
+    const double *in;
+    double *out;
+};
+cudaError_t grape_launch_filter(const FilterArgs &a, bool adjoint, cudaStream_t s);

@@ -219,6 +219,55 @@ class GrapeProblem:
         return float(F[0]), G
 
 
+    def gradient_filtered(self, u, omega0, stream=None):
+        """Phi and dPhi/du for n_steps Gaussian-filtered controls u
+        (n_steps x R); the problem's slices are the subpixels (App. A)."""
+        n_steps = int(u.shape[0])
+        if _is_cuda(u):
+            import torch
+            F = torch.empty(1, dtype=torch.float64, device=u.device)
+            G = torch.empty((n_steps, self.R), dtype=torch.float64, device=u.device)
+            _lib.grape_gradient_filtered(self._h, n_steps, self.R, omega0, u.data_ptr(),
+                                         F.data_ptr(), G.data_ptr(), _stream_ptr(stream))
+            return F, G
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        F = np.zeros(1)
+        G = np.zeros((n_steps, self.R))
+        _lib.grape_gradient_filtered(self._h, n_steps, self.R, omega0, u.ctypes.data,
+                                     F.ctypes.data, G.ctypes.data, _stream_ptr(stream))
+        return float(F[0]), G
+
+
+class GaussianFilter:
+    """Gaussian filter of the controls (App. A) on CUDA tensors: n_steps
+    controls over [0, T) -> n_sub subpixels, and the transposed map for
+    gradients.  omega0: one reference bandwidth per control (or one for all)."""
+
+    def __init__(self, n_steps: int, n_sub: int, T: float, omega0, n_controls: int):
+        self.n_steps, self.n_sub, self.R = int(n_steps), int(n_sub), int(n_controls)
+        self.Dt, self.dt = T / n_steps, T / n_sub
+        self.omega0 = list(omega0) if hasattr(omega0, "__len__") else [float(omega0)] * self.R
+
+    @staticmethod
+    def omega0_from_bandwidth(omega_b: float) -> float:
+        """w0 = wB / sqrt(-ln(1/sqrt 2)) for a 3 dB bandwidth wB."""
+        return omega_b / np.sqrt(-np.log(1.0 / np.sqrt(2.0)))
+
+    def apply(self, u, stream=None):
+        import torch
+        s = torch.empty((self.n_sub, self.R), dtype=torch.float64, device=u.device)
+        _lib.grape_filter_apply(self.n_steps, self.n_sub, self.R, self.Dt, self.dt, self.omega0,
+                                u.contiguous().data_ptr(), s.data_ptr(), _stream_ptr(stream))
+        return s
+
+    def adjoint(self, g_s, stream=None):
+        import torch
+        g_u = torch.empty((self.n_steps, self.R), dtype=torch.float64, device=g_s.device)
+        _lib.grape_filter_adjoint(self.n_steps, self.n_sub, self.R, self.Dt, self.dt, self.omega0,
+                                  g_s.contiguous().data_ptr(), g_u.data_ptr(), _stream_ptr(stream))
+        return g_u
+
+
 class GrapeBatch:
     """Many GrapeProblems evaluated by one batched, graph-captured launch
     (grape_batch_gradient).  Inputs and outputs are CUDA tensors."""

@@ -121,3 +121,16 @@ def test_create_without_gpu_reports_cuda_error():
 def test_set_tile_validates_on_the_host():
     lib = _lib.load()
     assert lib.grape_problem_set_tile(None, 4, 128) == _lib.GRAPE_EINVAL
+
+
+def test_filter_validates_on_the_host():
+    lib = _lib.load()
+    w = (ctypes.c_double * 2)(1.0, 1.0)
+    bad = (ctypes.c_double * 2)(1.0, -1.0)
+    assert lib.grape_filter_apply(0, 10, 2, 1.0, 0.1, w, None, None, None) == _lib.GRAPE_EINVAL
+    assert lib.grape_filter_apply(1, 10, 9, 1.0, 0.1, w, None, None, None) == _lib.GRAPE_EINVAL
+    assert lib.grape_filter_adjoint(1, 10, 2, 0.0, 0.1, w, None, None, None) == _lib.GRAPE_EINVAL
+    assert lib.grape_filter_adjoint(1, 10, 2, 1.0, 0.1, bad, None, None, None) == _lib.GRAPE_EINVAL
+    # valid sizes, but no device buffers
+    assert lib.grape_filter_apply(1, 10, 2, 1.0, 0.1, w, None, None, None) == _lib.GRAPE_EINVAL
+    assert lib.grape_gradient_filtered(None, 1, w, None, None, None, None) == _lib.GRAPE_EINVAL
