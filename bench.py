@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"],
                     help="kernel arithmetic: double-float on FP32 pipes or native FP64")
-    ap.add_argument("--workload", default="d120", choices=["d120", "d20", "batch256", "d600", "serve"])
+    ap.add_argument("--workload", default="d120", choices=["d120", "d20", "d120f", "batch256", "d600", "serve"])
     ap.add_argument("--scale", type=float, default=None,
                     help="slice-count multiplier of the batch256/serve/d600 workloads")
     ap.add_argument("--jobs", type=int, default=64, help="serve: jobs in the trace")
@@ -384,6 +384,49 @@ def run_d20(args):
         "gpu_launches": P.gradient_launches() * args.steps})), flush=True)
 
 
+def run_d120f(args):
+    """The d=120 problem with Gaussian-filtered controls (App. A): 200
+    controls of Delta t = 10 delta t on the 2000 subpixels of the headline
+    problem, bandwidth wB = 2 pi x 100 MHz with kappa = 2 pi x 1.1 MHz
+    (the paper's reset parameters), i.e. w0 = (100 / 1.1) / 0.5887 kappa."""
+    import torch
+    import workloads
+    from paper_1609_03170_gb300 import GaussianFilter, GrapeProblem
+    w = workloads.transmon_resonator_d120()
+    n_steps = w.n_slices // 10
+    w0 = GaussianFilter.omega0_from_bandwidth(100.0 / 1.1)
+    rng = np.random.default_rng(1609)
+    u = torch.from_numpy(rng.uniform(-1, 1, size=(n_steps, w.n_controls))).cuda()
+    P = GrapeProblem.from_workload(w)
+    stream = torch.cuda.Stream()
+    for _ in range(max(3, args.warmup)):
+        P.gradient_filtered(u, [w0] * w.n_controls, stream=stream)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        P.gradient_filtered(u, [w0] * w.n_controls, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # the two filter launches alone, on the same stream
+    f = GaussianFilter(n_steps, w.n_slices, w.T, w0, w.n_controls)
+    gs = torch.ones((w.n_slices, w.n_controls), dtype=torch.float64, device="cuda")
+    reps = 50
+    ev0.record(stream)
+    for _ in range(reps):
+        f.apply(u, stream=stream)
+        f.adjoint(gs, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    fms = ev0.elapsed_time(ev1) / reps
+    print(json.dumps(_base_line(args, "transmon_resonator_d120_filtered", 1000.0 / ms, UNIT, ms, {
+        "config": {"workload": "transmon_resonator_d120_filtered", "d": 120, "n_controls_steps": n_steps,
+                   "n_subpixels": w.n_slices, "omega0_kappa": w0, "n_rk": 4, "n_states": 3},
+        "filter_ms_per_step": fms, "filter_share": fms / ms,
+        "gpu_launches": (P.gradient_launches() + 2) * args.steps})), flush=True)
+
+
 def serve_trace(n_jobs, scale, rate, seed=1609):
     """Seeded trace: (arrival time, workload); 88% batch-distribution problems,
     10% d=120 / N_t=2000 problems, 2% d=300 / N_t=10000 problems (slice
@@ -468,7 +511,7 @@ def main():
         import torch
         torch.cuda.set_device(0)
         {"batch256": run_batch256, "d600": run_d600, "serve": run_serve,
-         "d20": run_d20}[args.workload](args)
+         "d20": run_d20, "d120f": run_d120f}[args.workload](args)
         return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":

@@ -19,6 +19,8 @@ Modules
   sparse     ctypes front end of grape_oracle.c, the same algorithm in plain C
              with sparse operators, for sizes the dense code cannot reach
   filter     Gaussian filtering of the controls and its chain rule (App. A)
+  penalty    photon-number penalty Phi_0 - beta Phi_p and its gradient through
+             the modified backward evolution (Sec. 5, App. B)
   lbfgs      projected L-BFGS steps of the serving optimiser
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,

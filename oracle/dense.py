@@ -96,8 +96,14 @@ def forward(model, u, rho0s, sigma, T, n_rk):
     return F, np.stack(rhoT)
 
 
-def gradient_exact(model, u, rho0s, sigma, T, n_rk):
+def gradient_exact(model, u, rho0s, sigma, T, n_rk, source=None):
     """Phi and dPhi/du_k(j), reverse mode through every RK4 stage.
+
+    `source` (a d x d matrix, default none) is added to the adjoint at every
+    slice boundary, the final time included: the gradient of a cost with the
+    running term sum_n Re Tr(source rho_n) over the boundary states rho_0 ..
+    rho_N (App. B, the photon-number penalty).  The returned Phi is the
+    final-time part only.
 
     For one substep with stage inputs y_1..y_4 and stage outputs
     k_s = L y_s, given mu = dPhi/d(rho after the substep) as a matrix of the
@@ -128,6 +134,8 @@ def gradient_exact(model, u, rho0s, sigma, T, n_rk):
             stages.append(per)
         F += cost(sig, rho)
         mu = np.array(sig, dtype=np.complex128)
+        if source is not None:
+            mu = mu + source
         for j in reversed(range(n_slices)):
             H = operators.hamiltonian(model, u[j])
             fd = lambda X, H=H: lindblad_dual(H, model.jumps, X)
@@ -147,14 +155,20 @@ def gradient_exact(model, u, rho0s, sigma, T, n_rk):
                         acc += np.real(np.trace(kb @ (-1j * (Hk @ y - y @ Hk))))
                     G[j, k] += acc
                 mu = mu + yb1 + yb2 + yb3 + yb4
+            if source is not None:
+                mu = mu + source
     return F, G
 
 
-def backward_targets(model, u, sigma, T, n_rk):
+def backward_targets(model, u, sigma, T, n_rk, source=None):
     """lambda_j for j = N..0 by backward RK4 on L^dag from lambda_N = sigma
-    (Sec. 3 backward integration; lambda_{j-1} = L_j^dag lambda_j, Eq. lambda)."""
+    (Sec. 3 backward integration; lambda_{j-1} = L_j^dag lambda_j, Eq. lambda).
+    With `source`, App. B's modified backward evolution: the source is added
+    to lambda_N and after every backward slice."""
     n_slices, dt, h = _geometry(T, u, n_rk)
     lam = np.array(sigma, dtype=np.complex128)
+    if source is not None:
+        lam = lam + source
     out = [None] * (n_slices + 1)
     out[n_slices] = lam
     for j in reversed(range(n_slices)):
@@ -162,13 +176,16 @@ def backward_targets(model, u, sigma, T, n_rk):
         fd = lambda X, H=H: lindblad_dual(H, model.jumps, X)
         for _ in range(n_rk):
             lam, _ = rk4_step(fd, lam, h)
+        if source is not None:
+            lam = lam + source
         out[j] = lam
     return out
 
 
-def gradient_first_order(model, u, rho0s, sigma, T, n_rk):
+def gradient_first_order(model, u, rho0s, sigma, T, n_rk, source=None):
     """Eq. (dphidu): dPhi/du_k(j) = Re(-i Delta t Tr(lambda_j [H_k, rho_j])),
-    with rho_j and lambda_j both taken at t = j Delta t, j = 1..N."""
+    with rho_j and lambda_j both taken at t = j Delta t, j = 1..N (lambda
+    from backward_targets, with `source` as there)."""
     n_slices, dt, h = _geometry(T, u, n_rk)
     R = len(model.Hc)
     G = np.zeros((n_slices, R))
@@ -177,7 +194,7 @@ def gradient_first_order(model, u, rho0s, sigma, T, n_rk):
         sig = _sigma_for(sigma, s)
         rhoT, traj = propagate(model, u, rho0, T, n_rk, keep_slices=True)
         F += cost(sig, rhoT)
-        lams = backward_targets(model, u, sig, T, n_rk)
+        lams = backward_targets(model, u, sig, T, n_rk, source)
         for j in range(1, n_slices + 1):
             rho_j, lam_j = traj[j], lams[j]
             for k, Hk in enumerate(model.Hc):
