@@ -159,6 +159,21 @@ grape_status grape_problem_memory(grape_problem_t problem, size_t *bytes);
 grape_status grape_problem_geometry(grape_problem_t problem, int32_t *cluster,
                                     int32_t *threads, int32_t *elems_per_thread);
 
+/* Running-cost penalty (Sec. 5 and App. B, the photon-number penalty):
+ * the performance index becomes Phi = Phi_0 - beta Phi_p with
+ *   Phi_p = dt * sum over initial states and boundaries n = 0..n_slices of
+ *           Re Tr(A rho_n),   dt = T / n_slices,
+ * for an operator A diagonal in the basis (diag: host, d real values; a^dag a
+ * is diag[n Q + q] = n).  The gradient comes from one modified backward
+ * evolution: -beta dt A is added to the adjoint at every slice boundary and
+ * at the final time, in the exact and the first-order gradient alike.
+ * grape_forward and grape_gradient then return the penalised Phi (the
+ * forward sweep runs in chunks of 64 slices to reach every boundary state).
+ * beta = 0 or diag = NULL removes the penalty.  Waits for the device.
+ * Errors: GRAPE_EINVAL (NULL problem, non-finite values), GRAPE_ENOMEM,
+ * GRAPE_ECUDA.  grape_gradient_static rejects penalised problems. */
+grape_status grape_problem_set_penalty(grape_problem_t problem, const double *diag, double beta);
+
 /* Sets the propagation tile of a cluster-kernel problem: the cluster width
  * (1, 2, 4, 8 or 16 CTAs per initial state, each CTA owning an equal share
  * of the state's entries) and the threads per CTA (a multiple of 32 in

@@ -56,7 +56,8 @@ _lib = None
 
 EXPORTS = ["grape_problem_create", "grape_problem_destroy", "grape_forward", "grape_gradient",
            "grape_filter_apply", "grape_filter_adjoint", "grape_gradient_filtered",
-           "grape_problem_memory", "grape_problem_geometry", "grape_problem_set_tile", "grape_set_profiling",
+           "grape_problem_memory", "grape_problem_geometry", "grape_problem_set_tile",
+           "grape_problem_set_penalty", "grape_set_profiling",
            "grape_phase_times", "grape_gradient_launches", "grape_gradient_static",
            "grape_batch_create", "grape_batch_destroy", "grape_batch_gradient", "grape_batch_info",
            "grape_problem_kernel", "grape_problem_status", "grape_server_create",
@@ -122,6 +123,8 @@ def load(build_if_missing: bool = True):
     lib.grape_problem_memory.restype = c_int32
     lib.grape_problem_geometry.argtypes = [c_void_p, P(c_int32), P(c_int32), P(c_int32)]
     lib.grape_problem_geometry.restype = c_int32
+    lib.grape_problem_set_penalty.argtypes = [c_void_p, P(c_double), c_double]
+    lib.grape_problem_set_penalty.restype = c_int32
     lib.grape_problem_set_tile.argtypes = [c_void_p, c_int32, c_int32]
     lib.grape_problem_set_tile.restype = c_int32
     lib.grape_set_profiling.argtypes = [c_void_p, c_int32]
@@ -279,6 +282,14 @@ def grape_problem_geometry(h):
     check(load().grape_problem_geometry(h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(e)),
           "grape_problem_geometry")
     return int(c.value), int(t.value), int(e.value)
+
+
+def grape_problem_set_penalty(h, diag, beta: float) -> None:
+    if diag is None:
+        check(load().grape_problem_set_penalty(h, None, 0.0), "grape_problem_set_penalty")
+        return
+    a = (c_double * len(diag))(*[float(x) for x in diag])
+    check(load().grape_problem_set_penalty(h, a, float(beta)), "grape_problem_set_penalty")
 
 
 def grape_problem_set_tile(h, cluster: int, threads: int) -> None:

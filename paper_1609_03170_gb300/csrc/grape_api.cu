@@ -240,6 +240,14 @@ struct grape_problem {
     // staged controls and gradient [n_steps][R] for host pointers
     double *d_fs = nullptr, *d_fgs = nullptr, *d_fu = nullptr, *d_fgu = nullptr;
     int f_steps = 0;
+    // running-cost penalty (App. B): diagonal operator A, source -beta dt A,
+    // per-boundary values Re Tr(A rho_n) summed over states [n_slices + 1],
+    // boundary states of a chunked forward sweep
+    bool penalty = false;
+    double pen_beta = 0.0;
+    double *d_pdiag = nullptr, *d_src = nullptr, *d_pen = nullptr;
+    double2 *d_fwd_bounds = nullptr;
+    static constexpr int kPenChunk = 64;
     double *d_u = nullptr, *d_F = nullptr, *d_G = nullptr;
     size_t bytes = 0;
     cudaStream_t s1 = nullptr;       // high-priority stream the gradient sweeps run on
@@ -723,6 +731,7 @@ PropArgs base_args(const grape_problem *P, int dir, const double *u) {
     a.maxwin = P->maxwin;
     a.rt_rows = P->rt_rows;
     a.fold = (P->variant & 2) ? P->fold : 0;
+    a.src = P->penalty ? P->d_src : nullptr;
     a.gbuf = P->d_gbuf;
     a.gbar = P->d_gbar;
     a.ce = P->ce;
@@ -794,12 +803,14 @@ int adjoint_chunks(const grape_problem *P, long long j0, long long j1) {
 int gradient_launch_count(const grape_problem *P, int seg, int nseg) {
     if (nseg <= 0) return -1;
     int n = 2;                                    // forward sweep, cost
+    if (P->penalty) n += 3;                       // adjoint start, final-state value, sum
     for (int gi = 0; gi < nseg; ++gi) {
         const long long j0 = (long long)gi * seg;
         const long long j1 = std::min<long long>(P->n_slices, j0 + seg);
         const int nch = adjoint_chunks(P, j0, j1);
         n += (nseg > 1 ? 1 : 0) + nch;
         if (P->R > 0) n += nch * (P->trace.nsplit > 1 ? 2 : 1);
+        if (P->penalty) n += 1;                   // boundary values of the segment
     }
     return n;
 }
@@ -880,6 +891,25 @@ grape_status stage_inputs(grape_problem *P, const double *u, const double **u_de
 
 }  // namespace
 
+// Running-cost penalty launches (App. B).  pen_rows: Re Tr(A rho_n) for
+// `rows` consecutive boundary states stored `stride` entries apart.
+grape_status pen_rows(grape_problem *P, const void *x, long long stride, long long rows, long long first,
+                      cudaStream_t s) {
+    GRAPE_CUDA_TRY(P->prec == GRAPE_PREC_FP64
+                       ? grape_launch_penalty_rows_f64(x, stride, (int)rows, P->ns, P->d, P->d_pdiag,
+                                                       P->d_pen + first, s)
+                       : grape_launch_penalty_rows_df(x, stride, (int)rows, P->ns, P->d, P->d_pdiag,
+                                                      P->d_pen + first, s));
+    return GRAPE_OK;
+}
+grape_status pen_finish(grape_problem *P, double *F, cudaStream_t s) {
+    const double scale = P->pen_beta * P->T / P->n_slices;
+    GRAPE_CUDA_TRY(P->prec == GRAPE_PREC_FP64
+                       ? grape_launch_penalty_finish_f64(P->d_pen, P->n_slices + 1, scale, F, s)
+                       : grape_launch_penalty_finish_df(P->d_pen, P->n_slices + 1, scale, F, s));
+    return GRAPE_OK;
+}
+
 // One gradient evaluation on stream s with device pointers only: forward
 // sweep (stage storage or checkpoints), cost, then per segment (last first)
 // the recomputed forward stage inputs, the adjoint sweep in chunks and the
@@ -912,6 +942,15 @@ grape_status run_gradient(grape_problem *P, const double *ud, double *Fd, double
         return st;
     GRAPE_CUDA_TRY(cudaMemcpyAsync(S.mu, P->d_sigma, mat * sizeof(double2),
                                    cudaMemcpyDeviceToDevice, s));
+    // boundary state n of a segment in the stage storage: the input of the
+    // slice's first stage (exact mode) or the stored boundary (first order)
+    const long long bstride = (long long)(exact ? (size_t)P->n_rk * 4 * mat : mat);
+    if (P->penalty) {
+        GRAPE_CUDA_TRY(P->prec == GRAPE_PREC_FP64
+                           ? grape_launch_add_diag_f64(S.mu, P->d_src, P->d, P->ns, s)
+                           : grape_launch_add_diag_df(S.mu, P->d_src, P->d, P->ns, s));
+        if ((st = pen_rows(P, S.x, 0, 1, P->n_slices, s)) != GRAPE_OK) return st;
+    }
     for (int gi = S.nseg - 1; gi >= 0; --gi) {
         const long long j0 = (long long)gi * S.seg;
         const long long j1 = std::min<long long>(P->n_slices, j0 + S.seg);
@@ -925,6 +964,7 @@ grape_status run_gradient(grape_problem *P, const double *ud, double *Fd, double
             else { r.bound_store = S.Y; r.bound_step = P->n_rk; }
             if ((st = launch_prop(P, r, s)) != GRAPE_OK) return st;
         }
+        if (P->penalty && (st = pen_rows(P, S.Y, bstride, j1 - j0, j0, s)) != GRAPE_OK) return st;
         // adjoint sweep in chunks (last slices first); the trace of each
         // finished chunk runs on s2, overlapping the next chunk
         const int nch = adjoint_chunks(P, j0, j1);
@@ -977,6 +1017,7 @@ grape_status run_gradient(grape_problem *P, const double *ud, double *Fd, double
             GRAPE_CUDA_TRY(cudaStreamWaitEvent(s, S.ev[grape_problem::kMaxChunks], 0));
         }
     }
+    if (P->penalty) return pen_finish(P, Fd, s);     // Phi = Phi_0 - beta dt sum_n Tr(A rho_n)
     return GRAPE_OK;
 }
 
@@ -1223,6 +1264,36 @@ grape_status grape_problem_geometry(grape_problem_t P, int32_t *cluster, int32_t
     return GRAPE_OK;
 }
 
+grape_status grape_problem_set_penalty(grape_problem_t P, const double *diag, double beta) {
+    if (!P) return fail(GRAPE_EINVAL, "NULL problem");
+    if (!std::isfinite(beta)) return fail(GRAPE_EINVAL, "penalty weight must be finite");
+    if (!diag || beta == 0.0) {
+        P->penalty = false;
+        P->pen_beta = 0.0;
+        return GRAPE_OK;
+    }
+    for (int i = 0; i < P->d; ++i)
+        if (!std::isfinite(diag[i])) return fail(GRAPE_EINVAL, "penalty operator entries must be finite");
+    DeviceGuard g(P->device);
+    const double dt = P->T / P->n_slices;
+    std::vector<double> a(diag, diag + P->d), src(P->d);
+    for (int i = 0; i < P->d; ++i) src[i] = -beta * dt * a[i];
+    if (!P->d_pdiag) {
+        P->d_pdiag = static_cast<double *>(P->alloc(P->d * sizeof(double)));
+        P->d_src = static_cast<double *>(P->alloc(P->d * sizeof(double)));
+        P->d_pen = static_cast<double *>(P->alloc((size_t)(P->n_slices + 1) * sizeof(double)));
+        if (!P->d_pdiag || !P->d_src || !P->d_pen) return fail(GRAPE_ENOMEM, "cudaMalloc failed for the penalty");
+    }
+    // callers' kernels may still read the old values: order after the device
+    GRAPE_CUDA_TRY(cudaDeviceSynchronize());
+    GRAPE_CUDA_TRY(cudaMemcpy(P->d_pdiag, a.data(), P->d * sizeof(double), cudaMemcpyHostToDevice));
+    GRAPE_CUDA_TRY(cudaMemcpy(P->d_src, src.data(), P->d * sizeof(double), cudaMemcpyHostToDevice));
+    GRAPE_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
+    P->pen_beta = beta;
+    P->penalty = true;
+    return GRAPE_OK;
+}
+
 grape_status grape_problem_set_tile(grape_problem_t P, int32_t cluster, int32_t threads) {
     if (!P) return fail(GRAPE_EINVAL, "NULL problem");
     if (!(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8 || cluster == 16))
@@ -1299,12 +1370,35 @@ grape_status grape_forward(grape_problem_t P, const double *u, double *F, double
     a.sub_end = (long long)P->n_slices * P->n_rk;
     a.x_in = P->d_rho0;
     a.x_out = P->d_x;
-    if ((st = launch_prop(P, a, s)) != GRAPE_OK) return st;
+    const size_t mat = P->d2 * P->ns;
+    if (!P->penalty) {
+        if ((st = launch_prop(P, a, s)) != GRAPE_OK) return st;
+    } else {
+        // the running cost needs every boundary state: chunks of kPenChunk
+        // slices keep their boundaries in a small buffer
+        if (!P->d_fwd_bounds) {
+            P->d_fwd_bounds = static_cast<double2 *>(
+                P->alloc((size_t)(grape_problem::kPenChunk + 1) * mat * sizeof(double2)));
+            if (!P->d_fwd_bounds) return fail(GRAPE_ENOMEM, "cudaMalloc failed for boundary states");
+        }
+        for (long long j0 = 0; j0 < P->n_slices; j0 += grape_problem::kPenChunk) {
+            const long long j1 = std::min<long long>(P->n_slices, j0 + grape_problem::kPenChunk);
+            a.sub_begin = j0 * P->n_rk;
+            a.sub_end = j1 * P->n_rk;
+            a.x_in = j0 == 0 ? P->d_rho0 : P->d_x;
+            a.bound_store = P->d_fwd_bounds;
+            a.bound_step = P->n_rk;
+            if ((st = launch_prop(P, a, s)) != GRAPE_OK) return st;
+            if ((st = pen_rows(P, P->d_fwd_bounds, (long long)mat, j1 - j0, j0, s)) != GRAPE_OK) return st;
+        }
+        if ((st = pen_rows(P, P->d_x, 0, 1, P->n_slices, s)) != GRAPE_OK) return st;
+    }
     const bool f_dev = is_device_ptr(F);
     if ((st = timed(P, PH_COST, s, [&] {
              return k_cost(P, P->d_x, f_dev ? F : P->d_F, s);
          })) != GRAPE_OK)
         return st;
+    if (P->penalty && (st = pen_finish(P, f_dev ? F : P->d_F, s)) != GRAPE_OK) return st;
     bool sync = false;
     if (rhoT) {
         const size_t n = P->d2 * P->ns;
@@ -1500,6 +1594,8 @@ grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F
     DeviceGuard g(P->device);
     if (!is_device_ptr(u) || !is_device_ptr(F) || (P->R > 0 && !is_device_ptr(grad)))
         return fail(GRAPE_EINVAL, "grape_gradient_static takes device pointers for u, F and grad");
+    if (P->penalty)
+        return fail(GRAPE_EINVAL, "grape_gradient_static does not evaluate the running-cost penalty");
     if (!g_static_ptr[P->device]) {   // once per device, with that device current
         void *ptr = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);

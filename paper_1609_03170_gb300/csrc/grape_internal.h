@@ -67,6 +67,7 @@ struct PropArgs {
     int maxwin;                         // largest window (entries) of the cluster
     int rt_rows;                        // rows of the largest push table
     int fold;                           // Hermitian kernel: own-entry coefficients folded (D table)
+    const double *src;                  // adjoint source on the diagonal per row (App. B), or null
     // grid kernel (state windows in global memory, one grid barrier per stage)
     void *gbuf;                         // [2][n_states][d*d] stage-input buffers
     unsigned *gbar;                     // [0] arrivals, [1] generation, [2] error flag
@@ -123,7 +124,14 @@ struct TraceArgs {
     cudaError_t grape_launch_grid_##SUFFIX(const PropArgs &p, int nblocks, int variant,         \
                                            size_t smem, cudaStream_t stream);                   \
     cudaError_t grape_prepare_grid_##SUFFIX(int variant, size_t smem_total, size_t smem,        \
-                                            int *max_blocks);
+                                            int *max_blocks);                                  \
+    cudaError_t grape_launch_add_diag_##SUFFIX(void *x, const double *src, int d, int n_states, \
+                                               cudaStream_t stream);                            \
+    cudaError_t grape_launch_penalty_rows_##SUFFIX(const void *x, long long row_stride, int rows, \
+                                                   int n_states, int d, const double *diag,     \
+                                                   double *out, cudaStream_t stream);           \
+    cudaError_t grape_launch_penalty_finish_##SUFFIX(const double *pen, long long count,        \
+                                                     double scale, double *F, cudaStream_t stream);
 
 GRAPE_DECLARE_LAUNCHERS(f64)
 GRAPE_DECLARE_LAUNCHERS(df)

@@ -40,6 +40,17 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release;\n\t"
                  "barrier.cluster.wait.acquire;" ::: "memory");
 }
+// The running cost's source (App. B, photon-number penalty): added to the
+// adjoint's diagonal when a backward sweep crosses a slice boundary, i.e.
+// after the slice's first substep (n a multiple of n_RK).
+template <class Num>
+__device__ __forceinline__ typename Num::val with_source(const PropArgs &p, long long n, int i, int j,
+                                                         typename Num::val v) {
+    if (p.src && p.reverse && (n % p.n_rk) == 0 && i == j)
+        return Num::add_real(v, Num::real_const(p.src[i]));
+    return v;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -221,8 +232,9 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_kernel(const PropA
                     as[li] = Num::store(acc);
                     z = Num::lin2(cg[s + 1], x, cb[s + 1], w);
                 } else {
-                    xs[li] = Num::store(acc);
-                    z = Num::scale(cg[0], acc);
+                    const V nx = with_source<Num>(p, n, ij.x, ij.y, acc);
+                    xs[li] = Num::store(nx);
+                    z = Num::scale(cg[0], nx);
                 }
                 push_value(nxt, p, rank, e, Num::store(z));
             }
@@ -547,8 +559,9 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                     as[li] = Num::store(acc);
                     z = unit_g ? Num::axpy(cb[s + 1], w, x) : Num::lin2(cg[s + 1], x, cb[s + 1], w);
                 } else {
-                    xs[li] = Num::store(acc);
-                    z = Num::scale(cg[0], acc);
+                    const V nx = with_source<Num>(p, n, ij.x, ij.y, acc);
+                    xs[li] = Num::store(nx);
+                    z = Num::scale(cg[0], nx);
                 }
                 hpush_pre(rowtab, rstride, ij.x - rfirst, ij.y, boff, Num::store(z));
                 if (ij.y > ij.x && ij.y - ij.x <= hb)
@@ -764,8 +777,9 @@ __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const Pro
                     as[li] = Num::store(acc);
                     z = unit_g ? Num::axpy(cb[s + 1], w, x) : Num::lin2(cg[s + 1], x, cb[s + 1], w);
                 } else {
-                    xs[li] = Num::store(acc);
-                    z = Num::scale(cg[0], acc);
+                    const V nx = with_source<Num>(p, n, q.x, q.y, acc);
+                    xs[li] = Num::store(nx);
+                    z = Num::scale(cg[0], nx);
                 }
                 store_herm<Num>(nxt + (size_t)q.z * d2, d, q.x, q.y, Num::store(z));
             }
@@ -874,6 +888,44 @@ static __global__ void __launch_bounds__(256) trace_finish_kernel(const TraceArg
     double s = 0.0;
     for (int sp = 0; sp < p.nsplit; ++sp) s += p.part[((size_t)row * p.nsplit + sp) * p.R + k];
     p.G[(size_t)row * p.R + k] = s;
+}
+
+// x[s][i][i] += src[i] (real): the adjoint's start value at the final time
+// carries the running cost's last term (App. B)
+template <class Num>
+__global__ void __launch_bounds__(256) add_diag_kernel(void *x_v, const double *src, int d, int n_states) {
+    using S = typename Num::store_t;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= d * n_states) return;
+    const int st = idx / d, i = idx - st * d;
+    S *x = static_cast<S *>(x_v) + (size_t)st * d * d + (size_t)i * d + i;
+    *x = Num::store(Num::add_real(Num::load(*x), Num::real_const(src[i])));
+}
+
+// out[row] = sum over states and i of diag[i] Re x_row[s][i][i], states then
+// rows in index order (FP64); x_row = x + row * row_stride entries
+template <class Num>
+__global__ void __launch_bounds__(128) penalty_rows_kernel(const void *x_v, long long row_stride, int rows,
+                                                           int n_states, int d, const double *diag,
+                                                           double *out) {
+    using S = typename Num::store_t;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= rows) return;
+    const S *x = static_cast<const S *>(x_v) + (size_t)row * row_stride;
+    const size_t d2 = (size_t)d * d;
+    double acc = 0.0;
+    for (int st = 0; st < n_states; ++st)
+        for (int i = 0; i < d; ++i)
+            acc = fma(diag[i], Num::to_double2(Num::load(x[st * d2 + (size_t)i * d + i])).x, acc);
+    out[row] = acc;
+}
+
+// F -= scale * sum_k pen[k], in index order (one thread: deterministic)
+static __global__ void penalty_finish_kernel(const double *pen, long long count, double scale, double *F) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = 0.0;
+    for (long long k = 0; k < count; ++k) t += pen[k];
+    F[0] -= scale * t;
 }
 
 template <class Num>
@@ -1065,6 +1117,24 @@ cudaError_t launch_to_double(const void *src, double2 *dst, size_t n, cudaStream
     return cudaGetLastError();
 }
 
+template <class Num>
+cudaError_t launch_add_diag(void *x, const double *src, int d, int ns, cudaStream_t s) {
+    add_diag_kernel<Num><<<(d * ns + 255) / 256, 256, 0, s>>>(x, src, d, ns);
+    return cudaGetLastError();
+}
+template <class Num>
+cudaError_t launch_penalty_rows(const void *x, long long stride, int rows, int ns, int d,
+                                const double *diag, double *out, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    penalty_rows_kernel<Num><<<(rows + 127) / 128, 128, 0, s>>>(x, stride, rows, ns, d, diag, out);
+    return cudaGetLastError();
+}
+static cudaError_t launch_penalty_finish(const double *pen, long long count, double scale, double *F,
+                                         cudaStream_t s) {
+    penalty_finish_kernel<<<1, 32, 0, s>>>(pen, count, scale, F);
+    return cudaGetLastError();
+}
+
 }  // namespace grape_k
 
 #define GRAPE_DEFINE_LAUNCHERS(SUFFIX, NUM)                                                     \
@@ -1100,4 +1170,17 @@ cudaError_t launch_to_double(const void *src, double2 *dst, size_t n, cudaStream
     cudaError_t grape_prepare_grid_##SUFFIX(int variant, size_t smem_total, size_t smem,        \
                                             int *max_blocks) {                                  \
         return grape_k::prepare_grid<NUM>(variant, smem_total, smem, max_blocks);               \
+    }                                                                                           \
+    cudaError_t grape_launch_add_diag_##SUFFIX(void *x, const double *src, int d, int n_states, \
+                                               cudaStream_t s) {                                \
+        return grape_k::launch_add_diag<NUM>(x, src, d, n_states, s);                           \
+    }                                                                                           \
+    cudaError_t grape_launch_penalty_rows_##SUFFIX(const void *x, long long row_stride, int rows, \
+                                                   int n_states, int d, const double *diag,     \
+                                                   double *out, cudaStream_t s) {               \
+        return grape_k::launch_penalty_rows<NUM>(x, row_stride, rows, n_states, d, diag, out, s); \
+    }                                                                                           \
+    cudaError_t grape_launch_penalty_finish_##SUFFIX(const double *pen, long long count,        \
+                                                     double scale, double *F, cudaStream_t s) {  \
+        return grape_k::launch_penalty_finish(pen, count, scale, F, s);                         \
     }

@@ -161,6 +161,17 @@ class GrapeProblem:
     def geometry(self):
         return _lib.grape_problem_geometry(self._h)
 
+    def set_penalty(self, diag, beta: float) -> None:
+        """Phi = Phi_0 - beta dt sum_n Re Tr(A rho_n) for A = diag(diag)
+        (App. B); diag=None removes it."""
+        if diag is not None and len(diag) != self.d:
+            raise ValueError(f"diag needs {self.d} values")
+        _lib.grape_problem_set_penalty(self._h, diag, beta)
+
+    def set_photon_penalty(self, Q: int, N: int, beta: float) -> None:
+        """The paper's photon-number penalty, A = a^dag a in the basis i = n Q + q."""
+        self.set_penalty(np.repeat(np.arange(N, dtype=np.float64), Q), beta)
+
     def set_tile(self, cluster: int, threads: int) -> None:
         """Cluster width and threads per CTA of the propagation kernel
         (results do not change, bit for bit)."""
