@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"],
                     help="kernel arithmetic: double-float on FP32 pipes or native FP64")
-    ap.add_argument("--workload", default="d120", choices=["d120", "d20", "d120f", "batch256", "d600", "serve"])
+    ap.add_argument("--workload", default="d120", choices=["d120", "d20", "d120f", "d120p", "batch256", "d600", "serve"])
     ap.add_argument("--scale", type=float, default=None,
                     help="slice-count multiplier of the batch256/serve/d600 workloads")
     ap.add_argument("--jobs", type=int, default=64, help="serve: jobs in the trace")
@@ -427,6 +427,33 @@ def run_d120f(args):
         "gpu_launches": (P.gradient_launches() + 2) * args.steps})), flush=True)
 
 
+def run_d120p(args):
+    """The d=120 problem with the paper's photon-number penalty,
+    Phi = Phi_0 - beta Phi_p with beta = 0.2 / T (Sec. 5, App. B)."""
+    import torch
+    import workloads
+    from paper_1609_03170_gb300 import GrapeProblem
+    w = workloads.transmon_resonator_d120()
+    P = GrapeProblem.from_workload(w)
+    P.set_photon_penalty(w.phys.Q, w.phys.N, 0.2 / w.T)
+    u = torch.from_numpy(w.u).cuda()
+    stream = torch.cuda.Stream()
+    for _ in range(max(3, args.warmup)):
+        P.gradient(u, stream=stream)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        P.gradient(u, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    print(json.dumps(_base_line(args, "transmon_resonator_d120_penalty", 1000.0 / ms, UNIT, ms, {
+        "config": {"workload": "transmon_resonator_d120_penalty", "d": 120, "n_slices": w.n_slices,
+                   "n_rk": 4, "n_states": 3, "beta": 0.2 / w.T},
+        "gpu_launches": P.gradient_launches() * args.steps})), flush=True)
+
+
 def serve_trace(n_jobs, scale, rate, seed=1609):
     """Seeded trace: (arrival time, workload); 88% batch-distribution problems,
     10% d=120 / N_t=2000 problems, 2% d=300 / N_t=10000 problems (slice
@@ -511,7 +538,7 @@ def main():
         import torch
         torch.cuda.set_device(0)
         {"batch256": run_batch256, "d600": run_d600, "serve": run_serve,
-         "d20": run_d20, "d120f": run_d120f}[args.workload](args)
+         "d20": run_d20, "d120f": run_d120f, "d120p": run_d120p}[args.workload](args)
         return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":
