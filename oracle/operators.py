@@ -47,6 +47,8 @@ def build(phys) -> DenseModel:
     if phys.qubit_energy:
         for q in range(Q):
             H0 += phys.qubit_energy[q] * proj[q]
+    if phys.g:                                  # Jaynes-Cummings exchange (Fig. 2 model)
+        H0 += phys.g * (a @ b.conj().T + a.conj().T @ b)
 
     kinds = {
         "res_x": a + a.conj().T,

@@ -62,7 +62,14 @@ def band_model(phys) -> BandModel:
     diag = chi * n + phys.delta * n + phys.kerr * n.astype(float) ** 2
     if phys.qubit_energy:
         diag = diag + np.asarray(phys.qubit_energy, dtype=float)[q]
-    H0 = BandOp.make(d, [(0, diag.astype(np.complex128))])
+    h0 = [(0, diag.astype(np.complex128))]
+    if getattr(phys, "g", 0.0):
+        # g (a b^dag + a^dag b): row (n, q) <- (n+1, q-1) at offset Q-1 and
+        # <- (n-1, q+1) at offset -(Q-1)
+        ab = np.where((n + 1 < N) & (q >= 1), np.sqrt(n + 1.0) * np.sqrt(q.astype(float)), 0.0)
+        ba = np.where((n >= 1) & (q + 1 < Q), np.sqrt(n.astype(float)) * np.sqrt(q + 1.0), 0.0)
+        h0 += [(Q - 1, phys.g * ab + 0j), (-(Q - 1), phys.g * ba + 0j)]
+    H0 = BandOp.make(d, h0)
 
     kinds = {
         "res_x": [(Q, up_res + 0j), (-Q, dn_res + 0j)],

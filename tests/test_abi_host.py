@@ -48,6 +48,10 @@ def dense_of(op: problem.BandOp, d):
     lambda: workloads.transmon_resonator_d120(n_slices=2),
     lambda: workloads.small(Q=3, N=5, gamma1=0.1, gamma_phi=0.2,
                             controls_=("res_x", "res_y", "qub_x", "qub_y")),
+    lambda: workloads.jaynes_cummings(16, n_slices=2),
+    lambda: workloads.make("jc_q3", workloads.Physics(Q=3, N=4, chi=(0.0, 0.5, 1.1), g=0.8,
+                                                      controls=("res_x", "qub_y")),
+                           T=0.5, n_slices=2, n_rk=1, states=[(1, 0.5)], u_bound=1.0),
 ])
 def test_band_model_equals_dense_operators(factory):
     w = factory()

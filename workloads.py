@@ -43,6 +43,7 @@ class Physics:
     gamma1: float = 0.0               # transmon relaxation rate
     gamma_phi: float = 0.0            # transmon pure-dephasing rate
     qubit_energy: Tuple[float, ...] = ()   # E_q per level, empty = all zero
+    g: float = 0.0                    # Jaynes-Cummings coupling g (a b^dag + a^dag b) (Fig. 2 model)
     controls: Tuple[str, ...] = ("res_x", "res_y")
 
     @property
@@ -186,6 +187,24 @@ def batch_problem(i: int, n_slices: Optional[int] = None) -> Workload:
     states = [(q, complex(mags[q] * np.exp(1j * phases[q]))) for q in range(Q)]
     return make(f"batch{i}", phys, T=BATCH_DT * nt, n_slices=nt, n_rk=4,
                 states=states, u_bound=2.0, control_seed=CONTROL_SEED + i)
+
+
+def jaynes_cummings(d: int, n_slices: int = 200, n_rk: int = 1) -> Workload:
+    """The scaling workload of Fig. 2: a qubit (Q=2) coupled to a cavity of
+    N = d/2 levels by a Jaynes-Cummings interaction g = 100 kappa, qubit
+    detuning Delta = 10 kappa (drive resonant with the cavity), cavity
+    quadrature controls, initial |alpha> (x) |e> with alpha = sqrt(d/8),
+    target |0> (x) |e>, T = pi / g over N_t = 200 slices, one state."""
+    if d % 2:
+        raise ValueError("d must be even (qubit x cavity)")
+    g = 100.0
+    phys = Physics(Q=2, N=d // 2, chi=(0.0, 0.0), kappa=1.0, qubit_energy=(0.0, 10.0), g=g)
+    w = make(f"jaynes_cummings_d{d}", phys, T=math.pi / g, n_slices=n_slices, n_rk=n_rk,
+             states=[(1, complex(math.sqrt(d / 8.0)))], u_bound=1.0)
+    sigma = np.zeros((d, d), dtype=np.complex128)
+    sigma[1, 1] = 1.0                 # |0> (x) |e>: index n Q + q = 1
+    w.sigma = sigma
+    return w
 
 
 def transmon_resonator_d600(n_slices: int = 40000) -> Workload:
