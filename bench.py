@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"],
                     help="kernel arithmetic: double-float on FP32 pipes or native FP64")
-    ap.add_argument("--workload", default="d120", choices=["d120", "d20", "d120f", "d120p", "batch256", "d600", "serve"])
+    ap.add_argument("--workload", default="d120", choices=["d120", "d20", "d120f", "d120p", "sweep", "batch256", "d600", "serve"])
     ap.add_argument("--scale", type=float, default=None,
                     help="slice-count multiplier of the batch256/serve/d600 workloads")
     ap.add_argument("--jobs", type=int, default=64, help="serve: jobs in the trace")
@@ -454,6 +454,99 @@ def run_d120p(args):
         "gpu_launches": P.gradient_launches() * args.steps})), flush=True)
 
 
+def _fit_exponent(ds, ts):
+    """Least-squares slope of log T against log d."""
+    x, y = np.log(np.asarray(ds, float)), np.log(np.asarray(ts, float))
+    return float(np.polyfit(x, y, 1)[0])
+
+
+def _expm_first_order_seconds(w):
+    """The paper's "standard" method on the host: the d^2 x d^2 Liouvillian
+    of every slice exponentiated (scipy expm), rho propagated as a vector,
+    lambda propagated back with the transposed propagators, and the
+    first-order gradient of Eq. (dphidu).  Oracle code, timed only."""
+    import scipy.linalg
+    from oracle import liouville, operators
+    t0 = time.perf_counter()
+    m = operators.build(w.phys)
+    dt = w.T / w.n_slices
+    props = [scipy.linalg.expm(dt * liouville.superop(operators.hamiltonian(m, w.u[j]), m.jumps))
+             for j in range(w.n_slices)]
+    ders = [liouville.control_superop(Hk) for Hk in m.Hc]
+    r = [liouville.vec(w.rho0[0])]
+    for Mj in props:
+        r.append(Mj @ r[-1])
+    lam = liouville.vec(w.sigma.T)
+    G = np.zeros(w.u.shape)
+    for j in reversed(range(w.n_slices)):
+        for k, Dk in enumerate(ders):
+            G[j, k] = float(np.real(lam @ (Dk @ r[j + 1]))) * dt
+        lam = lam @ props[j]
+    return time.perf_counter() - t0
+
+
+def run_sweep(args):
+    """Fig. 2 of the paper on GB300: time per evaluation of Phi and its
+    first-order gradient against d for the Jaynes-Cummings reset problem
+    (200 slices, one state), with the plain-C RK oracle and the expm
+    "standard" method on the host, and the power-law exponents."""
+    import torch
+    import workloads
+    from oracle import sparse
+    from paper_1609_03170_gb300 import GrapeProblem, _lib
+    gpu_d = [6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
+    cpu_d = [6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256]
+    expm_d = [6, 8, 10, 12, 16, 20]
+    stream = torch.cuda.Stream()
+    gpu = {}
+    for d in gpu_d:
+        w = workloads.jaynes_cummings(d)
+        P = GrapeProblem.from_workload(w, grad_mode=_lib.GRAPE_GRAD_FIRST_ORDER)
+        u = torch.from_numpy(w.u).cuda()
+        F = torch.empty(1, dtype=torch.float64, device="cuda")
+        G = torch.empty_like(u)
+        for _ in range(3):
+            _lib.grape_gradient(P.handle, u.data_ptr(), F.data_ptr(), G.data_ptr(), stream.cuda_stream)
+        reps = 10
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            _lib.grape_gradient(P.handle, u.data_ptr(), F.data_ptr(), G.data_ptr(), stream.cuda_stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        gpu[d] = {"ms": ev0.elapsed_time(ev1) / reps, "kernel": P.kernel(), "cluster": P.geometry()[0]}
+        P.close()
+    sparse.build()
+    cpu = {}
+    for d in cpu_d:
+        w = workloads.jaynes_cummings(d)
+        sparse.run_workload(w, mode=sparse.MODE_FIRST_ORDER, threads=1)
+        cpu[d] = 1000.0 * sparse.run_workload(w, mode=sparse.MODE_FIRST_ORDER, threads=1)[3]
+    expm = {d: 1000.0 * _expm_first_order_seconds(workloads.jaynes_cummings(d)) for d in expm_d}
+    big = [d for d in gpu_d if d >= 128]
+    line = _base_line(args, "jaynes_cummings_sweep", _fit_exponent(big, [gpu[d]["ms"] for d in big]),
+                      "exponent", gpu[gpu_d[-1]]["ms"], {
+        "metric": "T_grad scaling exponent xi (T_grad ~ d^xi), Fig. 2 workload",
+        "higher_is_better": False,
+        "config": {"workload": "jaynes_cummings_sweep", "n_slices": 200, "n_rk": 1, "n_states": 1,
+                   "grad_mode": "first_order", "g_kappa": 100.0, "delta_kappa": 10.0,
+                   "T": "pi/g", "alpha": "sqrt(d/8)"},
+        "gpu_ms": {str(d): round(v["ms"], 4) for d, v in gpu.items()},
+        "gpu_kernel": {str(d): f'{v["kernel"]}/{v["cluster"]}' for d, v in gpu.items()},
+        "cpu_rk_oracle_ms": {str(d): round(v, 3) for d, v in cpu.items()},
+        "cpu_expm_ms": {str(d): round(v, 2) for d, v in expm.items()},
+        "exponents": {
+            "gpu_d>=128": _fit_exponent(big, [gpu[d]["ms"] for d in big]),
+            "gpu_all": _fit_exponent(gpu_d, [gpu[d]["ms"] for d in gpu_d]),
+            "cpu_rk_oracle": _fit_exponent(cpu_d, [cpu[d] for d in cpu_d]),
+            "cpu_expm": _fit_exponent(expm_d, [expm[d] for d in expm_d]),
+            "paper": {"rk": 1.9, "expm": 5.8}},
+        "cpu_baseline": {"value": cpu[cpu_d[-1]], "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"first-order gradient at d={cpu_d[-1]}, 200 slices"},
+        "gpu_launches": None})
+    print(json.dumps(line), flush=True)
+
+
 def serve_trace(n_jobs, scale, rate, seed=1609):
     """Seeded trace: (arrival time, workload); 88% batch-distribution problems,
     10% d=120 / N_t=2000 problems, 2% d=300 / N_t=10000 problems (slice
@@ -538,7 +631,8 @@ def main():
         import torch
         torch.cuda.set_device(0)
         {"batch256": run_batch256, "d600": run_d600, "serve": run_serve,
-         "d20": run_d20, "d120f": run_d120f, "d120p": run_d120p}[args.workload](args)
+         "d20": run_d20, "d120f": run_d120f, "d120p": run_d120p,
+         "sweep": run_sweep}[args.workload](args)
         return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":

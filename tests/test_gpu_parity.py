@@ -359,3 +359,18 @@ def test_d120_full_size_against_c_oracle(gp):
                 assert abs(np.trace(rr) - 1) < 1e-12
                 assert np.max(np.abs(rr - rr.conj().T)) < 1e-13
             P.close()
+
+
+@pytest.mark.parametrize("d", [24, 40])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_jaynes_cummings_fig2_workload(gp, d, mode):
+    """The Fig. 2 scaling workload (qubit x cavity, Jaynes-Cummings coupling on
+    the +-(Q-1) bands, 200 slices) against the C oracle, exact and first order."""
+    w = workloads.jaynes_cummings(d)
+    cmode = sparse.MODE_EXACT if mode == 0 else sparse.MODE_FIRST_ORDER
+    F_ref, G_ref, r_ref, _ = sparse.run_workload(w, mode=cmode, threads=1)
+    P = gp.GrapeProblem.from_workload(w, grad_mode=mode)
+    F, r = P.forward(w.u)
+    assert rel(r, r_ref) < TOL
+    F2, G = P.gradient(w.u)
+    assert abs(F2 - F_ref) < TOL * max(abs(F_ref), 1e-300) and rel(G, G_ref) < TOL
