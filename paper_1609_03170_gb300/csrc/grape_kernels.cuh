@@ -541,6 +541,10 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                 const int li = u - u0;
                 const int2 ij = rc[li];
                 const short *na = nbad + (size_t)li * nstride;
+                // the stage input itself, stored first so that the global store
+                // completes while the entry is computed (the barrier's release
+                // at the end of the stage waits for it)
+                if (st) store_herm<Num>(st, d, ij.x, ij.y, cur[na[ns]]);
                 // own-entry coefficient: cached per slice (the entry is thread-private,
                 // so no barrier is needed) or recomputed when there is no room
                 V dij;
@@ -551,7 +555,6 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                     dij = diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR);
                 }
                 const V w = lindblad_h_at<Num, REALJ>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij);
-                if (st) store_herm<Num>(st, d, ij.x, ij.y, cur[na[ns]]);   // the stage input itself
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
                 V z;
