@@ -72,7 +72,7 @@ def propagate(model, u, rho0, T, n_rk, keep_slices=False):
     traj = [rho]
     for j in range(n_slices):
         H = operators.hamiltonian(model, u[j])
-        f = lambda r, H=H: lindblad(H, model.jumps, r)
+        f = lambda r, H=H, J=operators.jumps_at(model, u[j]): lindblad(H, J, r)
         for _ in range(n_rk):
             rho, _ = rk4_step(f, rho, h)
         if keep_slices:
@@ -113,8 +113,9 @@ def gradient_exact(model, u, rho0s, sigma, T, n_rk, source=None):
         kb2 = h/3 mu + h/2 yb3,    yb2 = L^dag kb2
         kb1 = h/6 mu + h/2 yb2,    yb1 = L^dag kb1
         mu_before = mu + yb1 + yb2 + yb3 + yb4
-    and each stage contributes Re Tr(kb_s (-i)[H_k, y_s]) to dPhi/du_k(j),
-    since dL/du_k rho = -i[H_k, rho] (Eq. master with Eq. Hamiltonian).
+    and each stage contributes Re Tr(kb_s (dL/du_k) y_s) to dPhi/du_k(j),
+    with dL/du_k rho = -i[H_k, rho] (Eq. master with Eq. Hamiltonian), plus
+    r D[c] rho for a control on a dissipation rate.
     """
     n_slices, dt, h = _geometry(T, u, n_rk)
     R = len(model.Hc)
@@ -126,7 +127,7 @@ def gradient_exact(model, u, rho0s, sigma, T, n_rk, source=None):
         stages = []                      # stages[j][r] = (y1, y2, y3, y4)
         for j in range(n_slices):
             H = operators.hamiltonian(model, u[j])
-            f = lambda r, H=H: lindblad(H, model.jumps, r)
+            f = lambda r, H=H, J=operators.jumps_at(model, u[j]): lindblad(H, J, r)
             per = []
             for _ in range(n_rk):
                 rho, ys = rk4_step(f, rho, h)
@@ -138,7 +139,7 @@ def gradient_exact(model, u, rho0s, sigma, T, n_rk, source=None):
             mu = mu + source
         for j in reversed(range(n_slices)):
             H = operators.hamiltonian(model, u[j])
-            fd = lambda X, H=H: lindblad_dual(H, model.jumps, X)
+            fd = lambda X, H=H, J=operators.jumps_at(model, u[j]): lindblad_dual(H, J, X)
             for r in reversed(range(n_rk)):
                 y1, y2, y3, y4 = stages[j][r]
                 kb4 = (h / 6) * mu
@@ -149,10 +150,10 @@ def gradient_exact(model, u, rho0s, sigma, T, n_rk, source=None):
                 yb2 = fd(kb2)
                 kb1 = (h / 6) * mu + (h / 2) * yb2
                 yb1 = fd(kb1)
-                for k, Hk in enumerate(model.Hc):
+                for k in range(R):
                     acc = 0.0
                     for kb, y in ((kb1, y1), (kb2, y2), (kb3, y3), (kb4, y4)):
-                        acc += np.real(np.trace(kb @ (-1j * (Hk @ y - y @ Hk))))
+                        acc += np.real(np.trace(kb @ operators.control_derivative(model, k, y)))
                     G[j, k] += acc
                 mu = mu + yb1 + yb2 + yb3 + yb4
             if source is not None:
@@ -173,7 +174,7 @@ def backward_targets(model, u, sigma, T, n_rk, source=None):
     out[n_slices] = lam
     for j in reversed(range(n_slices)):
         H = operators.hamiltonian(model, u[j])
-        fd = lambda X, H=H: lindblad_dual(H, model.jumps, X)
+        fd = lambda X, H=H, J=operators.jumps_at(model, u[j]): lindblad_dual(H, J, X)
         for _ in range(n_rk):
             lam, _ = rk4_step(fd, lam, h)
         if source is not None:
@@ -197,8 +198,8 @@ def gradient_first_order(model, u, rho0s, sigma, T, n_rk, source=None):
         lams = backward_targets(model, u, sig, T, n_rk, source)
         for j in range(1, n_slices + 1):
             rho_j, lam_j = traj[j], lams[j]
-            for k, Hk in enumerate(model.Hc):
-                G[j - 1, k] += np.real(-1j * dt * np.trace(lam_j @ (Hk @ rho_j - rho_j @ Hk)))
+            for k in range(R):
+                G[j - 1, k] += np.real(dt * np.trace(lam_j @ operators.control_derivative(model, k, rho_j)))
     return F, G
 
 

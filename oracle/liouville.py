@@ -55,7 +55,7 @@ def rk_poly(X):
 
 
 def slice_map(model, u_j, dt, n_rk, kind):
-    L = superop(operators.hamiltonian(model, u_j), model.jumps)
+    L = superop(operators.hamiltonian(model, u_j), operators.jumps_at(model, u_j))
     if kind == "rk":
         return np.linalg.matrix_power(rk_poly((dt / n_rk) * L), n_rk)
     if kind == "expm":
@@ -65,8 +65,11 @@ def slice_map(model, u_j, dt, n_rk, kind):
 
 def slice_map_derivative(model, u_j, k, dt, n_rk, kind):
     """d(slice map)/du_k through the block-matrix Frechet identity."""
-    L = superop(operators.hamiltonian(model, u_j), model.jumps)
+    L = superop(operators.hamiltonian(model, u_j), operators.jumps_at(model, u_j))
     E = control_superop(model.Hc[k])
+    for kk, r, c in model.rate_ctl:           # a control on a dissipation rate: r D[c]
+        if kk == k:
+            E = E + superop(np.zeros_like(model.Hc[k]), [(r, c)])
     n = L.shape[0]
     if kind == "rk":
         h = dt / n_rk

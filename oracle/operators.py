@@ -30,6 +30,10 @@ class DenseModel:
     H0: np.ndarray                        # drift Hamiltonian
     Hc: List[np.ndarray]                  # control Hamiltonians H_k (Eq. Hamiltonian)
     jumps: List[Tuple[float, np.ndarray]]  # (gamma_j, a_j) of Eq. (disspation)
+    # controls on dissipation rates (the variant mentioned after Eq. partialuk):
+    # (control k, weight r, c) adds u_k(j) r D[c] to the slice's Lindbladian;
+    # such a control has a zero Hamiltonian H_k
+    rate_ctl: List[Tuple[int, float, np.ndarray]] = dataclasses.field(default_factory=list)
 
 
 def build(phys) -> DenseModel:
@@ -56,14 +60,40 @@ def build(phys) -> DenseModel:
         "qub_x": b + b.conj().T,
         "qub_y": 1j * (b.conj().T - b),
     }
-    Hc = [kinds[k].astype(np.complex128) for k in phys.controls]
+    rate_ops = {"rate_a": a, "rate_b": b}          # u_k D[a], u_k D[b]
+    Hc, rate_ctl = [], []
+    for k, name in enumerate(phys.controls):
+        if name in rate_ops:
+            Hc.append(np.zeros((N * Q, N * Q), dtype=np.complex128))
+            rate_ctl.append((k, 1.0, rate_ops[name].astype(np.complex128)))
+        else:
+            Hc.append(kinds[name].astype(np.complex128))
 
     jumps = [(phys.kappa, a)]
     if phys.gamma1:
         jumps.append((phys.gamma1, b))
     if phys.gamma_phi:
         jumps.append((phys.gamma_phi, b.conj().T @ b))
-    return DenseModel(d=N * Q, H0=H0, Hc=Hc, jumps=jumps)
+    return DenseModel(d=N * Q, H0=H0, Hc=Hc, jumps=jumps, rate_ctl=rate_ctl)
+
+
+def jumps_at(model: DenseModel, u_j):
+    """The slice's dissipators: the fixed (gamma, c) and, for every rate
+    control, (u_k(j) r, c)."""
+    return list(model.jumps) + [(u_j[k] * r, c) for k, r, c in model.rate_ctl]
+
+
+def control_derivative(model: DenseModel, k: int, y: np.ndarray) -> np.ndarray:
+    """dL/du_k applied to y: -i[H_k, y] (Eq. partialuk before the Delta t
+    expansion), plus r D[c](y) when u_k is a rate control."""
+    Hk = model.Hc[k]
+    out = -1j * (Hk @ y - y @ Hk)
+    for kk, r, c in model.rate_ctl:
+        if kk == k:
+            cd = c.conj().T
+            cdc = cd @ c
+            out = out + r * (c @ y @ cd - 0.5 * (cdc @ y + y @ cdc))
+    return out
 
 
 def hamiltonian(model: DenseModel, u_j) -> np.ndarray:

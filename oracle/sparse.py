@@ -80,6 +80,8 @@ def run(phys, u, rho0s, sigma, T, n_rk, mode=MODE_EXACT, threads=0):
     """Returns (F, grad or None, rhoT, seconds)."""
     lib = _load()
     model = operators.build(phys)
+    if model.rate_ctl:
+        raise NotImplementedError("the C oracle has no controls on dissipation rates")
     ops = [model.H0] + list(model.Hc) + [c for _, c in model.jumps]
     rates = np.array([g for g, _ in model.jumps], dtype=np.float64)
     ptr, rows, cols, vals = _coo(ops)

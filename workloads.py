@@ -28,7 +28,7 @@ import numpy as np
 CONTROL_SEED = 1609
 PHASE_SEED = 3170
 
-CONTROL_KINDS = ("res_x", "res_y", "qub_x", "qub_y")
+CONTROL_KINDS = ("res_x", "res_y", "qub_x", "qub_y", "rate_a", "rate_b")   # rate_*: u D[a], u D[b]
 
 
 @dataclasses.dataclass(frozen=True)
