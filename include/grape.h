@@ -86,6 +86,11 @@ typedef struct {
                                    0 = automatic (no recomputation when the stage
                                    storage fits in 60% of the free device memory) */
     int32_t precision;          /* grape_precision of the kernels */
+    const int32_t *jump_control;/* NULL or [n_jumps]: -1 = fixed rate; k >= 0 = the
+                                   dissipator's rate is rates[m] * u_k(j) in slice j
+                                   (a control on a dissipation rate, the variant
+                                   mentioned after Eq. partialuk; Hc[k] must then be
+                                   empty and dL/du_k = rates[m] D[c_m]) */
 } grape_problem_desc;
 
 typedef struct grape_problem *grape_problem_t;

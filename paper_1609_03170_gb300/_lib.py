@@ -34,7 +34,7 @@ class grape_problem_desc(ctypes.Structure):
                 ("H0", grape_band_op), ("Hc", P(grape_band_op)), ("jumps", P(grape_band_op)),
                 ("rates", P(c_double)), ("rho0", P(c_double)), ("sigma", P(c_double)),
                 ("sigma_broadcast", c_int32), ("grad_mode", c_int32), ("ckpt_stride", c_int32),
-                ("precision", c_int32)]
+                ("precision", c_int32), ("jump_control", P(c_int32))]
 
 
 class grape_opt_params(ctypes.Structure):

@@ -139,10 +139,11 @@ struct HostDir {
     std::vector<cplx> A0, Ak;    // [nb][d], [R][nb][d]
     std::vector<int> oL, oR;     // nt
     std::vector<cplx> vL, vR;    // [nt][d]
+    std::vector<int> jctl;       // nt: control scaling the term, -1 fixed
 };
 
 HostDir make_dir(const Bands &A0, const std::vector<Bands> &Ak,
-                 const std::vector<Bands> &jumps, int d) {
+                 const std::vector<Bands> &jumps, const std::vector<int> &jump_ctl, int d) {
     HostDir h;
     std::map<int, int> idx;
     for (const auto &kv : A0) idx[kv.first] = 0;
@@ -161,13 +162,14 @@ HostDir make_dir(const Bands &A0, const std::vector<Bands> &Ak,
         for (const auto &kv : Ak[k])
             for (int i = 0; i < d; ++i)
                 h.Ak[((size_t)k * nb + idx[kv.first]) * d + i] = kv.second[i];
-    for (const auto &c : jumps)
-        for (const auto &a : c)
-            for (const auto &b : c) {
+    for (size_t m = 0; m < jumps.size(); ++m)
+        for (const auto &a : jumps[m])
+            for (const auto &b : jumps[m]) {
                 h.oL.push_back(a.first);
                 h.oR.push_back(b.first);
                 h.vL.insert(h.vL.end(), a.second.begin(), a.second.end());
                 h.vR.insert(h.vR.end(), b.second.begin(), b.second.end());
+                h.jctl.push_back(jump_ctl[m]);
             }
     return h;
 }
@@ -366,6 +368,8 @@ grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
         t->joL[q] = h.oL[q];
         t->joR[q] = h.oR[q];
         if (h.oL[q] == 0 && h.oR[q] == 0) t->jdiag |= 1 << q;
+        t->jctl[q] = h.jctl[q];
+        if (h.jctl[q] >= 0) t->jrate |= 1 << q;
     }
     auto cvt = [](const std::vector<cplx> &v) {
         std::vector<double2> o(v.size());
@@ -1064,25 +1068,50 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
         prune(C[m]);
     }
 
-    // Forward: A = H_eff = H0 - i/2 sum gamma c^+ c (+ sum u_k H_k), terms from sqrt(gamma) c.
+    // controls on dissipation rates
+    std::vector<int> jc(desc->n_jumps, -1);
+    if (desc->jump_control)
+        for (int m = 0; m < desc->n_jumps; ++m) {
+            const int k = desc->jump_control[m];
+            if (k < -1 || k >= desc->n_controls) return fail(GRAPE_EINVAL, "jump_control out of range");
+            if (k >= 0 && !Hc[k].empty())
+                return fail(GRAPE_EINVAL, "a control on a dissipation rate must have an empty Hamiltonian");
+            jc[m] = k;
+        }
+    // Forward: A = H_eff = H0 - i/2 sum gamma c^+ c (+ sum u_k A_k), terms from sqrt(gamma) c.
+    // A rate control k contributes A_k = -i/2 gamma c^+ c and scales its terms by u_k.
     Bands A0 = H0;
+    std::vector<Bands> Ak = Hc;                 // propagation's control parts
+    std::vector<Bands> Tk = Hc;                 // trace's control bands (see below)
     std::vector<Bands> Jf, Ja;
+    std::vector<int> jcf;
     for (int m = 0; m < desc->n_jumps; ++m) {
         const double g = desc->rates[m];
         if (g == 0.0 || C[m].empty()) continue;
-        add_into(A0, product(adjoint(C[m], d), C[m], d), cplx(0.0, -0.5 * g), d);
+        const Bands cdc = product(adjoint(C[m], d), C[m], d);
+        if (jc[m] < 0) {
+            add_into(A0, cdc, cplx(0.0, -0.5 * g), d);
+        } else {
+            add_into(Ak[jc[m]], cdc, cplx(0.0, -0.5 * g), d);
+            // -1/2 gamma {c^+c, y} enters Re Tr(kb dL/du y) as the commutator
+            // term of the trace kernel does with the band values +i/2 gamma c^+c
+            add_into(Tk[jc[m]], cdc, cplx(0.0, 0.5 * g), d);
+        }
         Jf.push_back(scaled(C[m], std::sqrt(g), d));
         Ja.push_back(scaled(adjoint(C[m], d), std::sqrt(g), d));
+        jcf.push_back(jc[m]);
     }
     prune(A0);
-    // Dual: A' = -H_eff^+, A'_k = -H_k^+, terms from sqrt(gamma) c^+.
+    for (auto &b : Ak) prune(b);
+    for (auto &b : Tk) prune(b);
+    // Dual: A' = -H_eff^+, A'_k = -A_k^+, terms from sqrt(gamma) c^+.
     Bands A0d = scaled(adjoint(A0, d), -1.0, d);
-    std::vector<Bands> Hcd(Hc.size());
-    for (size_t k = 0; k < Hc.size(); ++k) Hcd[k] = scaled(adjoint(Hc[k], d), -1.0, d);
+    std::vector<Bands> Hcd(Ak.size());
+    for (size_t k = 0; k < Ak.size(); ++k) Hcd[k] = scaled(adjoint(Ak[k], d), -1.0, d);
     for (auto &c : Jf) prune(c);
     for (auto &c : Ja) prune(c);
-    const HostDir hf = make_dir(A0, Hc, Jf, d);
-    const HostDir ha = make_dir(A0d, Hcd, Ja, d);
+    const HostDir hf = make_dir(A0, Ak, Jf, jcf, d);
+    const HostDir ha = make_dir(A0d, Hcd, Ja, jcf, d);
 
     // initial states (Hermitian) and the Hermitian part of sigma
     const size_t d2 = (size_t)d * d;
@@ -1116,11 +1145,11 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
     // control bands for the trace kernel
     TraceArgs tr;
     std::memset(&tr, 0, sizeof(tr));
-    std::vector<double2> cbv;
+    std::vector<double2> cbv, stv_l, stv_r;
     {
         std::map<int, int> doidx;
         for (int k = 0; k < desc->n_controls; ++k)
-            for (const auto &kv : Hc[k]) {
+            for (const auto &kv : Tk[k]) {
                 if (tr.ncb >= GRAPE_MAXCB) return fail(GRAPE_EINVAL, "too many control bands (max 8)");
                 auto it = doidx.find(kv.first);
                 if (it == doidx.end()) {
@@ -1138,6 +1167,21 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
         tr.ndo = (int)doidx.size();
         tr.d = d;
         tr.R = desc->n_controls;
+        // sandwich terms gamma c y c^+ of the rate-controlled dissipators: the
+        // forward jump terms (sqrt(gamma) c on both sides) of those dissipators
+        for (size_t q = 0; q < hf.oL.size(); ++q) {
+            if (hf.jctl[q] < 0) continue;
+            if (tr.nst >= GRAPE_MAXST)
+                return fail(GRAPE_EINVAL, "too many band pairs in rate-controlled dissipators (max 4)");
+            tr.st_k[tr.nst] = hf.jctl[q];
+            tr.st_oL[tr.nst] = hf.oL[q];
+            tr.st_oR[tr.nst] = hf.oR[q];
+            for (int i = 0; i < d; ++i) {
+                stv_l.push_back(make_double2(hf.vL[q * d + i].real(), hf.vL[q * d + i].imag()));
+                stv_r.push_back(make_double2(hf.vR[q * d + i].real(), hf.vR[q * d + i].imag()));
+            }
+            tr.nst++;
+        }
     }
 
     grape_problem *P = new grape_problem();
@@ -1211,6 +1255,13 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
     double2 *cb = nullptr;
     if ((st = upload(P, cbv, &cb)) != GRAPE_OK) return bail(st);
     tr.cb_val = cb;
+    if (tr.nst > 0) {
+        double2 *a = nullptr, *b = nullptr;
+        if ((st = upload(P, stv_l, &a)) != GRAPE_OK) return bail(st);
+        if ((st = upload(P, stv_r, &b)) != GRAPE_OK) return bail(st);
+        tr.st_vL = a;
+        tr.st_vR = b;
+    }
     P->trace = tr;
     P->trace.nsplit = trace_splits(P);
     P->d_x = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));

@@ -10,6 +10,7 @@
 #define GRAPE_MAXR 8     // control Hamiltonians
 #define GRAPE_MAXCB 8    // (control, band) pairs seen by the trace kernel
 #define GRAPE_MAXDO 8    // distinct band offsets among the control bands
+#define GRAPE_MAXST 4    // sandwich terms of dissipators whose rate is a control
 #define GRAPE_PROP_THREADS 512   // threads per CTA of the propagation kernel
 
 // One direction of the Lindblad action in the common form
@@ -27,6 +28,8 @@ struct PropTables {
     int joR[GRAPE_MAXT];        // oR_t
     int b0;                     // index of the offset-0 band, -1 if none
     int jdiag;                  // bit t set: jump term t has oL_t = oR_t = 0
+    int jrate;                  // bit t set: jump term t is scaled by a control (its rate is a control)
+    int jctl[GRAPE_MAXT];       // that control, -1: fixed
     const double2 *A0;          // [nb][d]
     const double2 *Ak;          // [R][nb][d]
     const double2 *vL;          // [nt][d]
@@ -106,6 +109,12 @@ struct TraceArgs {
     // part[row][split][R]; trace_finish_kernel adds the splits in order
     int nsplit;
     double *part;
+    // controls on dissipation rates: the sandwich part of Re Tr(kb D[c] y),
+    // sum over m, l of conj(K[m][l]) vL[m] conj(vR[l]) Y[m+oL][l+oR] per term
+    int nst;
+    int st_k[GRAPE_MAXST];
+    int st_oL[GRAPE_MAXST], st_oR[GRAPE_MAXST];
+    const double2 *st_vL, *st_vR;   // [nst][d]
 };
 
 // Launchers, one set per number type: _f64 native FP64, _df double-float.

@@ -27,6 +27,8 @@
 #include "grape_internal.h"
 #include "grape_num.cuh"
 
+#include <type_traits>
+
 namespace grape_k {
 
 using namespace grape_num;
@@ -104,6 +106,32 @@ __device__ __forceinline__ void push_value(S *buf, const PropArgs &p, int rank, 
 
 // W = Op(z) at element (i, j) of the window `cur` (local flat index le):
 //   W = -i (A z - z A^+)[i][j] + sum_t vL_t[i] conj(vR_t[j]) z[i+oL_t][j+oR_t]
+// Coefficient of jump term q at entry (i, j): vL_q[i] conj(vR_q[j]), times the
+// slice's control value when the term belongs to a dissipator whose rate is a
+// control (uj = the slice's controls; fixed terms are untouched).
+// RATE = false is the plain coefficient (no control touches the rates): the
+// callers branch once per call on t.jrate, so problems without rate controls
+// run the loops they always ran (a per-term test let the compiler speculate
+// the FP64 conversion of the control value into every iteration).
+template <class Num, bool RATE>
+__device__ __forceinline__ typename Num::real_t jump_real(const PropTables &t, int q, int i, int j, int d,
+                                                          const typename Num::store_t *vL,
+                                                          const typename Num::store_t *vR,
+                                                          const double *uj) {
+    typename Num::real_t c = Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j])));
+    if (RATE && ((t.jrate >> q) & 1)) c = Num::real_mul(c, Num::real_const(uj[t.jctl[q]]));
+    return c;
+}
+template <class Num, bool RATE>
+__device__ __forceinline__ typename Num::val jump_cplx(const PropTables &t, int q, int i, int j, int d,
+                                                       const typename Num::store_t *vL,
+                                                       const typename Num::store_t *vR,
+                                                       const double *uj) {
+    typename Num::val c = Num::mul_conjb(Num::load(vL[q * d + i]), Num::load(vR[q * d + j]));
+    if (RATE && ((t.jrate >> q) & 1)) c = Num::scale(Num::real_const(uj[t.jctl[q]]), c);
+    return c;
+}
+
 // REALJ: the jump tables are real, so each jump coefficient is one real
 // product.  Loops run over the problem's band and term counts (kept rolled:
 // the pair arithmetic makes every iteration long, and unrolled copies
@@ -113,7 +141,8 @@ __device__ __forceinline__ typename Num::val lindblad_at(const typename Num::sto
                                                          int i, int j, int d, const PropTables &t,
                                                          const typename Num::store_t *A,
                                                          const typename Num::store_t *vL,
-                                                         const typename Num::store_t *vR) {
+                                                         const typename Num::store_t *vR,
+                                                         const double *uj) {
     typename Num::acc w = Num::acc_zero();
 #pragma unroll 1
     for (int b = 0; b < t.nb; ++b) {
@@ -121,18 +150,18 @@ __device__ __forceinline__ typename Num::val lindblad_at(const typename Num::sto
         Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[le + t.off[b]]));
     }
     w = Num::acc_minus_i(w);                     // -i (A z - z A^+)
+    auto jumps = [&](auto rate) {
+        constexpr bool RT = decltype(rate)::value;
 #pragma unroll 1
-    for (int q = 0; q < t.nt; ++q) {
-        if (REALJ) {
-            const typename Num::real_t c =
-                Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j])));
-            Num::mac_real(w, c, Num::load(cur[le + t.jflat[q]]));
-        } else {
-            const typename Num::val coef = Num::mul_conjb(Num::load(vL[q * d + i]),
-                                                          Num::load(vR[q * d + j]));
-            Num::mac(w, coef, Num::load(cur[le + t.jflat[q]]));
+        for (int q = 0; q < t.nt; ++q) {
+            if (REALJ)
+                Num::mac_real(w, jump_real<Num, RT>(t, q, i, j, d, vL, vR, uj), Num::load(cur[le + t.jflat[q]]));
+            else
+                Num::mac(w, jump_cplx<Num, RT>(t, q, i, j, d, vL, vR, uj), Num::load(cur[le + t.jflat[q]]));
         }
-    }
+    };
+    if (t.jrate) jumps(std::true_type{});
+    else jumps(std::false_type{});
     return Num::done(w);
 }
 
@@ -223,7 +252,8 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_kernel(const PropA
             for (int e = e0 + threadIdx.x; e < e1; e += nth) {
                 const int le = e - wbase, li = e - e0;
                 const int2 ij = rc[li];
-                const V w = lindblad_at<Num, REALJ>(cur, le, ij.x, ij.y, d, p.tab, A, vL, vR);
+                const V w = lindblad_at<Num, REALJ>(cur, le, ij.x, ij.y, d, p.tab, A, vL, vR,
+                                                    p.u + (size_t)jcur * p.R);
                 if (st) st[e] = cur[le];
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
@@ -315,16 +345,20 @@ template <class Num, bool REALJ>
 __device__ __forceinline__ typename Num::val diag_coef(int i, int j, int d, const PropTables &t,
                                                        const typename Num::store_t *A,
                                                        const typename Num::store_t *vL,
-                                                       const typename Num::store_t *vR) {
+                                                       const typename Num::store_t *vR,
+                                                       const double *uj) {
     typename Num::val c = Num::zero();
     if (t.b0 >= 0) c = Num::minus_i(Num::sub_conj(Num::load(A[t.b0 * d + i]), Num::load(A[t.b0 * d + j])));
-    for (int q = 0; q < t.nt; ++q) {
-        if (!((t.jdiag >> q) & 1)) continue;
-        if (REALJ)
-            c = Num::add_real(c, Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j]))));
-        else
-            c = Num::add(c, Num::mul_conjb(Num::load(vL[q * d + i]), Num::load(vR[q * d + j])));
-    }
+    auto jumps = [&](auto rate) {
+        constexpr bool RT = decltype(rate)::value;
+        for (int q = 0; q < t.nt; ++q) {
+            if (!((t.jdiag >> q) & 1)) continue;
+            if (REALJ) c = Num::add_real(c, jump_real<Num, RT>(t, q, i, j, d, vL, vR, uj));
+            else c = Num::add(c, jump_cplx<Num, RT>(t, q, i, j, d, vL, vR, uj));
+        }
+    };
+    if (t.jrate) jumps(std::true_type{});
+    else jumps(std::false_type{});
     return c;
 }
 
@@ -335,7 +369,8 @@ __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::s
                                                            const typename Num::store_t *A,
                                                            const typename Num::store_t *vL,
                                                            const typename Num::store_t *vR,
-                                                           const typename Num::val dij) {
+                                                           const typename Num::val dij,
+                                                           const double *uj) {
     // neighbours outside the matrix point at the window's zero slot, so
     // every term is accumulated without a branch (adding 0 changes no bit).
     // The terms on the entry itself - the offset-0 band and the jump terms
@@ -349,19 +384,18 @@ __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::s
     }
     w = Num::acc_minus_i(w);
     Num::mac(w, dij, Num::load(cur[nb_ad[2 * t.nb + t.nt]]));
+    auto jumps = [&](auto rate) {
+        constexpr bool RT = decltype(rate)::value;
 #pragma unroll 1
-    for (int q = 0; q < t.nt; ++q) {
-        if ((t.jdiag >> q) & 1) continue;
-        const int aJ = nb_ad[2 * t.nb + q];
-        if (REALJ) {
-            const typename Num::real_t cf =
-                Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j])));
-            Num::mac_real(w, cf, Num::load(cur[aJ]));
-        } else {
-            Num::mac(w, Num::mul_conjb(Num::load(vL[q * d + i]), Num::load(vR[q * d + j])),
-                     Num::load(cur[aJ]));
+        for (int q = 0; q < t.nt; ++q) {
+            if ((t.jdiag >> q) & 1) continue;
+            const int aJ = nb_ad[2 * t.nb + q];
+            if (REALJ) Num::mac_real(w, jump_real<Num, RT>(t, q, i, j, d, vL, vR, uj), Num::load(cur[aJ]));
+            else Num::mac(w, jump_cplx<Num, RT>(t, q, i, j, d, vL, vR, uj), Num::load(cur[aJ]));
         }
-    }
+    };
+    if (t.jrate) jumps(std::true_type{});
+    else jumps(std::false_type{});
     return Num::raw(w);
 }
 
@@ -527,6 +561,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                 store_herm<Num>(dst, d, rc[u - u0].x, rc[u - u0].y, xs[u - u0]);
         }
         const S *A = bands + tb * nbd;
+        const double *uj = p.u + (size_t)jcur * p.R;   // controls of the current slice
         bool flip = false;
 #pragma unroll 1
         for (int s = 0; s < 4; ++s) {
@@ -549,12 +584,12 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                 // so no barrier is needed) or recomputed when there is no room
                 V dij;
                 if (p.fold) {
-                    if (s == 0 && dfresh) Dt[li] = Num::store(diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR));
+                    if (s == 0 && dfresh) Dt[li] = Num::store(diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR, uj));
                     dij = Num::load(Dt[li]);
                 } else {
-                    dij = diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR);
+                    dij = diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR, uj);
                 }
-                const V w = lindblad_h_at<Num, REALJ>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij);
+                const V w = lindblad_h_at<Num, REALJ>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij, uj);
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
                 V z;
@@ -648,7 +683,8 @@ __device__ __forceinline__ typename Num::val lindblad_g_at(const typename Num::s
                                                            int j, int d, const PropTables &t,
                                                            const typename Num::store_t *A,
                                                            const typename Num::store_t *vL,
-                                                           const typename Num::store_t *vR) {
+                                                           const typename Num::store_t *vR,
+                                                           const double *uj) {
     // same terms in the same order as lindblad_h_at (identical bits)
     typename Num::acc w = Num::acc_zero();
 #pragma unroll 1
@@ -660,21 +696,21 @@ __device__ __forceinline__ typename Num::val lindblad_g_at(const typename Num::s
             Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(__ldcg(&cur[(size_t)i * d + c])));
     }
     w = Num::acc_minus_i(w);
-    Num::mac(w, diag_coef<Num, REALJ>(i, j, d, t, A, vL, vR), Num::load(__ldcg(&cur[(size_t)i * d + j])));
+    Num::mac(w, diag_coef<Num, REALJ>(i, j, d, t, A, vL, vR, uj), Num::load(__ldcg(&cur[(size_t)i * d + j])));
+    auto jumps = [&](auto rate) {
+        constexpr bool RT = decltype(rate)::value;
 #pragma unroll 1
-    for (int q = 0; q < t.nt; ++q) {
-        if ((t.jdiag >> q) & 1) continue;
-        const int r = i + t.joL[q], c = j + t.joR[q];
-        if (r < 0 || r >= d || c < 0 || c >= d) continue;
-        const typename Num::val zv = Num::load(__ldcg(&cur[(size_t)r * d + c]));
-        if (REALJ) {
-            const typename Num::real_t cf =
-                Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j])));
-            Num::mac_real(w, cf, zv);
-        } else {
-            Num::mac(w, Num::mul_conjb(Num::load(vL[q * d + i]), Num::load(vR[q * d + j])), zv);
+        for (int q = 0; q < t.nt; ++q) {
+            if ((t.jdiag >> q) & 1) continue;
+            const int r = i + t.joL[q], c = j + t.joR[q];
+            if (r < 0 || r >= d || c < 0 || c >= d) continue;
+            const typename Num::val zv = Num::load(__ldcg(&cur[(size_t)r * d + c]));
+            if (REALJ) Num::mac_real(w, jump_real<Num, RT>(t, q, i, j, d, vL, vR, uj), zv);
+            else Num::mac(w, jump_cplx<Num, RT>(t, q, i, j, d, vL, vR, uj), zv);
         }
-    }
+    };
+    if (t.jrate) jumps(std::true_type{});
+    else jumps(std::false_type{});
     return Num::raw(w);
 }
 
@@ -771,7 +807,8 @@ __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const Pro
                 const int li = (int)(e - e0);
                 const int4 q = ent[li];
                 const S *cs = cur + (size_t)q.z * d2;
-                const V w = lindblad_g_at<Num, REALJ>(cs, q.x, q.y, d, p.tab, A, vL, vR);
+                const V w = lindblad_g_at<Num, REALJ>(cs, q.x, q.y, d, p.tab, A, vL, vR,
+                                                      p.u + (size_t)jcur * p.R);
                 if (stg) store_herm<Num>(stg + (size_t)q.z * d2, d, q.x, q.y, __ldcg(&cs[(size_t)q.x * d + q.y]));
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
@@ -825,12 +862,21 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int d = p.d;
     const size_t d2 = (size_t)d * d;
+    S *svL = hv + p.ncb * d;                         // [nst][d] sandwich tables
+    S *svR = svL + p.nst * d;
     for (int i = threadIdx.x; i < p.ncb * d; i += blockDim.x)
         hv[i] = Num::store(Num::from_double2(__ldg(&p.cb_val[i])));
+    for (int i = threadIdx.x; i < p.nst * d; i += blockDim.x) {
+        svL[i] = Num::store(Num::from_double2(__ldg(&p.st_vL[i])));
+        svR[i] = Num::store(Num::from_double2(__ldg(&p.st_vR[i])));
+    }
     __syncthreads();
     typename Num::acc Z[GRAPE_MAXCB];                // lane-private, in the number type
 #pragma unroll
     for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = Num::acc_zero();
+    typename Num::acc Zs[GRAPE_MAXST];               // sandwich terms (rate controls)
+#pragma unroll
+    for (int t = 0; t < GRAPE_MAXST; ++t) Zs[t] = Num::acc_zero();
     const S *Kb = static_cast<const S *>(p.K);
     const S *Yb = static_cast<const S *>(p.Y);
 
@@ -854,16 +900,41 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
                 for (int c = 0; c < GRAPE_MAXCB; ++c)
                     if (c < p.ncb && p.cb_do[c] == o) Num::mac(Z[c], Num::load(hv[c * d + m]), pv);
             }
+            // rate controls: sum over l of Y[m+oL][l+oR] conj(K[m][l] vR[l]), times vL[m]
+#pragma unroll 1
+            for (int t = 0; t < p.nst; ++t) {
+                const int r = m + p.st_oL[t];
+                if (r < 0 || r >= d) continue;
+                const int oR = p.st_oR[t];
+                typename Num::acc P = Num::acc_zero();
+#pragma unroll 1
+                for (int l = lane; l < d; l += 32) {
+                    const int c = l + oR;
+                    if (c < 0 || c >= d) continue;
+                    typename Num::acc kv = Num::acc_zero();
+                    Num::mac(kv, Num::load(K[(size_t)m * d + l]), Num::load(svR[t * d + l]));
+                    Num::mac_conjb(P, Num::load(Y[(size_t)r * d + c]), Num::done(kv));
+                }
+                Num::mac(Zs[t], Num::load(svL[t * d + m]), Num::done(P));
+            }
         }
     }
     // deterministic reduction: warp shuffles, then warps in index order (FP64)
     __shared__ double red[GRAPE_MAXCB][32];
+    __shared__ double reds[GRAPE_MAXST][32];
 #pragma unroll
     for (int c = 0; c < GRAPE_MAXCB; ++c) {
         double v = Num::to_double2(Num::done(Z[c])).y;
 #pragma unroll
         for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
         if (lane == 0) red[c][warp] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < GRAPE_MAXST; ++t) {
+        double v = Num::to_double2(Num::done(Zs[t])).x;   // real part: Re Tr(kb gamma c y c^+)
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
+        if (lane == 0) reds[t][warp] = v;
     }
     __syncthreads();
     if (threadIdx.x < GRAPE_MAXR) {
@@ -876,7 +947,14 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
                 for (int w = 0; w < nwarps; ++w) t += red[c][w];
                 s += t;
             }
-            const double v = p.weight * (-2.0 * s);
+            double sw = 0.0;
+            for (int t = 0; t < p.nst; ++t) {
+                if (p.st_k[t] != k) continue;
+                double a = 0.0;
+                for (int w = 0; w < nwarps; ++w) a += reds[t][w];
+                sw += a;
+            }
+            const double v = p.weight * (-2.0 * s + sw);
             if (nsplit == 1) p.G[(size_t)row * p.R + k] = v;
             else p.part[((size_t)row * nsplit + split) * p.R + k] = v;
         }
@@ -1088,7 +1166,7 @@ cudaError_t max_clusters(int threads, int variant, size_t smem, int ncl, int n_b
 template <class Num>
 cudaError_t launch_trace(const TraceArgs &p, cudaStream_t s) {
     if (p.n_rows <= 0) return cudaSuccess;
-    const size_t smem = (size_t)p.ncb * p.d * sizeof(typename Num::store_t);
+    const size_t smem = (size_t)(p.ncb + 2 * p.nst) * p.d * sizeof(typename Num::store_t);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(trace_kernel<Num>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

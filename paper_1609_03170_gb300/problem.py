@@ -45,6 +45,9 @@ class BandModel:
     Hc: List[BandOp]
     jumps: List[BandOp]
     rates: np.ndarray
+    # per jump: -1 fixed rate, k: the rate is rates[m] * u_k (a control on a
+    # dissipation rate, whose Hc[k] is empty)
+    jump_control: Optional[List[int]] = None
 
 
 def band_model(phys) -> BandModel:
@@ -77,14 +80,20 @@ def band_model(phys) -> BandModel:
         "qub_x": [(1, up_qub + 0j), (-1, dn_qub + 0j)],
         "qub_y": [(1, -1j * up_qub), (-1, 1j * dn_qub)],
     }
-    Hc = [BandOp.make(d, kinds[k]) for k in phys.controls]
+    rate_ops = {"rate_a": [(Q, up_res + 0j)], "rate_b": [(1, up_qub + 0j)]}   # u D[a], u D[b]
+    Hc = [BandOp.make(d, [] if k in rate_ops else kinds[k]) for k in phys.controls]
 
     jumps, rates = [BandOp.make(d, [(Q, up_res + 0j)])], [phys.kappa]
     if phys.gamma1:
         jumps.append(BandOp.make(d, [(1, up_qub + 0j)])); rates.append(phys.gamma1)
     if phys.gamma_phi:
         jumps.append(BandOp.make(d, [(0, q.astype(np.complex128))])); rates.append(phys.gamma_phi)
-    return BandModel(d=d, H0=H0, Hc=Hc, jumps=jumps, rates=np.array(rates, dtype=np.float64))
+    jc = [-1] * len(jumps)
+    for k, name in enumerate(phys.controls):
+        if name in rate_ops:
+            jumps.append(BandOp.make(d, rate_ops[name])); rates.append(1.0); jc.append(k)
+    return BandModel(d=d, H0=H0, Hc=Hc, jumps=jumps, rates=np.array(rates, dtype=np.float64),
+                     jump_control=jc if any(c >= 0 for c in jc) else None)
 
 
 def _dptr(a: np.ndarray):
@@ -131,10 +140,15 @@ class GrapeProblem:
         rates = np.ascontiguousarray(model.rates, dtype=np.float64)
         rho_f = rho0.view(np.float64)
         sig_f = sigma.view(np.float64)
+        jc = None
+        if model.jump_control is not None:
+            jc_arr = np.ascontiguousarray(model.jump_control, dtype=np.int32)
+            keep.append(jc_arr)
+            jc = jc_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         desc = _lib.grape_problem_desc(
             d, self.R, J, self.n_states, self.n_slices, self.n_rk, self.T,
             band(model.H0), Hc, jumps, _dptr(rates), _dptr(rho_f), _dptr(sig_f),
-            1 if sigma.ndim == 2 else 0, int(grad_mode), int(ckpt_stride), int(precision))
+            1 if sigma.ndim == 2 else 0, int(grad_mode), int(ckpt_stride), int(precision), jc)
         self.precision = int(precision)
         self._h = _lib.grape_problem_create(desc)
         del keep

@@ -138,3 +138,17 @@ def test_filter_validates_on_the_host():
     # valid sizes, but no device buffers
     assert lib.grape_filter_apply(1, 10, 2, 1.0, 0.1, w, None, None, None) == _lib.GRAPE_EINVAL
     assert lib.grape_gradient_filtered(None, 1, w, None, None, None, None) == _lib.GRAPE_EINVAL
+
+
+def test_band_model_of_rate_controls():
+    """A control on a dissipation rate: empty Hamiltonian band list, its
+    dissipator appended to the jumps with rate 1 and its control index."""
+    w = workloads.small(Q=2, N=4, controls_=("res_x", "rate_a", "rate_b"), gamma1=0.05)
+    bm = problem.band_model(w.phys)
+    dm = operators.build(w.phys)
+    assert len(bm.Hc[1].offsets) == 0 and len(bm.Hc[2].offsets) == 0
+    fixed = len(dm.jumps)
+    assert bm.jump_control == [-1] * fixed + [1, 2]
+    for (k, r, c), jb, rate in zip(dm.rate_ctl, bm.jumps[fixed:], bm.rates[fixed:]):
+        assert r == rate
+        assert np.max(np.abs(dense_of(jb, w.d) - c)) < 1e-15
