@@ -614,7 +614,10 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                     flip = true;
                 }
             }
-            cluster_sync_all();
+            // a one-CTA cluster needs only the CTA barrier (it orders the CTA's own
+            // shared-memory stores, whatever window address they used)
+            if (p.ncl == 1) __syncthreads();
+            else cluster_sync_all();
         }
         if (flip) tb ^= 1;
         dfresh = flip;
