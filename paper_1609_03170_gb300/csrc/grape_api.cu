@@ -1205,10 +1205,14 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
     P->prec = desc->precision;
     auto bail = [&](grape_status s) { delete P; return s; };
     {
+        // real jump tables select the kernels with one real coefficient per
+        // term; rate-controlled terms always take the complex-table kernels,
+        // which alone carry the per-slice scaling
         bool real_jumps = true;
         for (const HostDir *h : {&hf, &ha})
             for (const auto *v : {&h->vL, &h->vR})
                 for (const cplx &c : *v) real_jumps = real_jumps && c.imag() == 0.0;
+        for (int c : jcf) real_jumps = real_jumps && c < 0;
         P->variant = real_jumps ? 1 : 0;
     }
     if ((st = upload_dir(P, hf, &P->tab[0])) != GRAPE_OK) return bail(st);

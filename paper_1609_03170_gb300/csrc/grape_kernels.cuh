@@ -109,18 +109,17 @@ __device__ __forceinline__ void push_value(S *buf, const PropArgs &p, int rank, 
 // Coefficient of jump term q at entry (i, j): vL_q[i] conj(vR_q[j]), times the
 // slice's control value when the term belongs to a dissipator whose rate is a
 // control (uj = the slice's controls; fixed terms are untouched).
-// RATE = false is the plain coefficient (no control touches the rates): the
-// callers branch once per call on t.jrate, so problems without rate controls
-// run the loops they always ran (a per-term test let the compiler speculate
-// the FP64 conversion of the control value into every iteration).
+// Rate-controlled terms exist only in problems that run the complex-table
+// kernels (REALJ = false); there the callers branch once per call on
+// t.jrate (RATE), so no kernel pays for the scaling it does not use (a
+// per-term test let the compiler speculate the FP64 conversion of the
+// control value into every iteration).
 template <class Num, bool RATE>
 __device__ __forceinline__ typename Num::real_t jump_real(const PropTables &t, int q, int i, int j, int d,
                                                           const typename Num::store_t *vL,
                                                           const typename Num::store_t *vR,
                                                           const double *uj) {
-    typename Num::real_t c = Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j])));
-    if (RATE && ((t.jrate >> q) & 1)) c = Num::real_mul(c, Num::real_const(uj[t.jctl[q]]));
-    return c;
+    return Num::real_mul(Num::re(Num::load(vL[q * d + i])), Num::re(Num::load(vR[q * d + j])));
 }
 template <class Num, bool RATE>
 __device__ __forceinline__ typename Num::val jump_cplx(const PropTables &t, int q, int i, int j, int d,
@@ -160,7 +159,7 @@ __device__ __forceinline__ typename Num::val lindblad_at(const typename Num::sto
                 Num::mac(w, jump_cplx<Num, RT>(t, q, i, j, d, vL, vR, uj), Num::load(cur[le + t.jflat[q]]));
         }
     };
-    if (t.jrate) jumps(std::true_type{});
+    if (!REALJ && t.jrate) jumps(std::true_type{});
     else jumps(std::false_type{});
     return Num::done(w);
 }
@@ -357,7 +356,7 @@ __device__ __forceinline__ typename Num::val diag_coef(int i, int j, int d, cons
             else c = Num::add(c, jump_cplx<Num, RT>(t, q, i, j, d, vL, vR, uj));
         }
     };
-    if (t.jrate) jumps(std::true_type{});
+    if (!REALJ && t.jrate) jumps(std::true_type{});
     else jumps(std::false_type{});
     return c;
 }
@@ -394,7 +393,7 @@ __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::s
             else Num::mac(w, jump_cplx<Num, RT>(t, q, i, j, d, vL, vR, uj), Num::load(cur[aJ]));
         }
     };
-    if (t.jrate) jumps(std::true_type{});
+    if (!REALJ && t.jrate) jumps(std::true_type{});
     else jumps(std::false_type{});
     return Num::raw(w);
 }
@@ -712,7 +711,7 @@ __device__ __forceinline__ typename Num::val lindblad_g_at(const typename Num::s
             else Num::mac(w, jump_cplx<Num, RT>(t, q, i, j, d, vL, vR, uj), zv);
         }
     };
-    if (t.jrate) jumps(std::true_type{});
+    if (!REALJ && t.jrate) jumps(std::true_type{});
     else jumps(std::false_type{});
     return Num::raw(w);
 }
