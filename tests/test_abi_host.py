@@ -2,6 +2,7 @@
 declared symbol, descriptor validation rejects bad input before touching the
 device, and the package-side band model equals the oracle's dense operators."""
 import ctypes
+import dataclasses
 import os
 import re
 
@@ -152,3 +153,16 @@ def test_band_model_of_rate_controls():
     for (k, r, c), jb, rate in zip(dm.rate_ctl, bm.jumps[fixed:], bm.rates[fixed:]):
         assert r == rate
         assert np.max(np.abs(dense_of(jb, w.d) - c)) < 1e-15
+
+
+def test_create_validates_rate_controls():
+    w = workloads.small(Q=2, N=4, controls_=("res_x", "rate_a"))
+    bm = problem.band_model(w.phys)
+    bad = dataclasses.replace(bm, jump_control=[-1, 2])          # control index out of range
+    with pytest.raises(_lib.GrapeError) as e:
+        problem.GrapeProblem(bad, w.rho0, w.sigma, w.T, w.n_slices, w.n_rk)
+    assert e.value.status == _lib.GRAPE_EINVAL and "jump_control" in str(e.value)
+    bad = dataclasses.replace(bm, jump_control=[-1, 0])          # res_x has a Hamiltonian
+    with pytest.raises(_lib.GrapeError) as e:
+        problem.GrapeProblem(bad, w.rho0, w.sigma, w.T, w.n_slices, w.n_rk)
+    assert e.value.status == _lib.GRAPE_EINVAL and "empty Hamiltonian" in str(e.value)
