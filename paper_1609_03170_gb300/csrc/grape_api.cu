@@ -149,9 +149,16 @@ HostDir make_dir(const Bands &A0, const std::vector<Bands> &Ak,
     for (const auto &kv : A0) idx[kv.first] = 0;
     for (const auto &B : Ak)
         for (const auto &kv : B) idx[kv.first] = 0;
+    // the offset-0 band goes last: the kernels that fold it into the
+    // own-entry coefficient then loop over the first nb - 1 bands only
     for (auto &kv : idx) {
+        if (kv.first == 0) continue;
         kv.second = (int)h.off.size();
         h.off.push_back(kv.first);
+    }
+    if (idx.count(0)) {
+        idx[0] = (int)h.off.size();
+        h.off.push_back(0);
     }
     const int nb = (int)h.off.size(), R = (int)Ak.size();
     h.A0.assign((size_t)nb * d, cplx());

@@ -375,9 +375,10 @@ __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::s
     // The terms on the entry itself - the offset-0 band and the jump terms
     // with both offsets 0 - come as one coefficient D_ij (diag_coef).
     typename Num::acc w = Num::acc_zero();
-#pragma unroll 1
-    for (int b = 0; b < t.nb; ++b) {
-        if (b == t.b0) continue;
+    // the offset-0 band, when there is one, is the last (the host orders it so)
+    const int nbo = (t.b0 >= 0) ? t.nb - 1 : t.nb;
+#pragma unroll 2
+    for (int b = 0; b < nbo; ++b) {
         Num::mac(w, Num::load(A[b * d + i]), Num::load(cur[nb_ad[2 * b]]));
         Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[nb_ad[2 * b + 1]]));
     }
