@@ -19,6 +19,11 @@
  *            Re(-i dt Tr(lambda_j [H_k, rho_j])), lambda from backward RK4
  *            on L^+ starting at lambda_N = sigma (Sec. 3 backward integration)
  *   mode 0:  forward and cost only.
+ * Two variants of the paper: a control k may drive the rate of dissipator j
+ * (rate gamma_j u_k(j) in slice j, dL/du_k = gamma_j D[a_j]; the remarks after
+ * Eq. partialuk), and a running cost -beta dt sum_{n=0..N} Tr(A rho_n) with A
+ * diagonal (Sec. 5 and App. B, the photon-number penalty) adds -beta dt A to
+ * the adjoint at the final time and after every backward slice.
  *
  * Operators are sparse coordinate lists: op 0 = H_0, ops 1..R = H_k,
  * ops R+1..R+J = a_j.  Matrices are d x d row-major, complex values stored as
@@ -82,7 +87,16 @@ typedef struct {
     int d, R, J;
     sparse H0, *Hc, *jump, *jdj; /* jdj[m] = a_m^+ a_m */
     const double *rate;
+    const int *jctl;             /* NULL or [J]: control driving the rate of jump m, -1 none */
+    const double *pen;           /* NULL or [d]: diagonal of the running-cost operator A */
+    double beta;                 /* its weight */
 } model;
+
+/* the slice's generator: H_j and the effective rates */
+typedef struct {
+    sparse H;
+    double *g;
+} slice_op;
 
 static void set_zero(cplx *X, size_t n) { memset(X, 0, n * sizeof(cplx)); }
 
@@ -126,15 +140,27 @@ static sparse slice_hamiltonian(const model *m, const double *uj) {
 
 static void free_sparse(sparse *s) { free(s->r); free(s->c); free(s->v); }
 
+static slice_op slice_operator(const model *m, const double *uj) {
+    slice_op S;
+    S.H = slice_hamiltonian(m, uj);
+    S.g = malloc(sizeof(double) * (m->J + 1));
+    for (int j = 0; j < m->J; j++)
+        S.g[j] = m->rate[j] * ((m->jctl && m->jctl[j] >= 0) ? uj[m->jctl[j]] : 1.0);
+    return S;
+}
+
+static void free_slice(slice_op *S) { free_sparse(&S->H); free(S->g); }
+
 /* out = L rho (Eq. master) */
-static void lindblad(const model *m, const sparse *H, const cplx *rho, cplx *out, cplx *tmp) {
+static void lindblad(const model *m, const slice_op *S, const cplx *rho, cplx *out, cplx *tmp) {
     int d = m->d;
     size_t n = (size_t)d * d;
+    const sparse *H = &S->H;
     set_zero(out, n);
     left(H, -I, rho, out, d);
     right(H, I, rho, out, d);
     for (int j = 0; j < m->J; j++) {
-        double g = m->rate[j];
+        double g = S->g[j];
         set_zero(tmp, n);
         left(&m->jump[j], 1.0, rho, tmp, d);
         right_adj(&m->jump[j], g, tmp, out, d);
@@ -144,14 +170,15 @@ static void lindblad(const model *m, const sparse *H, const cplx *rho, cplx *out
 }
 
 /* out = L^+ X */
-static void lindblad_dual(const model *m, const sparse *H, const cplx *X, cplx *out, cplx *tmp) {
+static void lindblad_dual(const model *m, const slice_op *S, const cplx *X, cplx *out, cplx *tmp) {
     int d = m->d;
     size_t n = (size_t)d * d;
+    const sparse *H = &S->H;
     set_zero(out, n);
     left(H, I, X, out, d);
     right(H, -I, X, out, d);
     for (int j = 0; j < m->J; j++) {
-        double g = m->rate[j];
+        double g = S->g[j];
         set_zero(tmp, n);
         left_adj(&m->jump[j], 1.0, X, tmp, d);
         right(&m->jump[j], g, tmp, out, d);
@@ -160,10 +187,10 @@ static void lindblad_dual(const model *m, const sparse *H, const cplx *X, cplx *
     }
 }
 
-typedef void (*rhs_fn)(const model *, const sparse *, const cplx *, cplx *, cplx *);
+typedef void (*rhs_fn)(const model *, const slice_op *, const cplx *, cplx *, cplx *);
 
 /* one classic RK4 step y -> ynew; optionally keeps the four stage inputs */
-static void rk4(rhs_fn f, const model *m, const sparse *H, double h, const cplx *y,
+static void rk4(rhs_fn f, const model *m, const slice_op *H, double h, const cplx *y,
                 cplx *ynew, cplx *stage_in /* 4*n or NULL */, cplx *w /* 6*n work */) {
     size_t n = (size_t)m->d * m->d;
     cplx *k1 = w, *k2 = w + n, *k3 = w + 2 * n, *k4 = w + 3 * n, *yt = w + 4 * n, *tmp = w + 5 * n;
@@ -189,13 +216,38 @@ static cplx trace_prod(const cplx *A, const cplx *B, int d) {
     return s;
 }
 
-/* Re Tr(Kb (-i)[H_k, Y]) */
+/* Re Tr(Kb (dL/du_k) Y): (-i)[H_k, Y], plus gamma_j D[a_j] Y for every
+   dissipator j whose rate control k drives */
 static double control_term(const model *m, int k, const cplx *Kb, const cplx *Y, cplx *tmp) {
     int d = m->d;
-    set_zero(tmp, (size_t)d * d);
+    size_t n = (size_t)d * d;
+    set_zero(tmp, n);
     left(&m->Hc[k], -I, Y, tmp, d);
     right(&m->Hc[k], I, Y, tmp, d);
+    if (m->jctl) {
+        cplx *t2 = malloc(sizeof(cplx) * n);
+        for (int j = 0; j < m->J; j++) {
+            if (m->jctl[j] != k) continue;
+            double g = m->rate[j];
+            set_zero(t2, n);
+            left(&m->jump[j], 1.0, Y, t2, d);
+            right_adj(&m->jump[j], g, t2, tmp, d);
+            left(&m->jdj[j], -0.5 * g, Y, tmp, d);
+            right(&m->jdj[j], -0.5 * g, Y, tmp, d);
+        }
+        free(t2);
+    }
     return creal(trace_prod(Kb, tmp, d));
+}
+
+/* Re Tr(A X) for the diagonal A; and X += s A */
+static double pen_value(const model *m, const cplx *X) {
+    double t = 0;
+    for (int i = 0; i < m->d; i++) t += m->pen[i] * creal(X[(size_t)i * m->d + i]);
+    return t;
+}
+static void add_pen(const model *m, double s, cplx *X) {
+    for (int i = 0; i < m->d; i++) X[(size_t)i * m->d + i] += s * m->pen[i];
 }
 
 static void one_state(const model *m, int n_slices, int n_rk, double T, const double *u,
@@ -209,8 +261,9 @@ static void one_state(const model *m, int n_slices, int n_rk, double T, const do
     cplx *w = malloc(sizeof(cplx) * n * 6);
     memcpy(traj, rho0, n * sizeof(cplx));
     cplx *cur = traj;
+    double pen_sum = m->pen ? pen_value(m, cur) : 0.0;    /* boundary n = 0 */
     for (int j = 0; j < n_slices; j++) {
-        sparse H = slice_hamiltonian(m, u + (size_t)j * R);
+        slice_op H = slice_operator(m, u + (size_t)j * R);
         cplx *nxt = keep ? traj + (size_t)(j + 1) * n : traj + (size_t)((j + 1) & 1) * n;
         const cplx *y = cur;
         for (int r = 0; r < n_rk; r++) {
@@ -218,9 +271,10 @@ static void one_state(const model *m, int n_slices, int n_rk, double T, const do
             y = nxt;
         }
         cur = nxt;
-        free_sparse(&H);
+        if (m->pen) pen_sum += pen_value(m, cur);          /* boundary j + 1 */
+        free_slice(&H);
     }
-    *F = creal(trace_prod(sig, cur, d));
+    *F = creal(trace_prod(sig, cur, d)) - m->beta * dt * pen_sum;
     if (rhoT) memcpy(rhoT, cur, n * sizeof(cplx));
 
     if (mode == 1) {
@@ -230,8 +284,9 @@ static void one_state(const model *m, int n_slices, int n_rk, double T, const do
         cplx *kb = malloc(sizeof(cplx) * n), *yb = malloc(sizeof(cplx) * n * 4);
         cplx *tmp = malloc(sizeof(cplx) * n), *tmp2 = malloc(sizeof(cplx) * n);
         memcpy(mu, sig, n * sizeof(cplx));
+        if (m->pen) add_pen(m, -m->beta * dt, mu);
         for (int j = n_slices - 1; j >= 0; j--) {
-            sparse H = slice_hamiltonian(m, u + (size_t)j * R);
+            slice_op H = slice_operator(m, u + (size_t)j * R);
             /* stage inputs of the slice, recomputed from the saved rho_j */
             const cplx *y = traj + (size_t)j * n;
             for (int r = 0; r < n_rk; r++) {
@@ -253,25 +308,28 @@ static void one_state(const model *m, int n_slices, int n_rk, double T, const do
                 for (size_t i = 0; i < n; i++)
                     mu[i] += yb[i] + yb[n + i] + yb[2 * n + i] + yb[3 * n + i];
             }
-            free_sparse(&H);
+            if (m->pen) add_pen(m, -m->beta * dt, mu);      /* running cost at boundary j */
+            free_slice(&H);
         }
         free(mu); free(st); free(ys); free(kb); free(yb); free(tmp); free(tmp2);
     } else if (mode == 2) {
         cplx *lam = malloc(sizeof(cplx) * n), *lam2 = malloc(sizeof(cplx) * n);
         cplx *tmp = malloc(sizeof(cplx) * n);
         memcpy(lam, sig, n * sizeof(cplx));
+        if (m->pen) add_pen(m, -m->beta * dt, lam);
         for (int j = n_slices; j >= 1; j--) {
             const cplx *rho_j = traj + (size_t)j * n;
             for (int k = 0; k < R; k++) {
                 /* Re(-i dt Tr(lambda_j [H_k, rho_j])) = dt * Re Tr(lambda_j (-i)[H_k, rho_j]) */
                 G[(size_t)(j - 1) * R + k] += dt * control_term(m, k, lam, rho_j, tmp);
             }
-            sparse H = slice_hamiltonian(m, u + (size_t)(j - 1) * R);
+            slice_op H = slice_operator(m, u + (size_t)(j - 1) * R);
             for (int r = 0; r < n_rk; r++) {
                 rk4(lindblad_dual, m, &H, h, lam, lam2, NULL, w);
                 memcpy(lam, lam2, n * sizeof(cplx));
             }
-            free_sparse(&H);
+            if (m->pen) add_pen(m, -m->beta * dt, lam);
+            free_slice(&H);
         }
         free(lam); free(lam2); free(tmp);
     }
@@ -297,13 +355,15 @@ static sparse view(const int *op_ptr, const int *rows, const int *cols, const do
 int grape_oracle_run(int d, int n_states, int n_slices, int n_rk, double T,
                      int n_controls, int n_jumps,
                      const int *op_ptr, const int *rows, const int *cols, const double *vals,
-                     const double *rates,
+                     const double *rates, const int *jump_control,
+                     const double *pen_diag, double pen_beta,
                      const double *rho0, const double *sigma, int sigma_per_state,
                      const double *u, int mode, int n_threads,
                      double *F, double *grad, double *rhoT) {
     if (d <= 0 || n_states <= 0 || n_slices <= 0 || n_rk <= 0 || mode < 0 || mode > 2) return 1;
     model m;
     m.d = d; m.R = n_controls; m.J = n_jumps; m.rate = rates;
+    m.jctl = jump_control; m.pen = pen_diag; m.beta = pen_beta;
     m.H0 = view(op_ptr, rows, cols, vals, 0);
     m.Hc = malloc(sizeof(sparse) * (n_controls + 1));
     m.jump = malloc(sizeof(sparse) * (n_jumps + 1));

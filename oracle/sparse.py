@@ -47,7 +47,7 @@ def _load():
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
             ctypes.c_int, ctypes.c_int,
             P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_double),
-            P(ctypes.c_double),
+            P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_double), ctypes.c_double,
             P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int,
             P(ctypes.c_double), ctypes.c_int, ctypes.c_int,
             P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double)]
@@ -76,14 +76,17 @@ def _p(a, t):
     return a.ctypes.data_as(ctypes.POINTER(t))
 
 
-def run(phys, u, rho0s, sigma, T, n_rk, mode=MODE_EXACT, threads=0):
-    """Returns (F, grad or None, rhoT, seconds)."""
+def run(phys, u, rho0s, sigma, T, n_rk, mode=MODE_EXACT, threads=0, penalty=None, beta=0.0):
+    """Returns (F, grad or None, rhoT, seconds).  Controls on dissipation
+    rates come from the physics; `penalty` (the diagonal of A, length d) with
+    weight `beta` adds the running cost -beta dt sum_n Re Tr(A rho_n)."""
     lib = _load()
     model = operators.build(phys)
-    if model.rate_ctl:
-        raise NotImplementedError("the C oracle has no controls on dissipation rates")
-    ops = [model.H0] + list(model.Hc) + [c for _, c in model.jumps]
-    rates = np.array([g for g, _ in model.jumps], dtype=np.float64)
+    jumps = list(model.jumps) + [(r, c) for _, r, c in model.rate_ctl]
+    jctl = np.array([-1] * len(model.jumps) + [k for k, _, _ in model.rate_ctl], dtype=np.int32)
+    ops = [model.H0] + list(model.Hc) + [c for _, c in jumps]
+    rates = np.array([g for g, _ in jumps], dtype=np.float64)
+    pen = None if penalty is None else np.ascontiguousarray(penalty, dtype=np.float64)
     ptr, rows, cols, vals = _coo(ops)
     u = np.ascontiguousarray(u, dtype=np.float64)
     n_slices, R = u.shape
@@ -95,9 +98,11 @@ def run(phys, u, rho0s, sigma, T, n_rk, mode=MODE_EXACT, threads=0):
     G = np.zeros((n_slices, R))
     rhoT = np.zeros((n_states, d, d), dtype=np.complex128)
     t0 = time.perf_counter()
-    rc = lib.grape_oracle_run(d, n_states, n_slices, n_rk, float(T), R, len(model.jumps),
+    rc = lib.grape_oracle_run(d, n_states, n_slices, n_rk, float(T), R, len(jumps),
                               _p(ptr, ctypes.c_int), _p(rows, ctypes.c_int), _p(cols, ctypes.c_int),
                               _p(vals, ctypes.c_double), _p(rates, ctypes.c_double),
+                              _p(jctl, ctypes.c_int) if model.rate_ctl else None,
+                              _p(pen, ctypes.c_double) if pen is not None else None, float(beta),
                               _p(rho0s.view(np.float64), ctypes.c_double),
                               _p(sig.view(np.float64), ctypes.c_double), per_state,
                               _p(u, ctypes.c_double), int(mode), int(threads),
@@ -109,5 +114,6 @@ def run(phys, u, rho0s, sigma, T, n_rk, mode=MODE_EXACT, threads=0):
     return float(F[0]), (G if mode != MODE_FORWARD else None), rhoT, dt
 
 
-def run_workload(w, mode=MODE_EXACT, threads=0):
-    return run(w.phys, w.u, w.rho0, w.sigma, w.T, w.n_rk, mode=mode, threads=threads)
+def run_workload(w, mode=MODE_EXACT, threads=0, penalty=None, beta=0.0):
+    return run(w.phys, w.u, w.rho0, w.sigma, w.T, w.n_rk, mode=mode, threads=threads,
+               penalty=penalty, beta=beta)

@@ -131,3 +131,17 @@ def test_static_entry_point_rejects_a_penalty(gp):
     with pytest.raises(gp._lib.GrapeError) as e:
         gp._lib.grape_gradient_static(P.handle, u.data_ptr(), F.data_ptr(), G.data_ptr(), 0)
     assert e.value.status == gp._lib.GRAPE_EINVAL
+
+
+def test_d120_penalty_matches_the_c_oracle(gp):
+    """The d=120 problem (reduced to 12 slices) with the photon-number penalty
+    against the plain-C oracle's running cost."""
+    from oracle import sparse
+    w = workloads.transmon_resonator_d120(n_slices=12)
+    diag = np.repeat(np.arange(w.phys.N, dtype=np.float64), w.phys.Q)
+    beta = 0.2 / w.T
+    F_ref, G_ref, _, _ = sparse.run_workload(w, threads=3, penalty=diag, beta=beta)
+    P = gp.GrapeProblem.from_workload(w)
+    P.set_photon_penalty(w.phys.Q, w.phys.N, beta)
+    F, G = P.gradient(w.u)
+    assert abs(F - F_ref) < TOL * abs(F_ref) and rel(G, G_ref) < TOL

@@ -89,3 +89,17 @@ def test_rate_control_on_d20_with_checkpoints(gp):
     Pc = gp.GrapeProblem.from_workload(w, ckpt_stride=7)
     Fc, Gc = Pc.gradient(w.u)
     assert Fc == F and np.array_equal(Gc, G)
+
+
+def test_rate_controls_on_d120_match_the_c_oracle(gp):
+    """The d=120 model with a control on the resonator decay and one on the
+    transmon relaxation (12 slices) against the plain-C oracle."""
+    from oracle import sparse
+    base = workloads.transmon_resonator_d120(n_slices=12)
+    phys = dataclasses.replace(base.phys, controls=("res_x", "res_y", "rate_a", "rate_b"))
+    w = workloads.make("d120_rates", phys, T=base.T, n_slices=12, n_rk=4, states=base.states, u_bound=1.0)
+    w.u[:, 2:] = np.abs(w.u[:, 2:])
+    F_ref, G_ref, _, _ = sparse.run_workload(w, threads=3)
+    P = gp.GrapeProblem.from_workload(w)
+    F, G = P.gradient(w.u)
+    assert abs(F - F_ref) < TOL * abs(F_ref) and rel(G, G_ref) < TOL

@@ -280,3 +280,27 @@ def test_c_oracle_gradient_matches_fd_d120():
         Fp = sparse.run(w.phys, up, w.rho0, w.sigma, w.T, w.n_rk, mode=0, threads=3)[0]
         Fm = sparse.run(w.phys, um, w.rho0, w.sigma, w.T, w.n_rk, mode=0, threads=3)[0]
         assert abs((Fp - Fm) / 2e-5 - G[j, k]) < 1e-6 * np.max(np.abs(G))
+
+
+@pytest.mark.parametrize("mode", [sparse.MODE_EXACT, sparse.MODE_FIRST_ORDER])
+def test_c_oracle_equals_dense_with_rate_controls_and_penalty(mode):
+    """The C oracle's rate controls (remarks after Eq. partialuk) and running
+    cost (App. B) against the dense oracle, exact and first-order."""
+    from oracle import penalty
+    w = workloads.small(Q=2, N=4, n_slices=5, n_rk=2, T=0.6, gamma1=0.05,
+                        controls_=("res_x", "rate_a", "qub_y", "rate_b"))
+    w.u[:, 1] = np.abs(w.u[:, 1]) + 0.2
+    w.u[:, 3] = np.abs(w.u[:, 3])
+    m = operators.build(w.phys)
+    A = penalty.number_operator(w.phys)
+    beta = 0.35
+    F1, G1 = penalty.phi_and_gradient(m, w.u, w.rho0, w.sigma, w.T, w.n_rk, A, beta,
+                                      first_order=(mode == sparse.MODE_FIRST_ORDER))
+    F2, G2, _, _ = sparse.run_workload(w, mode=mode, threads=2, penalty=np.real(np.diag(A)), beta=beta)
+    assert abs(F1 - F2) < 1e-13 * abs(F1)
+    assert rel(G2, G1) < 1e-12
+    # and without the penalty, the rate controls alone
+    F3, G3 = (dense.gradient_exact if mode == sparse.MODE_EXACT else dense.gradient_first_order)(
+        m, w.u, w.rho0, w.sigma, w.T, w.n_rk)
+    F4, G4, _, _ = sparse.run_workload(w, mode=mode, threads=2)
+    assert abs(F3 - F4) < 1e-13 * abs(F3) and rel(G4, G3) < 1e-12
