@@ -21,6 +21,8 @@ forms; not the headline line):
   --workload serve     a Poisson trace of pulse optimisations (50 projected
                        L-BFGS iterations each) through the serving loop, with
                        continuous batching and one job at a time
+  --workload peaks     the measured FMA throughput of the FP32 and FP64 pipes
+                       (the ALU roofs of the double-float and native kernels)
   --scale s            multiplies every problem's number of slices
 """
 import argparse
@@ -41,10 +43,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GRAPE grad evals/s (fwd+adjoint), % HBM roofline; served p50/p99 latency"
 UNIT = "grad_evals/s"
-FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 nominal (recipe table)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x clock
+FP64_NOMINAL_TFLOPS = 1.25       # GB300 FP64, nominal (context only)
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x max clock (context only)
 DF_FP32_OPS_PER_FLOP = 6.0       # pair-arithmetic cost of one FP64-equivalent flop
 CPU_SAMPLE_SLICES = 200          # oracle sample: 200 of the 2000 slices
+FP64_SAMPLE_SLICES = 200         # native-FP64 arm: the first 200 of the 2000 slices
 
 
 def parse():
@@ -56,7 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="df64", choices=["df64", "fp64"],
                     help="kernel arithmetic: double-float on FP32 pipes or native FP64")
-    ap.add_argument("--workload", default="d120", choices=["d120", "d20", "d120f", "d120p", "sweep", "batch256", "d600", "serve"])
+    ap.add_argument("--workload", default="d120",
+                    choices=["d120", "d20", "d120f", "d120p", "sweep", "batch256", "d600", "serve", "peaks"])
     ap.add_argument("--scale", type=float, default=None,
                     help="slice-count multiplier of the batch256/serve/d600 workloads")
     ap.add_argument("--jobs", type=int, default=64, help="serve: jobs in the trace")
@@ -232,13 +236,50 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+def _dtype(args):
+    return "df64" if args.precision == "df64" else "f64"
+
+
 def _base_line(args, workload, value, unit, ms, extra):
     line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "df64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": _dtype(args), "data": "synthetic",
             "config": {"workload": workload}}
     line.update(extra)
     return line
+
+
+def _prec(args):
+    from paper_1609_03170_gb300 import _lib
+    return _lib.GRAPE_PREC_FP64 if args.precision == "fp64" else _lib.GRAPE_PREC_DF64
+
+
+def fma_peaks(dev):
+    """FMA throughput of the FP32 and FP64 pipes (grape_fma_peak), with the
+    SM clock sampled while the probes run."""
+    from paper_1609_03170_gb300 import _lib
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    fp32, fp32_ms = _lib.grape_fma_peak(_lib.GRAPE_PREC_DF64)
+    fp64, fp64_ms = _lib.grape_fma_peak(_lib.GRAPE_PREC_FP64)
+    time.sleep(0.3)
+    clk = clocks.stop()
+    return {"fp32_tflops": fp32, "fp64_tflops": fp64, "fp32_run_ms": fp32_ms,
+            "fp64_run_ms": fp64_ms, "clocks": clk,
+            "how": "grape_fma_peak: independent FMA chains (8 per thread) on every SM, "
+                   "best of 3 timed runs after a warm-up, CUDA events, 2 flops per FMA",
+            "nominal": {"fp32_tflops": FP32_NOMINAL_TFLOPS, "fp64_tflops": FP64_NOMINAL_TFLOPS}}
+
+
+def run_peaks(args):
+    p = fma_peaks(0)
+    if p["clocks"]:
+        ghz = p["clocks"]["sm_mhz"] / 1000.0
+        p["fp32_tflops_per_ghz"] = p["fp32_tflops"] / ghz
+        p["fp64_tflops_per_ghz"] = p["fp64_tflops"] / ghz
+    p["double_float_roof_tflops"] = p["fp32_tflops"] / DF_FP32_OPS_PER_FLOP
+    print(json.dumps({"workload": "peaks", **p}), flush=True)
 
 
 def run_batch256(args):
@@ -250,7 +291,7 @@ def run_batch256(args):
     for i in range(256):
         nt = workloads.batch_problem(i).n_slices
         ws.append(workloads.batch_problem(i, n_slices=max(4, int(round(nt * scale)))))
-    probs = [GrapeProblem.from_workload(w) for w in ws]
+    probs = [GrapeProblem.from_workload(w, precision=_prec(args)) for w in ws]
     us = [torch.from_numpy(w.u).cuda() for w in ws]
     stream = torch.cuda.Stream()
     # one problem at a time on one stream, on a sample (every 256/sample-th
@@ -263,7 +304,7 @@ def run_batch256(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     seq_sample_ms = 0.0
     for i in idx:
-        Pi = GrapeProblem.from_workload(ws[i])
+        Pi = GrapeProblem.from_workload(ws[i], precision=_prec(args))
         _lib.grape_gradient(Pi.handle, us[i].data_ptr(), Fd.data_ptr(), Gs[i].data_ptr(),
                             stream.cuda_stream)
         torch.cuda.synchronize()
@@ -320,7 +361,7 @@ def run_d600(args):
     scale = 1.0 if args.scale is None else args.scale
     n = max(2, int(round(40000 * scale)))
     w = workloads.transmon_resonator_d600(n_slices=n)
-    P = GrapeProblem.from_workload(w, ckpt_stride=200)
+    P = GrapeProblem.from_workload(w, ckpt_stride=200, precision=_prec(args))
     u = torch.from_numpy(w.u).cuda()
     P.set_profiling(True)
     for _ in range(args.warmup):
@@ -350,7 +391,7 @@ def run_d20(args):
     from oracle import sparse
     from paper_1609_03170_gb300 import GrapeProblem, _lib
     w = workloads.qubit_resonator_d20()
-    P = GrapeProblem.from_workload(w)
+    P = GrapeProblem.from_workload(w, precision=_prec(args))
     stream = torch.cuda.Stream()
     u = torch.from_numpy(w.u).cuda()
     F = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -397,7 +438,7 @@ def run_d120f(args):
     w0 = GaussianFilter.omega0_from_bandwidth(100.0 / 1.1)
     rng = np.random.default_rng(1609)
     u = torch.from_numpy(rng.uniform(-1, 1, size=(n_steps, w.n_controls))).cuda()
-    P = GrapeProblem.from_workload(w)
+    P = GrapeProblem.from_workload(w, precision=_prec(args))
     stream = torch.cuda.Stream()
     for _ in range(max(3, args.warmup)):
         P.gradient_filtered(u, [w0] * w.n_controls, stream=stream)
@@ -434,7 +475,7 @@ def run_d120p(args):
     import workloads
     from paper_1609_03170_gb300 import GrapeProblem
     w = workloads.transmon_resonator_d120()
-    P = GrapeProblem.from_workload(w)
+    P = GrapeProblem.from_workload(w, precision=_prec(args))
     P.set_photon_penalty(w.phys.Q, w.phys.N, 0.2 / w.T)
     u = torch.from_numpy(w.u).cuda()
     stream = torch.cuda.Stream()
@@ -625,6 +666,71 @@ def run_serve(args):
         "throughput_vs_serial": batched["jobs_per_s"] / serial["jobs_per_s"]})), flush=True)
 
 
+def native_fp64_arm(args, dev):
+    """The same gradient in native FP64 (GRAPE_PREC_FP64) on a bounded sample:
+    the first FP64_SAMPLE_SLICES slices of the d=120 problem (the same d,
+    states, controls and RK substeps), scaled to the whole problem, with the
+    adjoint launches' FP64-equivalent flops against the measured FP64 roof."""
+    import torch
+    import workloads
+    from paper_1609_03170_gb300 import GrapeProblem, _lib
+    from paper_1609_03170_gb300 import problem as _problem
+    w = workloads.transmon_resonator_d120(n_slices=FP64_SAMPLE_SLICES)
+    P = GrapeProblem.from_workload(w, precision=_lib.GRAPE_PREC_FP64)
+    stream = torch.cuda.Stream()
+    u = torch.from_numpy(w.u).cuda()
+    F = torch.empty(1, dtype=torch.float64, device="cuda")
+    G = torch.empty((w.n_slices, w.n_controls), dtype=torch.float64, device="cuda")
+
+    def step():
+        _lib.grape_gradient(P.handle, u.data_ptr(), F.data_ptr(), G.data_ptr(), stream.cuda_stream)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    reps = 3
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    P.set_profiling(True)
+    P.phase_times()
+    for _ in range(reps):
+        step()
+    torch.cuda.synchronize()
+    ph = P.phase_times()
+    bm = _problem.band_model(w.phys)
+    nb, nt, ndo = band_counts(bm)
+    counts = algorithmic_counts(w, nb, nt, ndo)
+    adj_ms, adj_n = ph["adjoint"]
+    achieved = counts["flops_adjoint"] * reps / (adj_ms * 1e-3) / 1e12
+    scale = 2000.0 / FP64_SAMPLE_SLICES
+    P.close()
+    return {"value": 1000.0 / (ms * scale), "unit": UNIT, "ms_per_step": ms * scale,
+            "dtype": "f64",
+            "sample": f"first {FP64_SAMPLE_SLICES} of the 2000 slices (same d, states, controls, "
+                      f"substeps), {ms:.2f} ms per gradient, scaled x{scale:g}",
+            "adjoint_tflops": achieved, "roof": "measured FP64 FMA throughput (alu_peaks.fp64_tflops)"}
+
+
+def band_counts(bm):
+    """Bands of A = H_eff (union of H0, control and c^+c offsets), jump
+    terms and distinct control-band offsets of a band model."""
+    offs = set(int(o) for o in bm.H0.offsets)
+    for h in bm.Hc:
+        offs |= set(int(o) for o in h.offsets)
+    for c in bm.jumps:
+        for o1 in c.offsets:
+            for o2 in c.offsets:
+                offs.add(int(o2) - int(o1))
+    nt = sum(len(c.offsets) ** 2 for c in bm.jumps)
+    ndo = len(set(int(o) for h in bm.Hc for o in h.offsets))
+    return len(offs), nt, ndo
+
+
 def main():
     args = parse()
     if args.workload != "d120":
@@ -632,7 +738,7 @@ def main():
         torch.cuda.set_device(0)
         {"batch256": run_batch256, "d600": run_d600, "serve": run_serve,
          "d20": run_d20, "d120f": run_d120f, "d120p": run_d120p,
-         "sweep": run_sweep}[args.workload](args)
+         "sweep": run_sweep, "peaks": run_peaks}[args.workload](args)
         return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":
@@ -711,6 +817,12 @@ def main():
     e2e_s = (time.perf_counter() - t0) / args.steps
     clk = clocks.stop()
 
+    # ---- measured FMA throughput (the ALU roofs) and the native-FP64 arm ---
+    peaks_alu = fma_peaks(dev)
+    fp64_arm = None
+    if args.precision == "df64":
+        fp64_arm = native_fp64_arm(args, dev)
+
     if dist:
         ms, e2e_s = max_over_ranks(dist, [ms, e2e_s])
     if rank != 0:
@@ -719,17 +831,8 @@ def main():
 
     from paper_1609_03170_gb300 import problem as _problem
     bm = _problem.band_model(w.phys)
-    # bands of A = H_eff (union of H0, controls and c^+c offsets) and jump terms
-    offs = set(int(o) for o in bm.H0.offsets)
-    for h in bm.Hc:
-        offs |= set(int(o) for o in h.offsets)
-    for c in bm.jumps:
-        for o1 in c.offsets:
-            for o2 in c.offsets:
-                offs.add(int(o2) - int(o1))
-    nt = sum(len(c.offsets) ** 2 for c in bm.jumps)
-    ndo = len(set(int(o) for h in bm.Hc for o in h.offsets))
-    counts = algorithmic_counts(w, len(offs), nt, ndo)
+    nb, nt, ndo = band_counts(bm)
+    counts = algorithmic_counts(w, nb, nt, ndo)
 
     fwd_ms, fwd_n = phases["forward"]
     adj_ms, adj_n = phases["adjoint"]
@@ -750,16 +853,17 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     if args.precision == "fp64":
-        peak_tflops, peak_source = FP64_PEAK_TFLOPS, "FP64 nominal 1.25 TFLOP/s (GB300)"
+        peak_tflops = peaks_alu["fp64_tflops"]
+        peak_source = "of measured: FP64 FMA throughput (grape_fma_peak) in this run"
     else:
         # double-float: FP64-equivalent flops on the FP32 pipes; the roof is the
-        # FP32 FMA rate (152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s)
-        # divided by the FP32 instructions one FP64-equivalent flop costs in the
-        # pair arithmetic (12 per real multiply-add: TwoProduct 2, cross terms 2,
-        # TwoSum 6, error gathering 2 -> 6 per flop)
-        peak_tflops = FP32_PEAK_TFLOPS / DF_FP32_OPS_PER_FLOP
-        peak_source = ("double-float roof: FP32 80.5 TFLOP/s nominal / 6 FP32 instructions "
-                       "per FP64-equivalent flop")
+        # FP32 FMA rate measured in this run divided by the FP32 instructions
+        # one FP64-equivalent flop costs in the pair arithmetic (12 per real
+        # multiply-add: TwoProduct 2, cross terms 2, TwoSum 6, error
+        # gathering 2 -> 6 per flop)
+        peak_tflops = peaks_alu["fp32_tflops"] / DF_FP32_OPS_PER_FLOP
+        peak_source = ("of measured: FP32 FMA throughput (grape_fma_peak) in this run / 6 FP32 "
+                       "instructions per FP64-equivalent flop")
     step_bytes = counts["bytes_forward"] + counts["bytes_adjoint"] + counts["bytes_trace"]
     value = world * 1000.0 / ms
     line = {
@@ -791,7 +895,12 @@ def main():
                 "d2h_bytes_per_step": int(F_host.numel() * 8 + G_host.numel() * 8)},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
+        "alu_peaks": peaks_alu,
     }
+    if fp64_arm is not None:
+        fp64_arm["frac"] = fp64_arm["adjoint_tflops"] / peaks_alu["fp64_tflops"]
+        fp64_arm["df64_speedup"] = value / fp64_arm["value"]
+        line["fp64"] = fp64_arm
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

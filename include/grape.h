@@ -19,7 +19,8 @@
  *  - controls u are slice-major: u[j * n_controls + k];
  *  - pointers passed to grape_forward / grape_gradient may be host or device
  *    memory (told apart with cudaPointerGetAttributes); device pointers must
- *    be on the problem's device and are only borrowed;
+ *    be memory of the problem's device (another device's memory is rejected
+ *    with GRAPE_EINVAL) and are only borrowed;
  *  - every call returns a grape_status; on failure grape_last_error() gives a
  *    thread-local message.  No call aborts, traps or waits without a bound.
  */
@@ -217,20 +218,27 @@ grape_status grape_phase_times(grape_problem_t problem, double ms[4], int32_t la
  * the device memory, host callbacks where cudaMalloc may not be called, or
  * latency-bound loops that must not wait on the allocator.  The problem is
  * created beforehand with grape_problem_create; the stage storage, the
- * propagated states and any checkpoints come from one file-scope device
- * array of 64 MiB that every GPU loading libgrape.so holds until the process
- * exits.  u, F and grad must be device pointers on the problem's device
- * (GRAPE_EINVAL otherwise); a problem whose scratch exceeds 64 MiB even with
- * one-slice checkpoint segments is rejected with GRAPE_EINVAL and a message
- * giving the bytes it needs.  The call makes no cudaMalloc/cudaFree and no
- * host allocation of its own; it only enqueues work on `stream`.
- * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array and it keeps the
- * last call's contents (nothing in it needs to start at zero: every buffer is
- * written before it is read), so calls whose GPU work overlaps - on two
- * streams, or from two threads - race and give wrong results: serialise them.
- * Results equal those of grape_gradient. */
+ * propagated states, the partial traces and any checkpoints come from one
+ * file-scope device array of 64 MiB per device, which stays held until the
+ * process exits.  It is committed on a device when the first problem is
+ * created there (grape_problem_create looks up its device address once per
+ * device, with that device current; a failed lookup makes this call return
+ * GRAPE_ECUDA), so this call itself makes no cudaMalloc/cudaFree, no
+ * module load and no host allocation of its own; it only enqueues work on
+ * `stream`.  u, F and grad must be device memory of the problem's device
+ * (GRAPE_EINVAL otherwise, also for another device's memory).  The
+ * checkpoint segment length is the longest whose scratch fits; a problem
+ * that needs more than 64 MiB with every segment length is rejected with
+ * GRAPE_EINVAL and a message giving the least bytes it needs, as is a
+ * problem with a running-cost penalty.  All calls share the one array and
+ * it keeps the last call's contents (nothing in it needs to start at zero:
+ * every buffer is written before it is read), so calls whose GPU work
+ * overlaps - on two streams, or from two threads - race and give wrong
+ * results: serialise them.  Results equal those of grape_gradient bit for
+ * bit (the traces are split and summed in the same order).  Grid-kernel
+ * problems (grape_problem_kernel == 2): this call cannot wait for the
+ * device, so after the stream has completed call grape_problem_status; on
+ * GRAPE_ETIMEOUT a grid barrier gave up and F and grad are invalid. */
 grape_status grape_gradient_static(grape_problem_t problem, const double *u, double *F,
                                    double *grad, void *stream);
 
@@ -324,6 +332,18 @@ int32_t grape_gradient_launches(grape_problem_t problem);
 
 /* Thread-local message of the last failed call on this thread. */
 const char *grape_last_error(void);
+
+/* Measured FMA throughput of the current device, the denominator of the
+ * propagation kernels' ALU roofline (a measurement helper; the paper has no
+ * counterpart).  precision = GRAPE_PREC_DF64 measures the FP32 pipes that the
+ * double-float kernels run on, GRAPE_PREC_FP64 the FP64 pipe of the native
+ * kernels.  A kernel of independent multiply-add chains (8 per thread, all
+ * SMs) runs once to warm up and three times timed with CUDA events on a
+ * private stream; *tflops = 2 x multiply-adds / best time (TFLOP/s), *ms =
+ * that time.  Allocates and frees a small output buffer; waits for the
+ * device.  Errors: GRAPE_EINVAL (NULL outputs, unknown precision),
+ * GRAPE_ECUDA. */
+grape_status grape_fma_peak(int32_t precision, double *tflops, double *ms);
 
 /* Library version string. */
 const char *grape_version(void);

@@ -62,7 +62,7 @@ EXPORTS = ["grape_problem_create", "grape_problem_destroy", "grape_forward", "gr
            "grape_batch_create", "grape_batch_destroy", "grape_batch_gradient", "grape_batch_info",
            "grape_problem_kernel", "grape_problem_status", "grape_server_create",
            "grape_server_destroy", "grape_submit", "grape_poll",
-           "grape_last_error", "grape_version"]
+           "grape_fma_peak", "grape_last_error", "grape_version"]
 
 
 def library_path() -> str:
@@ -137,6 +137,8 @@ def load(build_if_missing: bool = True):
     lib.grape_last_error.restype = ctypes.c_char_p
     lib.grape_version.argtypes = []
     lib.grape_version.restype = ctypes.c_char_p
+    lib.grape_fma_peak.argtypes = [c_int32, P(c_double), P(c_double)]
+    lib.grape_fma_peak.restype = c_int32
     _lib = lib
     return lib
 
@@ -317,3 +319,12 @@ def grape_gradient_launches(h) -> int:
 
 def grape_version() -> str:
     return load().grape_version().decode()
+
+
+def grape_fma_peak(precision: int):
+    """Measured FMA throughput of the current device: (TFLOP/s, ms of the
+    timed run) of the FP32 pipes (GRAPE_PREC_DF64) or the FP64 pipe
+    (GRAPE_PREC_FP64)."""
+    t, ms = c_double(), c_double()
+    check(load().grape_fma_peak(int(precision), ctypes.byref(t), ctypes.byref(ms)), "grape_fma_peak")
+    return float(t.value), float(ms.value)

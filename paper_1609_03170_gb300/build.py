@@ -1,6 +1,6 @@
 """Builds libgrape.so in-tree with nvcc for sm_103a (no cmake, no torch extension).
 
-The two translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 ``paper_1609_03170_gb300/libgrape.so``; object files go to ``_build/``.
 """
 from __future__ import annotations
@@ -17,7 +17,7 @@ INC = os.path.join(ROOT, "include")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgrape.so")
 SOURCES = ["grape_kernels_df.cu", "grape_kernels_f64.cu", "grape_api.cu", "grape_lbfgs.cu",
-           "grape_filter.cu"]
+           "grape_filter.cu", "grape_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

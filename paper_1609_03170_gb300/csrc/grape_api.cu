@@ -23,8 +23,14 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <climits>
+#include <cstdint>
 #include <string>
 #include <vector>
+
+// Looks up the device address of the no-allocation entry point's static
+// scratch array once per device (defined with the array, further below).
+static void static_scratch_setup(int dev);
 
 namespace {
 
@@ -181,14 +187,39 @@ HostDir make_dir(const Bands &A0, const std::vector<Bands> &Ak,
     return h;
 }
 
-bool is_device_ptr(const void *p) {
-    if (!p) return false;
+// Where a caller's pointer lives, for a call on device `dev`: *on_dev is set
+// for device memory of `dev` and for managed memory (the kernels read it
+// directly), cleared for host memory (pageable, pinned or registered: it is
+// copied through the problem's staging buffers).  Device memory of another
+// device is rejected with GRAPE_EINVAL: the kernels would dereference peer
+// memory, which faults without peer access.
+grape_status locate_ptr(const void *p, int dev, const char *name, bool *on_dev) {
+    *on_dev = false;
+    if (!p) return GRAPE_OK;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return GRAPE_OK;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) {
+        *on_dev = true;
+    } else if (a.type == cudaMemoryTypeDevice) {
+        if (a.device != dev)
+            return fail(GRAPE_EINVAL, std::string(name) + " is device memory of device " +
+                                          std::to_string(a.device) + ", not of the call's device " +
+                                          std::to_string(dev));
+        *on_dev = true;
+    }
+    return GRAPE_OK;
+}
+
+// locate_ptr for pointers that must be device memory of `dev`
+grape_status require_device_ptr(const void *p, int dev, const char *name) {
+    bool on_dev = false;
+    const grape_status st = locate_ptr(p, dev, name, &on_dev);
+    if (st != GRAPE_OK) return st;
+    if (!on_dev) return fail(GRAPE_EINVAL, std::string(name) + " must be device memory");
+    return GRAPE_OK;
 }
 
 int pow2ceil(long long x) {
@@ -891,7 +922,10 @@ grape_status stage_inputs(grape_problem *P, const double *u, const double **u_de
     const size_t ub = (size_t)P->n_slices * P->R * sizeof(double);
     if (P->R == 0) { *u_dev = P->d_u; return GRAPE_OK; }
     if (!u) return fail(GRAPE_EINVAL, "u is NULL");
-    if (is_device_ptr(u)) {
+    bool on_dev = false;
+    grape_status st = locate_ptr(u, P->device, "u", &on_dev);
+    if (st != GRAPE_OK) return st;
+    if (on_dev) {
         *u_dev = u;
     } else {
         GRAPE_CUDA_TRY(cudaMemcpyAsync(P->d_u, u, ub, cudaMemcpyHostToDevice, s));
@@ -1036,7 +1070,15 @@ extern "C" {
 
 const char *grape_last_error(void) { return g_last_error.c_str(); }
 
-const char *grape_version(void) { return "grape-gb300 0.2 (sm_103a, df64/fp64)"; }
+const char *grape_version(void) { return "grape-gb300 0.3 (sm_103a, df64/fp64)"; }
+
+grape_status grape_fma_peak(int32_t precision, double *tflops, double *ms) {
+    if (!tflops || !ms) return fail(GRAPE_EINVAL, "NULL tflops or ms");
+    if (precision != GRAPE_PREC_DF64 && precision != GRAPE_PREC_FP64)
+        return fail(GRAPE_EINVAL, "unknown precision");
+    GRAPE_CUDA_TRY(grape_probe_fma(precision, tflops, ms));
+    return GRAPE_OK;
+}
 
 grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_t *out) {
     if (!desc || !out) return fail(GRAPE_EINVAL, "NULL descriptor or output");
@@ -1199,6 +1241,7 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
         return fail(GRAPE_ECUDA, "no CUDA device");
     }
     P->device = dev;
+    static_scratch_setup(dev);   // grape_gradient_static's array, committed once per device
     P->d = d;
     P->d2 = d2;
     P->R = desc->n_controls;
@@ -1426,6 +1469,9 @@ grape_status grape_forward(grape_problem_t P, const double *u, double *F, double
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double *ud;
     grape_status st;
+    bool f_dev = false, r_dev = false;
+    if ((st = locate_ptr(F, P->device, "F", &f_dev)) != GRAPE_OK) return st;
+    if ((st = locate_ptr(rhoT, P->device, "rhoT", &r_dev)) != GRAPE_OK) return st;
     if ((st = stage_inputs(P, u, &ud, s)) != GRAPE_OK) return st;
     PropArgs a = base_args(P, 0, ud);
     a.sub_begin = 0;
@@ -1455,7 +1501,6 @@ grape_status grape_forward(grape_problem_t P, const double *u, double *F, double
         }
         if ((st = pen_rows(P, P->d_x, 0, 1, P->n_slices, s)) != GRAPE_OK) return st;
     }
-    const bool f_dev = is_device_ptr(F);
     if ((st = timed(P, PH_COST, s, [&] {
              return k_cost(P, P->d_x, f_dev ? F : P->d_F, s);
          })) != GRAPE_OK)
@@ -1464,7 +1509,6 @@ grape_status grape_forward(grape_problem_t P, const double *u, double *F, double
     bool sync = false;
     if (rhoT) {
         const size_t n = P->d2 * P->ns;
-        const bool r_dev = is_device_ptr(rhoT);
         GRAPE_CUDA_TRY(k_to_double(P, P->d_x, r_dev ? reinterpret_cast<double2 *>(rhoT) : P->d_out, n, s));
         if (!r_dev) {
             GRAPE_CUDA_TRY(cudaMemcpyAsync(rhoT, P->d_out, n * sizeof(double2), cudaMemcpyDeviceToHost, s));
@@ -1510,8 +1554,11 @@ grape_status filter_call(int32_t N, int32_t M, int32_t R, double Dt, double dt, 
     FilterArgs a;
     grape_status st = filter_args(N, M, R, Dt, dt, omega0, &a);
     if (st != GRAPE_OK) return st;
-    if (!is_device_ptr(in) || !is_device_ptr(out))
-        return fail(GRAPE_EINVAL, "filter: input and output must be device memory");
+    if (!in || !out) return fail(GRAPE_EINVAL, "filter: input and output must be device memory");
+    int dev = 0;
+    GRAPE_CUDA_TRY(cudaGetDevice(&dev));
+    if ((st = require_device_ptr(in, dev, "filter input")) != GRAPE_OK) return st;
+    if ((st = require_device_ptr(out, dev, "filter output")) != GRAPE_OK) return st;
     a.in = in;
     a.out = out;
     GRAPE_CUDA_TRY(grape_launch_filter(a, adjoint, static_cast<cudaStream_t>(stream)));
@@ -1546,7 +1593,9 @@ grape_status grape_gradient_filtered(grape_problem_t P, int32_t n_steps, const d
         P->d_fgs = static_cast<double *>(P->alloc(sub_b));
         if (!P->d_fs || !P->d_fgs) return fail(GRAPE_ENOMEM, "cudaMalloc failed for filtered controls");
     }
-    const bool u_dev = is_device_ptr(u), g_dev = is_device_ptr(grad);
+    bool u_dev = false, g_dev = false;
+    if ((st = locate_ptr(u, P->device, "u", &u_dev)) != GRAPE_OK) return st;
+    if ((st = locate_ptr(grad, P->device, "grad", &g_dev)) != GRAPE_OK) return st;
     if ((!u_dev || !g_dev) && P->f_steps < n_steps) {
         P->d_fu = static_cast<double *>(P->alloc(step_b));
         P->d_fgu = static_cast<double *>(P->alloc(step_b));
@@ -1574,11 +1623,12 @@ grape_status grape_gradient(grape_problem_t P, const double *u, double *F, doubl
     DeviceGuard g(P->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     grape_status st;
+    bool f_dev = false, g_dev = false;
+    if ((st = locate_ptr(F, P->device, "F", &f_dev)) != GRAPE_OK) return st;
+    if ((st = locate_ptr(grad, P->device, "grad", &g_dev)) != GRAPE_OK) return st;
     if ((st = plan_gradient(P)) != GRAPE_OK) return st;
     const double *ud;
     if ((st = stage_inputs(P, u, &ud, s)) != GRAPE_OK) return st;
-    const bool f_dev = is_device_ptr(F);
-    const bool g_dev = grad && is_device_ptr(grad);
     GradScratch S;
     S.Y = P->d_Y;
     S.K = P->d_K;
@@ -1628,8 +1678,9 @@ grape_status grape_gradient(grape_problem_t P, const double *u, double *F, doubl
 // called, or real-time loops that must not block on the allocator.  The
 // problem tables are created beforehand by grape_problem_create; every buffer
 // the gradient needs beyond its inputs and outputs (RK stage storage of the
-// forward and adjoint sweeps, checkpoints, the propagated state) comes from
-// the file-scope array below instead of cudaMalloc.
+// forward and adjoint sweeps, checkpoints, the propagated and adjoint states,
+// the partial traces) comes from the file-scope array below instead of
+// cudaMalloc.
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;   // 64 MiB per device
@@ -1638,14 +1689,36 @@ constexpr int kMaxDevices = 64;
 // Device memory held by every GPU that loads this library, until exit.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Device address of g_static_scratch per device, looked up once per device.
-// In host code the symbol name is only a host-side stand-in, never a device
-// address, so it must go through cudaGetSymbolAddress.
-void *g_static_ptr[kMaxDevices] = {};
+// Device address of g_static_scratch per device.  In host code the symbol
+// name is only a host-side stand-in, never a device address, so it goes
+// through cudaGetSymbolAddress once per device, with that device current.
+// That lookup also loads the module that holds the array (modules load
+// lazily), which is when the 64 MiB are committed on the device: it runs in
+// grape_problem_create, which allocates anyway, so that the static entry
+// point itself only reads the cached address.
+struct StaticScratch {
+    std::once_flag once;
+    void *ptr = nullptr;
+    cudaError_t err = cudaErrorNotReady;
+};
+StaticScratch g_static[kMaxDevices];
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
 }  // namespace
+
+// with device `dev` current
+static void static_scratch_setup(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return;
+    StaticScratch &sl = g_static[dev];
+    std::call_once(sl.once, [&] {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) cudaGetLastError();
+        sl.err = (e == cudaSuccess && !ptr) ? cudaErrorInvalidSymbol : e;
+        sl.ptr = (sl.err == cudaSuccess) ? ptr : nullptr;
+    });
+}
 
 extern "C" {
 
@@ -1654,44 +1727,56 @@ grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F
     if (!P || !u || !F || (!grad && P->R > 0)) return fail(GRAPE_EINVAL, "NULL problem, u, F or grad");
     if (P->device < 0 || P->device >= kMaxDevices) return fail(GRAPE_EINVAL, "device index too large");
     DeviceGuard g(P->device);
-    if (!is_device_ptr(u) || !is_device_ptr(F) || (P->R > 0 && !is_device_ptr(grad)))
-        return fail(GRAPE_EINVAL, "grape_gradient_static takes device pointers for u, F and grad");
+    grape_status st;
+    if ((st = require_device_ptr(u, P->device, "u")) != GRAPE_OK) return st;
+    if ((st = require_device_ptr(F, P->device, "F")) != GRAPE_OK) return st;
+    if (P->R > 0 && (st = require_device_ptr(grad, P->device, "grad")) != GRAPE_OK) return st;
     if (P->penalty)
         return fail(GRAPE_EINVAL, "grape_gradient_static does not evaluate the running-cost penalty");
-    if (!g_static_ptr[P->device]) {   // once per device, with that device current
-        void *ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-        if (e != cudaSuccess || !ptr)
-            return fail(GRAPE_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") +
-                                         cudaGetErrorString(e));
-        g_static_ptr[P->device] = ptr;
-    }
-    unsigned char *base = static_cast<unsigned char *>(g_static_ptr[P->device]);
+    static_scratch_setup(P->device);   // done by grape_problem_create; a no-op here
+    if (g_static[P->device].err != cudaSuccess)
+        return fail(GRAPE_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") +
+                                     cudaGetErrorString(g_static[P->device].err));
+    unsigned char *base = static_cast<unsigned char *>(g_static[P->device].ptr);
 
     // scratch plan: propagated state, adjoint state, stage storage of one
-    // segment (forward and adjoint) and, with several segments, checkpoints
+    // segment (forward and adjoint), the segment's partial traces and, with
+    // several segments, the checkpoints
     const bool exact = (P->mode == GRAPE_GRAD_EXACT);
+    const int nsplit = std::max(1, P->trace.nsplit);
     const size_t mat = align256(P->d2 * P->ns * sizeof(double2));
     auto per_seg = [&](long long sg) {
         return align256(exact ? (size_t)sg * P->n_rk * 4 * P->d2 * P->ns * sizeof(double2)
                               : (size_t)(sg + 1) * P->d2 * P->ns * sizeof(double2));
     };
+    auto part_bytes = [&](long long sg) {
+        return nsplit > 1 ? align256((size_t)sg * nsplit * std::max(P->R, 1) * sizeof(double)) : 0;
+    };
     auto need = [&](long long sg) {
         const long long ns = (P->n_slices + sg - 1) / sg;
-        return 2 * mat + 2 * per_seg(sg) + (ns > 1 ? (size_t)(ns + 1) * mat : 0);
+        return 2 * mat + 2 * per_seg(sg) + part_bytes(sg) + (ns > 1 ? (size_t)(ns + 1) * mat : 0);
     };
-    long long seg = P->n_slices;
-    while (seg > 1 && need(seg) > kStaticScratchBytes) seg = (seg + 1) / 2;
-    if (need(seg) > kStaticScratchBytes)
-        return fail(GRAPE_EINVAL, "problem needs " + std::to_string(need(seg)) +
-                                      " bytes of scratch; the static scratch holds " +
-                                      std::to_string(kStaticScratchBytes));
+    // the longest segment that fits (fewest launches); the need is not
+    // monotonic in the length (stage storage grows, checkpoints shrink), so
+    // every length is tried
+    long long seg = 0;
+    size_t least = SIZE_MAX;
+    for (long long sg = P->n_slices; sg >= 1; --sg) {
+        const size_t nb = need(sg);
+        least = std::min(least, nb);
+        if (nb <= kStaticScratchBytes) { seg = sg; break; }
+    }
+    if (seg == 0)
+        return fail(GRAPE_EINVAL, "problem needs at least " + std::to_string(least) +
+                                      " bytes of scratch with every checkpoint segment length; "
+                                      "the static scratch holds " + std::to_string(kStaticScratchBytes));
     const int nseg = (int)((P->n_slices + seg - 1) / seg);
     double2 *x = reinterpret_cast<double2 *>(base);
     double2 *mu = reinterpret_cast<double2 *>(base + mat);
     double2 *Y = reinterpret_cast<double2 *>(base + 2 * mat);
     double2 *K = reinterpret_cast<double2 *>(base + 2 * mat + per_seg(seg));
-    double2 *ckpt = reinterpret_cast<double2 *>(base + 2 * mat + 2 * per_seg(seg));
+    double *part = reinterpret_cast<double *>(base + 2 * mat + 2 * per_seg(seg));
+    double2 *ckpt = reinterpret_cast<double2 *>(base + 2 * mat + 2 * per_seg(seg) + part_bytes(seg));
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long nsub = (long long)P->n_slices * P->n_rk;
@@ -1733,9 +1818,12 @@ grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F
         if (exact) b.stage_store = K;
         else { b.bound_store = K; b.bound_step = P->n_rk; }
         GRAPE_CUDA_TRY(k_prop(P, b, s));
+        if (P->R == 0) continue;
+        // the problem's own split count, so that the traces are summed in
+        // the same order as in grape_gradient (identical bits)
         TraceArgs t = P->trace;
-        t.nsplit = 1;
-        t.part = nullptr;
+        t.nsplit = nsplit;
+        t.part = nsplit > 1 ? part : nullptr;
         t.n_rows = (int)(j1 - j0);
         t.G = grad + (size_t)j0 * P->R;
         if (exact) {
@@ -1749,7 +1837,10 @@ grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F
             t.npairs = P->ns;
             t.weight = P->T / P->n_slices;
         }
-        if (P->R > 0) GRAPE_CUDA_TRY(k_trace(P, t, s));
+        GRAPE_CUDA_TRY(k_trace(P, t, s));
+        if (nsplit > 1)
+            GRAPE_CUDA_TRY(P->prec == GRAPE_PREC_FP64 ? grape_launch_trace_finish_f64(t, s)
+                                                      : grape_launch_trace_finish_df(t, s));
     }
     return GRAPE_OK;
 }
@@ -2115,16 +2206,18 @@ grape_status grape_batch_gradient(grape_batch_t B, const double *const *u, doubl
     };
     if (B->exec && key == B->key) return launch();
     // validate once, outside the capture
-    if (!is_device_ptr(F)) return fail(GRAPE_EINVAL, "batch F must be device memory");
+    grape_status st = GRAPE_OK;
+    const int dev = B->device;
+    if ((st = require_device_ptr(F, dev, "batch F")) != GRAPE_OK) return st;
     for (int i = 0; i < n; ++i) {
-        if (!is_device_ptr(u[i]) || (B->probs[i]->R > 0 && !is_device_ptr(grad[i])))
-            return fail(GRAPE_EINVAL, "batch u and grad must be device memory");
+        if ((st = require_device_ptr(u[i], dev, "batch u")) != GRAPE_OK) return st;
+        if (B->probs[i]->R > 0 && (st = require_device_ptr(grad[i], dev, "batch grad")) != GRAPE_OK)
+            return st;
     }
     if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
     if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
     std::vector<bool> prof(n);
     for (int i = 0; i < n; ++i) { prof[i] = B->probs[i]->profiling; B->probs[i]->profiling = false; }
-    grape_status st = GRAPE_OK;
     GRAPE_CUDA_TRY(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeRelaxed));
     cudaError_t e = cudaEventRecord(B->fork, B->cap);
     for (int l = 0; l < B->n_lanes && e == cudaSuccess && st == GRAPE_OK; ++l) {

@@ -180,3 +180,8 @@ struct FilterArgs {
     double *out;
 };
 cudaError_t grape_launch_filter(const FilterArgs &a, bool adjoint, cudaStream_t s);
+
+// FMA throughput of the current device (grape_probe.cu): TFLOP/s (two flops
+// per multiply-add) of the FP32 pipes (GRAPE_PREC_DF64) or the FP64 pipe
+// (GRAPE_PREC_FP64), and the duration of the timed run.
+cudaError_t grape_probe_fma(int precision, double *tflops, double *ms);

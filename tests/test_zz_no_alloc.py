@@ -1,11 +1,15 @@
 """grape_gradient_static: the gradient for callers that cannot allocate
 device memory (their allocator owns the device memory, or they run where
 cudaMalloc may not be called).  Its scratch lives in a static 64 MiB device
-array; its results must equal grape_gradient's, call after call.
+array; its results must equal grape_gradient's, call after call: within the
+parity tolerance and, since the traces are split and summed in the same
+order, bit for bit.
 
 This file is collected last on purpose, so that a run stopping at the first
 failure has already run every other test.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -24,9 +28,27 @@ def torch_cuda():
     return torch
 
 
-def _compare(torch, w, grad_mode=0):
+class env:
+    """Environment variables the library reads when a problem is created."""
+    def __init__(self, **kv):
+        self.kv = kv
+
+    def __enter__(self):
+        self.old = {k: os.environ.get(k) for k in self.kv}
+        os.environ.update({k: str(v) for k, v in self.kv.items()})
+
+    def __exit__(self, *a):
+        for k, v in self.old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def _compare(torch, w, grad_mode=0, **create_env):
     from paper_1609_03170_gb300 import GrapeProblem, _lib
-    P = GrapeProblem.from_workload(w, grad_mode=grad_mode)
+    with env(**create_env):
+        P = GrapeProblem.from_workload(w, grad_mode=grad_mode)
     u = torch.from_numpy(w.u).cuda()
     F_ref = torch.empty(1, dtype=torch.float64, device="cuda")
     G_ref = torch.empty((w.n_slices, w.n_controls), dtype=torch.float64, device="cuda")
@@ -41,6 +63,8 @@ def _compare(torch, w, grad_mode=0):
         torch.cuda.synchronize()
         assert abs(F.item() - F_ref.item()) <= TOL * abs(F_ref.item())
         assert float((G - G_ref).abs().max()) <= TOL * scale
+        assert F.item() == F_ref.item() and torch.equal(G, G_ref)
+    return P
 
 
 def test_static_gradient_matches_allocating_gradient(torch_cuda):
@@ -79,3 +103,35 @@ def test_static_gradient_rejects_host_pointers_and_oversize(torch_cuda):
     with pytest.raises(_lib.GrapeError) as e:
         _lib.grape_gradient_static(Pb.handle, u.data_ptr(), Fd.data_ptr(), Gd.data_ptr(), 0)
     assert e.value.status == _lib.GRAPE_EINVAL and "static scratch" in str(e.value)
+
+
+def test_static_gradient_on_the_grid_kernel(torch_cuda):
+    """A problem forced onto the grid kernel: same results as grape_gradient,
+    and no barrier gave up (grape_problem_status after the stream)."""
+    from paper_1609_03170_gb300 import _lib
+    w = workloads.small(Q=3, N=7, n_slices=9, n_rk=3, T=0.9, gamma1=0.2, gamma_phi=0.1,
+                        controls_=("res_x", "res_y", "qub_x"))
+    P = _compare(torch_cuda, w, GRAPE_KERNEL="grid", GRAPE_GRID_BLOCKS=7)
+    assert P.kernel() == "grid"
+    _lib.grape_problem_status(P.handle)
+
+
+def test_static_gradient_reports_a_grid_barrier_timeout(torch_cuda):
+    """With a barrier limit of zero polls the grid kernel's barriers give up
+    by design: the static call only enqueues work and returns, and
+    grape_problem_status after the stream reports GRAPE_ETIMEOUT (results
+    invalid); the flag is cleared and the device stays usable."""
+    from paper_1609_03170_gb300 import GrapeProblem, _lib
+    w = workloads.small(Q=2, N=6, n_slices=3, n_rk=2)
+    with env(GRAPE_KERNEL="grid", GRAPE_GRID_BLOCKS=8, GRAPE_SPIN_LIMIT=0):
+        P = GrapeProblem.from_workload(w)
+    u = torch_cuda.from_numpy(w.u).cuda()
+    F = torch_cuda.empty(1, dtype=torch_cuda.float64, device="cuda")
+    G = torch_cuda.empty((w.n_slices, w.n_controls), dtype=torch_cuda.float64, device="cuda")
+    _lib.grape_gradient_static(P.handle, u.data_ptr(), F.data_ptr(), G.data_ptr(), 0)
+    torch_cuda.cuda.synchronize()
+    with pytest.raises(_lib.GrapeError) as e:
+        _lib.grape_problem_status(P.handle)
+    assert e.value.status == _lib.GRAPE_ETIMEOUT
+    _lib.grape_problem_status(P.handle)          # cleared after the report
+    _compare(torch_cuda, w)                      # the context is intact
