@@ -107,12 +107,14 @@ def algorithmic_counts(w, nb, nt, ndo):
     complex entry, added) and 8 for the stage combinations.  Trace per
     stage pair: one complex multiply-add per entry and distinct control-band
     offset.  Bytes: every stage input is written once by the forward and the
-    adjoint sweep and read once by the trace kernel (16 B per entry)."""
+    adjoint sweep and read once by the trace kernel, as a packed upper
+    triangle (16 B per upper entry: the stage values are Hermitian)."""
     d2 = w.d * w.d
     entries = 4 * w.n_slices * w.n_rk * w.n_states * d2
+    upper = 4 * w.n_slices * w.n_rk * w.n_states * (w.d * (w.d + 1) // 2)
     f_prop = (16 * nb + 4 * nt + 8) * entries
     f_trace = 8 * ndo * entries
-    bytes_prop = 16 * entries
+    bytes_prop = 16 * upper
     return {"flops_forward": f_prop, "flops_adjoint": f_prop, "flops_trace": f_trace,
             "bytes_forward": bytes_prop, "bytes_adjoint": bytes_prop,
             "bytes_trace": 2 * bytes_prop, "entries": entries}

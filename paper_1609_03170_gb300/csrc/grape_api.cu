@@ -142,6 +142,7 @@ bool hermitian(const Bands &A, int d) {
 
 struct HostDir {
     std::vector<int> off;        // nb
+    int nbr = 0;                 // leading bands that are real for every control value
     std::vector<cplx> A0, Ak;    // [nb][d], [R][nb][d]
     std::vector<int> oL, oR;     // nt
     std::vector<cplx> vL, vR;    // [nt][d]
@@ -155,13 +156,30 @@ HostDir make_dir(const Bands &A0, const std::vector<Bands> &Ak,
     for (const auto &kv : A0) idx[kv.first] = 0;
     for (const auto &B : Ak)
         for (const auto &kv : B) idx[kv.first] = 0;
-    // the offset-0 band goes last: the kernels that fold it into the
+    // bands whose values are real for every control value (A0 and every Ak
+    // real there) come first: the kernels multiply them as real numbers.
+    // The offset-0 band goes last: the kernels that fold it into the
     // own-entry coefficient then loop over the first nb - 1 bands only
-    for (auto &kv : idx) {
-        if (kv.first == 0) continue;
-        kv.second = (int)h.off.size();
-        h.off.push_back(kv.first);
-    }
+    auto real_band = [&](int o) {
+        auto is_real = [](const Bands &B, int o) {
+            auto it = B.find(o);
+            if (it == B.end()) return true;
+            for (const cplx &c : it->second)
+                if (c.imag() != 0.0) return false;
+            return true;
+        };
+        if (!is_real(A0, o)) return false;
+        for (const auto &B : Ak)
+            if (!is_real(B, o)) return false;
+        return true;
+    };
+    for (int pass = 0; pass < 2; ++pass)
+        for (auto &kv : idx) {
+            if (kv.first == 0 || real_band(kv.first) != (pass == 0)) continue;
+            kv.second = (int)h.off.size();
+            h.off.push_back(kv.first);
+            if (pass == 0) h.nbr++;
+        }
     if (idx.count(0)) {
         idx[0] = (int)h.off.size();
         h.off.push_back(0);
@@ -256,6 +274,8 @@ struct grape_problem {
     int variant = 0;                 // bit 0 = real jump tables, bit 1 = Hermitian kernel
     int hb = 0, cu = 0, maxwin = 0, htab_len = 0, rt_rows = 0;   // Hermitian kernel geometry
     int fold = 0;                    // Hermitian kernel: own-entry coefficients cached in shared memory
+    int bulk = 0;                    // Hermitian kernel: stage storage through staging rows and bulk copies
+    int jcache = 0;                  // Hermitian kernel: jump coefficients cached per entry
     int omax = 0;                    // largest band offset of either Lindbladian
     int hb_h = 0;                    // lower entries the Hermitian stencil reads
     std::map<int, int *> htabs;      // Hermitian tables per cluster width
@@ -394,6 +414,7 @@ grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
     std::memset(t, 0, sizeof(*t));
     t->nb = (int)h.off.size();
     t->nt = (int)h.oL.size();
+    t->nbr = h.nbr;
     for (int b = 0; b < t->nb; ++b) {
         t->off[b] = h.off[b];
         t->off_row[b] = h.off[b] * d;
@@ -629,23 +650,51 @@ grape_status plan_h(grape_problem *P, int ncl, int threads) {
     int maxwin = 0, cu = 0, rt_rows = 0;
     const std::vector<int> tab = hermitian_table(d, ncl, P->omax, hb, &maxwin, &cu, &rt_rows);
     if (maxwin >= 32767) return fail(GRAPE_EINVAL, "state window too large for 16-bit addresses");
-    const size_t smem = ((size_t)2 * (maxwin + 1) + 2 * (size_t)cu + 2 * (size_t)nb * d +
-                         2 * (size_t)nt * d) * sizeof(double2) +
+    // shared memory without windows, own-entry and jump-coefficient tables
+    const size_t base = (2 * (size_t)cu + 2 * (size_t)nb * d + 2 * (size_t)nt * d) * sizeof(double2) +
                         (size_t)cu * sizeof(int2) + 12 * sizeof(double) + tab.size() * sizeof(int) +
                         (size_t)rt_rows * (ncl + 1) * sizeof(uint32_t) +
                         (size_t)cu * (2 * nb + nt + 1) * sizeof(short);
     const int variant = (P->variant & 1) | 2;
-    // own-entry coefficients cached per slice (16 B per owned entry) when the
-    // table fits, else recomputed every stage: the same values either way
-    bool fold = true;
-    if (const char *env = std::getenv("GRAPE_FOLD")) fold = std::atoi(env) != 0;
-    const size_t smem_fold = smem + (size_t)cu * sizeof(double2);
-    fold = fold && smem_fold + 1024 <= (size_t)max_smem && cluster_fits(P, variant, threads, smem_fold, ncl);
-    const size_t use = fold ? smem_fold : smem;
-    if (!fold) {
-        if (use + 1024 > (size_t)max_smem) return fail(GRAPE_EINVAL, "state window does not fit in shared memory");
-        if (!cluster_fits(P, variant, threads, use, ncl))
-            return fail(GRAPE_EINVAL, "no cluster of this shape can be resident");
+    // Options, each kept only when the tile still fits (the same values, so
+    // the same bits, either way): the own-entry coefficients cached per slice
+    // (16 B per owned entry) instead of recomputed every stage; two staging
+    // rows of the owned entries (32 B per owned entry), through which the
+    // stage inputs reach the stage storage by bulk asynchronous copies
+    // instead of per-thread stores; the jump coefficients of real jump
+    // tables cached per entry (8 B per term with an offset and owned entry).
+    bool want_fold = true, want_bulk = true, want_jc = (variant & 1) != 0;
+    if (const char *env = std::getenv("GRAPE_FOLD")) want_fold = std::atoi(env) != 0;
+    if (const char *env = std::getenv("GRAPE_BULK")) want_bulk = std::atoi(env) != 0;
+    if (const char *env = std::getenv("GRAPE_JCACHE")) want_jc = want_jc && std::atoi(env) != 0;
+    int njt = 0;
+    for (int q = 0; q < P->tab[0].nt; ++q) njt += ((P->tab[0].jdiag >> q) & 1) ? 0 : 1;
+    int njt_d = 0;
+    for (int q = 0; q < P->tab[1].nt; ++q) njt_d += ((P->tab[1].jdiag >> q) & 1) ? 0 : 1;
+    njt = std::max(njt, njt_d);
+    struct Opt { bool fold, bulk, jc; };
+    const Opt opts[] = {{true, true, true}, {true, true, false}, {true, false, true},
+                        {true, false, false}, {false, true, false}, {false, false, false}};
+    size_t use = 0;
+    bool found = false, fold = false, bulk = false, jcache = false;
+    for (const Opt &o : opts) {
+        if ((o.fold && !want_fold) || (o.bulk && !want_bulk) || (o.jc && !want_jc)) continue;
+        const size_t sm = base + 2 * (size_t)(maxwin + 1) * sizeof(double2) +
+                          (o.fold ? (size_t)cu * sizeof(double2) : 0) +
+                          (o.bulk ? 2 * (size_t)cu * sizeof(double2) : 0) +
+                          (o.jc ? (size_t)njt * cu * sizeof(double) : 0);
+        if (sm + 1024 > (size_t)max_smem || !cluster_fits(P, variant, threads, sm, ncl)) continue;
+        use = sm;
+        fold = o.fold;
+        bulk = o.bulk;
+        jcache = o.jc;
+        found = true;
+        break;
+    }
+    if (!found) {
+        const size_t least = base + 2 * (size_t)(maxwin + 1) * sizeof(double2);
+        if (least + 1024 > (size_t)max_smem) return fail(GRAPE_EINVAL, "state window does not fit in shared memory");
+        return fail(GRAPE_EINVAL, "no cluster of this shape can be resident");
     }
     auto it = P->htabs.find(ncl);
     if (it == P->htabs.end()) {
@@ -664,6 +713,8 @@ grape_status plan_h(grape_problem *P, int ncl, int threads) {
     P->rt_rows = rt_rows;
     P->smem = use;
     P->fold = fold ? 1 : 0;
+    P->bulk = bulk ? 1 : 0;
+    P->jcache = jcache ? 1 : 0;
     P->threads = threads;
     P->chunk = cu;
     P->halo = 0;
@@ -773,6 +824,8 @@ PropArgs base_args(const grape_problem *P, int dir, const double *u) {
     a.maxwin = P->maxwin;
     a.rt_rows = P->rt_rows;
     a.fold = (P->variant & 2) ? P->fold : 0;
+    a.bulk = (P->variant & 2) ? P->bulk : 0;
+    a.jcache = (P->variant & 2) ? P->jcache : 0;
     a.src = P->penalty ? P->d_src : nullptr;
     a.gbuf = P->d_gbuf;
     a.gbar = P->d_gbar;
@@ -782,13 +835,25 @@ PropArgs base_args(const grape_problem *P, int dir, const double *u) {
     return a;
 }
 
+// Entries of one set of stored stage values (all states): the exact
+// gradient's stage storage holds packed upper triangles (d(d+1)/2 entries
+// per state), the first-order mode's slice boundaries and the checkpoints
+// hold full matrices (d^2).
+size_t packed_set(const grape_problem *P) { return (size_t)P->d * (P->d + 1) / 2 * P->ns; }
+size_t full_set(const grape_problem *P) { return P->d2 * P->ns; }
+
+// stage storage of one segment, Y or K, in bytes
+size_t stage_bytes(const grape_problem *P, long long seg) {
+    return (P->mode == GRAPE_GRAD_EXACT) ? (size_t)seg * P->n_rk * 4 * packed_set(P) * sizeof(double2)
+                                         : (size_t)(seg + 1) * full_set(P) * sizeof(double2);
+}
+// checkpoints of a segment plan, in bytes
+size_t ckpt_bytes(const grape_problem *P, long long seg) {
+    return seg < P->n_slices ? (size_t)((P->n_slices + seg - 1) / seg + 1) * full_set(P) * sizeof(double2) : 0;
+}
+
 size_t seg_bytes(const grape_problem *P, long long seg) {
-    const size_t mat = P->d2 * sizeof(double2) * P->ns;
-    const size_t per = (P->mode == GRAPE_GRAD_EXACT) ? (size_t)seg * P->n_rk * 4 * mat
-                                                    : (size_t)(seg + 1) * mat;
-    size_t total = 2 * per;
-    if (seg < P->n_slices) total += (size_t)((P->n_slices + seg - 1) / seg + 1) * mat;
-    return total;
+    return 2 * stage_bytes(P, seg) + ckpt_bytes(P, seg);
 }
 
 // Device buffers one gradient evaluation needs beyond its inputs and outputs.
@@ -804,25 +869,29 @@ long long trace_pairs(const grape_problem *P) {
     return (P->mode == GRAPE_GRAD_EXACT) ? (long long)P->n_rk * 4 * P->ns : (long long)P->ns;
 }
 
-// Splits of each slice's trace over CTAs, a constant of the problem (so the
+// Splits of each slice's trace over CTAs, constants of the problem (so the
 // summation order, and with it every bit of the gradient, does not depend on
-// how the slices are grouped into launches): each split takes a contiguous
-// range of the slice's stage pairs worth about 2^17 band-element products.
-int trace_splits(const grape_problem *P) {
+// how the slices are grouped into launches or on the propagation tile).
+// Exact gradient (packed storage): per state, chunks of 256 x epc upper
+// entries, epc chosen so that a state has at most 64 chunks.  First-order
+// mode (full matrices): contiguous ranges of the slice's pairs worth about
+// 2^17 band-element products each.
+void trace_layout(const grape_problem *P, TraceArgs *t) {
+    t->n_states = P->ns;
+    if (P->mode == GRAPE_GRAD_EXACT) {
+        const long long nu = (long long)P->d * (P->d + 1) / 2;
+        t->packed = 1;
+        t->epc = (int)std::max<long long>(1, (nu + 256 * 64 - 1) / (256 * 64));
+        t->nchunk = (int)((nu + 256LL * t->epc - 1) / (256LL * t->epc));
+        t->nsplit = P->ns * t->nchunk;
+        return;
+    }
     const long long npairs = trace_pairs(P);
-    const long long work = (long long)P->d * P->d * std::max(1, P->trace.ndo);
+    const long long work = (long long)P->d * P->d * std::max(1, t->ndo);
     const long long per = std::max<long long>(1, ((1LL << 17) + work - 1) / work);
-    return (int)std::max<long long>(1, (npairs + per - 1) / per);
-}
-
-// stage storage of one segment (Y and K) and the checkpoints, in bytes
-size_t stage_bytes(const grape_problem *P, long long seg) {
-    const size_t mat = P->d2 * sizeof(double2) * P->ns;
-    return (P->mode == GRAPE_GRAD_EXACT) ? (size_t)seg * P->n_rk * 4 * mat : (size_t)(seg + 1) * mat;
-}
-size_t ckpt_bytes(const grape_problem *P, long long seg) {
-    const size_t mat = P->d2 * sizeof(double2) * P->ns;
-    return seg < P->n_slices ? (size_t)((P->n_slices + seg - 1) / seg + 1) * mat : 0;
+    t->packed = 0;
+    t->epc = t->nchunk = 1;
+    t->nsplit = (int)std::max<long long>(1, (npairs + per - 1) / per);
 }
 
 // largest segment (halving from the whole problem) whose storage fits the budget
@@ -876,15 +945,13 @@ grape_status plan_gradient(grape_problem *P, size_t budget_override = 0) {
     }
     if (seg_bytes(P, seg) > budget && P->ckpt_stride <= 0)
         return fail(GRAPE_ENOMEM, "gradient storage does not fit in device memory");
-    const size_t mat = P->d2 * sizeof(double2) * P->ns;
-    const size_t per = (P->mode == GRAPE_GRAD_EXACT) ? (size_t)seg * P->n_rk * 4 * mat
-                                                    : (size_t)(seg + 1) * mat;
+    const size_t per = stage_bytes(P, seg);
     P->d_Y = static_cast<double2 *>(P->alloc_grad(per));
     P->d_K = static_cast<double2 *>(P->alloc_grad(per));
     if (!P->d_Y || !P->d_K) return fail(GRAPE_ENOMEM, "cudaMalloc failed for gradient storage");
     const int nseg = (int)((P->n_slices + seg - 1) / seg);
     if (nseg > 1) {
-        P->d_ckpt = static_cast<double2 *>(P->alloc_grad((size_t)(nseg + 1) * mat));
+        P->d_ckpt = static_cast<double2 *>(P->alloc_grad(ckpt_bytes(P, seg)));
         if (!P->d_ckpt) return fail(GRAPE_ENOMEM, "cudaMalloc failed for checkpoints");
     }
     P->seg = (int)seg;
@@ -937,14 +1004,15 @@ grape_status stage_inputs(grape_problem *P, const double *u, const double **u_de
 }  // namespace
 
 // Running-cost penalty launches (App. B).  pen_rows: Re Tr(A rho_n) for
-// `rows` consecutive boundary states stored `stride` entries apart.
+// `rows` consecutive boundary states stored `stride` entries apart (packed:
+// upper triangles, as in the exact gradient's stage storage).
 grape_status pen_rows(grape_problem *P, const void *x, long long stride, long long rows, long long first,
-                      cudaStream_t s) {
+                      cudaStream_t s, int packed = 0) {
     GRAPE_CUDA_TRY(P->prec == GRAPE_PREC_FP64
                        ? grape_launch_penalty_rows_f64(x, stride, (int)rows, P->ns, P->d, P->d_pdiag,
-                                                       P->d_pen + first, s)
+                                                       P->d_pen + first, packed, s)
                        : grape_launch_penalty_rows_df(x, stride, (int)rows, P->ns, P->d, P->d_pdiag,
-                                                      P->d_pen + first, s));
+                                                      P->d_pen + first, packed, s));
     return GRAPE_OK;
 }
 grape_status pen_finish(grape_problem *P, double *F, cudaStream_t s) {
@@ -965,7 +1033,8 @@ grape_status run_gradient(grape_problem *P, const double *ud, double *Fd, double
     const bool exact = (P->mode == GRAPE_GRAD_EXACT);
     const long long nsub = (long long)P->n_slices * P->n_rk;
     const double dt = P->T / P->n_slices;
-    const size_t mat = P->d2 * P->ns;
+    const size_t mat = full_set(P);                  // a state set as full matrices
+    const size_t pst = exact ? packed_set(P) : mat;  // a stored stage set (packed in exact mode)
 
     // forward sweep: stage storage directly (one segment) or checkpoints
     PropArgs f = base_args(P, 0, ud);
@@ -989,7 +1058,7 @@ grape_status run_gradient(grape_problem *P, const double *ud, double *Fd, double
                                    cudaMemcpyDeviceToDevice, s));
     // boundary state n of a segment in the stage storage: the input of the
     // slice's first stage (exact mode) or the stored boundary (first order)
-    const long long bstride = (long long)(exact ? (size_t)P->n_rk * 4 * mat : mat);
+    const long long bstride = (long long)(exact ? (size_t)P->n_rk * 4 * pst : mat);
     if (P->penalty) {
         GRAPE_CUDA_TRY(P->prec == GRAPE_PREC_FP64
                            ? grape_launch_add_diag_f64(S.mu, P->d_src, P->d, P->ns, s)
@@ -1009,14 +1078,15 @@ grape_status run_gradient(grape_problem *P, const double *ud, double *Fd, double
             else { r.bound_store = S.Y; r.bound_step = P->n_rk; }
             if ((st = launch_prop(P, r, s)) != GRAPE_OK) return st;
         }
-        if (P->penalty && (st = pen_rows(P, S.Y, bstride, j1 - j0, j0, s)) != GRAPE_OK) return st;
+        if (P->penalty && (st = pen_rows(P, S.Y, bstride, j1 - j0, j0, s, exact ? 1 : 0)) != GRAPE_OK)
+            return st;
         // adjoint sweep in chunks (last slices first); the trace of each
         // finished chunk runs on s2, overlapping the next chunk
         const int nch = adjoint_chunks(P, j0, j1);
         for (int ci = nch - 1; ci >= 0; --ci) {
             const long long cA = j0 + (j1 - j0) * ci / nch;
             const long long cB = j0 + (j1 - j0) * (ci + 1) / nch;
-            const size_t kofs = exact ? (size_t)(cA - j0) * P->n_rk * 4 * mat : (size_t)(cA - j0) * mat;
+            const size_t kofs = exact ? (size_t)(cA - j0) * P->n_rk * 4 * pst : (size_t)(cA - j0) * mat;
             PropArgs b = base_args(P, 1, ud);
             b.sub_begin = cA * P->n_rk;
             b.sub_end = cB * P->n_rk;
@@ -1046,7 +1116,7 @@ grape_status run_gradient(grape_problem *P, const double *ud, double *Fd, double
                 t.npairs = P->ns;
                 t.weight = dt;
             }
-            if (!S.part) t.nsplit = 1;
+            if (!S.part && !t.packed) t.nsplit = 1;
             t.part = S.part ? S.part + (size_t)cA * t.nsplit * P->R : nullptr;
             if ((st = timed(P, PH_TRACE, ts, [&] { return k_trace(P, t, ts); })) != GRAPE_OK)
                 return st;
@@ -1317,7 +1387,7 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
         tr.st_vR = b;
     }
     P->trace = tr;
-    P->trace.nsplit = trace_splits(P);
+    trace_layout(P, &P->trace);
     P->d_x = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
     P->d_mu = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
     P->d_out = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
@@ -1745,10 +1815,7 @@ grape_status grape_gradient_static(grape_problem_t P, const double *u, double *F
     const bool exact = (P->mode == GRAPE_GRAD_EXACT);
     const int nsplit = std::max(1, P->trace.nsplit);
     const size_t mat = align256(P->d2 * P->ns * sizeof(double2));
-    auto per_seg = [&](long long sg) {
-        return align256(exact ? (size_t)sg * P->n_rk * 4 * P->d2 * P->ns * sizeof(double2)
-                              : (size_t)(sg + 1) * P->d2 * P->ns * sizeof(double2));
-    };
+    auto per_seg = [&](long long sg) { return align256(stage_bytes(P, sg)); };
     auto part_bytes = [&](long long sg) {
         return nsplit > 1 ? align256((size_t)sg * nsplit * std::max(P->R, 1) * sizeof(double)) : 0;
     };

@@ -21,6 +21,8 @@
 // A(u) = A0 + sum_k u_k Ak is rebuilt in shared memory once per slice.
 struct PropTables {
     int nb, nt;
+    int nbr;                    // the first nbr bands are real for every control value
+                                // (real multiply-adds); the offset-0 band is never among them
     int off[GRAPE_MAXB];        // band offsets o_b: A_b[i] = A[i][i + o_b]
     int off_row[GRAPE_MAXB];    // o_b * d (flat shift of row i -> i + o_b)
     int jflat[GRAPE_MAXT];      // oL_t * d + oR_t
@@ -58,7 +60,8 @@ struct PropArgs {
     // entry: double2 for FP64, float4 hi/lo pairs for double-float)
     const void *x_in;                   // [n_states][d*d]
     void *x_out;                        // [n_states][d*d] (may alias x_in)
-    void *stage_store;                  // [(n - sub_begin)][4][n_states][d*d] or null
+    void *stage_store;                  // [(n - sub_begin)][4][n_states][d(d+1)/2] or null: every
+                                        // stage input, packed upper triangle (row-major order)
     void *bound_store;                  // [slot][n_states][d*d] or null
     long long bound_step;               // substeps between bound stores
     // Hermitian kernel (upper triangle only): the cluster's ownership and
@@ -70,6 +73,10 @@ struct PropArgs {
     int maxwin;                         // largest window (entries) of the cluster
     int rt_rows;                        // rows of the largest push table
     int fold;                           // Hermitian kernel: own-entry coefficients folded (D table)
+    int bulk;                           // Hermitian kernel: stage inputs reach the stage storage
+                                        // through a staging copy and bulk asynchronous copies
+    int jcache;                         // Hermitian kernel, real jump tables: coefficients of the
+                                        // jump terms cached per owned entry
     const double *src;                  // adjoint source on the diagonal per row (App. B), or null
     // grid kernel (state windows in global memory, one grid barrier per stage)
     void *gbuf;                         // [2][n_states][d*d] stage-input buffers
@@ -92,6 +99,13 @@ struct PropArgs {
 //   G[j][k] = weight * sum_q (-2) Im sum_b sum_m Hk_b[m] P_{o_b}[m],
 //   P_o[m]  = sum_l K_q[m + o][l] conj(Y_q[m][l]),
 // i.e. -2 Im Tr(K Y H_k) = Re Tr(K (-i)[H_k, Y]) for Hermitian K and Y.
+// Packed storage (exact gradient): K_q and Y_q hold upper triangles
+// (d(d+1)/2 entries, row-major), and the same sum runs over the upper
+// entries (i, j), j >= i, as
+//   Tr(K Y H) = sum_{i<=j} sum_o [ H_o[i] conj(Y_ij) K_{i+o,j}
+//                                  + (i < j) H_o[j] Y_ij conj(K_{i,j+o}) ]
+// (H_o[m] = H[m][m+o]; an entry below the diagonal is the conjugate of its
+// mirror).  Each row's pairs are split by state and by chunks of entries.
 struct TraceArgs {
     int d, R;
     int ncb, ndo;
@@ -109,6 +123,10 @@ struct TraceArgs {
     // part[row][split][R]; trace_finish_kernel adds the splits in order
     int nsplit;
     double *part;
+    // packed storage: nsplit = n_states * nchunk CTAs per row, CTA (state s,
+    // chunk c) sums the entries [c * 256 * epc, (c + 1) * 256 * epc) of state
+    // s over its pairs q = (substep * 4 + stage) * n_states + s
+    int packed, nchunk, epc, n_states;
     // controls on dissipation rates: the sandwich part of Re Tr(kb D[c] y),
     // sum over m, l of conj(K[m][l]) vL[m] conj(vR[l]) Y[m+oL][l+oR] per term
     int nst;
@@ -138,7 +156,7 @@ struct TraceArgs {
                                                cudaStream_t stream);                            \
     cudaError_t grape_launch_penalty_rows_##SUFFIX(const void *x, long long row_stride, int rows, \
                                                    int n_states, int d, const double *diag,     \
-                                                   double *out, cudaStream_t stream);           \
+                                                   double *out, int packed, cudaStream_t stream); \
     cudaError_t grape_launch_penalty_finish_##SUFFIX(const double *pen, long long count,        \
                                                      double scale, double *F, cudaStream_t stream);
 

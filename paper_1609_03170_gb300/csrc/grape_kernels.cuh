@@ -42,6 +42,7 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release;\n\t"
                  "barrier.cluster.wait.acquire;" ::: "memory");
 }
+
 // The running cost's source (App. B, photon-number penalty): added to the
 // adjoint's diagonal when a backward sweep crosses a slice boundary, i.e.
 // after the slice's first substep (n a multiple of n_RK).
@@ -243,9 +244,10 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_kernel(const PropA
         for (int s = 0; s < 4; ++s) {
             const S *cur = (s & 1) ? buf1 : buf0;
             S *nxt = (s & 1) ? buf0 : buf1;
-            S *st = nullptr;
+            S *st = nullptr;                     // packed stage storage of this state
             if (stage_store)
-                st = stage_store + ((size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states) * d2 + soff;
+                st = stage_store + ((size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states + state) *
+                                       (size_t)(d * (d + 1) / 2);
             const R as_ = ca[s];
 #pragma unroll 1
             for (int e = e0 + threadIdx.x; e < e1; e += nth) {
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_kernel(const PropA
                 const int2 ij = rc[li];
                 const V w = lindblad_at<Num, REALJ>(cur, le, ij.x, ij.y, d, p.tab, A, vL, vR,
                                                     p.u + (size_t)jcur * p.R);
-                if (st) st[e] = cur[le];
+                if (st && ij.y >= ij.x) st[ij.x * d - ij.x * (ij.x - 1) / 2 + (ij.y - ij.x)] = cur[le];
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
                 V z;
@@ -361,6 +363,30 @@ __device__ __forceinline__ typename Num::val diag_coef(int i, int j, int d, cons
     return c;
 }
 
+// The Hamiltonian bands: the first t.nbr are real for every control value
+// (real multiply-adds: the same bits as the complex ones with a zero
+// imaginary part, half the work), the offset-0 band is last and excluded
+// (it is part of the own-entry coefficient).  x1(b), x2(b): the neighbours
+// (i + o_b, j) and (i, j + o_b).
+template <class Num, class X1, class X2>
+__device__ __forceinline__ void band_terms(typename Num::acc &w, const PropTables &t,
+                                           const typename Num::store_t *A, int i, int j, int d,
+                                           X1 &&x1, X2 &&x2) {
+    const int nbo = (t.b0 >= 0) ? t.nb - 1 : t.nb;
+#pragma unroll 1
+    for (int b = 0; b < t.nbr; ++b) {
+        Num::mac_real(w, Num::load_re(A[b * d + i]), x1(b));
+        Num::mac_real(w, Num::neg_real(Num::load_re(A[b * d + j])), x2(b));
+    }
+#pragma unroll 2
+    for (int b = t.nbr; b < nbo; ++b) {
+        Num::mac(w, Num::load(A[b * d + i]), x1(b));
+        Num::mac_conj_neg(w, Num::load(A[b * d + j]), x2(b));
+    }
+}
+
+// jc: null, or the entry's cached coefficients of the jump terms with an
+// offset (real tables only), jc[q' * jstride] for the q'-th such term
 template <class Num, bool REALJ>
 __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::store_t *cur,
                                                            const short *nb_ad, int i, int j, int d,
@@ -369,21 +395,28 @@ __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::s
                                                            const typename Num::store_t *vL,
                                                            const typename Num::store_t *vR,
                                                            const typename Num::val dij,
-                                                           const double *uj) {
+                                                           const double *uj,
+                                                           const typename Num::real_t *jc, int jstride) {
     // neighbours outside the matrix point at the window's zero slot, so
     // every term is accumulated without a branch (adding 0 changes no bit).
     // The terms on the entry itself - the offset-0 band and the jump terms
     // with both offsets 0 - come as one coefficient D_ij (diag_coef).
     typename Num::acc w = Num::acc_zero();
-    // the offset-0 band, when there is one, is the last (the host orders it so)
-    const int nbo = (t.b0 >= 0) ? t.nb - 1 : t.nb;
-#pragma unroll 2
-    for (int b = 0; b < nbo; ++b) {
-        Num::mac(w, Num::load(A[b * d + i]), Num::load(cur[nb_ad[2 * b]]));
-        Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(cur[nb_ad[2 * b + 1]]));
-    }
+    band_terms<Num>(w, t, A, i, j, d,
+                    [&](int b) { return Num::load(cur[nb_ad[2 * b]]); },
+                    [&](int b) { return Num::load(cur[nb_ad[2 * b + 1]]); });
     w = Num::acc_minus_i(w);
     Num::mac(w, dij, Num::load(cur[nb_ad[2 * t.nb + t.nt]]));
+    if (REALJ && jc) {
+        int qq = 0;
+#pragma unroll 1
+        for (int q = 0; q < t.nt; ++q) {
+            if ((t.jdiag >> q) & 1) continue;
+            Num::mac_real(w, jc[qq * jstride], Num::load(cur[nb_ad[2 * t.nb + q]]));
+            ++qq;
+        }
+        return Num::raw(w);
+    }
     auto jumps = [&](auto rate) {
         constexpr bool RT = decltype(rate)::value;
 #pragma unroll 1
@@ -418,10 +451,39 @@ __device__ __forceinline__ void hpush_pre(const uint32_t *rowtab, int rstride, i
     for (int t = 1; t <= n; ++t) st_cluster_addr(e[t] + boff + (uint32_t)c * (uint32_t)sizeof(S), v);
 }
 
-// Shared memory: buf0, buf1 [maxwin + 1] (the last entry of each stays zero);
-// xs, as [cu]; D [cu] when p.fold; bands [2][nb][d];
-// vL, vR [nt][d]; rc [cu] (int2); 12 RK coefficients; htab copy (ints);
-// row push table [rt_rows][ncl + 1] (u32); neighbour addresses [cu][ns + 1] (i16).
+// Bulk asynchronous copies shared::cta -> global (the copy engine reads the
+// source while the CTA computes; the cluster barrier's release does not wait
+// for them).  Addresses 16-byte aligned, sizes multiples of 16 bytes.
+__device__ __forceinline__ void bulk_store(void *gdst, uint32_t ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the sources of every committed copy have been read
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed copy has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// orders this thread's shared-memory writes before later async-proxy reads
+__device__ __forceinline__ void fence_proxy_async_cta() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Shared memory: buf0, buf1 [maxwin + 1] (the last entry of each stays
+// zero); xs, as [cu]; D [cu] when p.fold; stg [2][cu] when p.bulk;
+// bands [2][nb][d]; vL, vR [nt][d]; rc [cu] (int2); 12 RK coefficients; jump
+// coefficients [njt][cu] (real_t) when p.jcache; htab copy (ints); row push
+// table [rt_rows][ncl + 1] (u32); neighbour addresses [cu][ns + 1] (i16).
+//
+// Stage inputs go to the stage storage as packed upper triangles: a CTA's
+// owned entries [u0, u1) are one contiguous range of it.  With p.bulk every
+// thread also writes the next stage input of its entries, in that order,
+// into one of two staging rows; after the stage's barrier one thread copies
+// the row to HBM with one bulk asynchronous copy and makes sure, before the
+// next barrier, that the copy has read it (the row is rewritten one stage
+// later).  The barrier's release then orders only the distributed-shared-
+// memory pushes.  Without p.bulk (tiles where the staging rows do not fit)
+// each thread stores its entries' stage inputs itself, before computing them.
 template <class Num, bool REALJ>
 __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const PropArgs p) {
     using S = typename Num::store_t;
@@ -429,6 +491,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     using R = typename Num::real_t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int d = p.d, d2 = d * d;
+    const int NU = d * (d + 1) / 2;
     const int nbd = p.tab.nb * d;
     const int wst = p.maxwin + 1;                // window stride; slot maxwin is the zero slot
     S *buf0 = reinterpret_cast<S *>(smem_raw);
@@ -436,14 +499,18 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     S *xs = buf1 + wst;
     S *as = xs + p.cu;
     S *Dt = as + p.cu;                           // [cu] own-entry coefficients when p.fold
-    S *bands = Dt + (p.fold ? p.cu : 0);
+    S *stg = Dt + (p.fold ? p.cu : 0);           // [2][cu] staging rows when p.bulk
+    S *bands = stg + (p.bulk ? 2 * p.cu : 0);
     S *vL = bands + 2 * nbd;
     S *vR = vL + p.tab.nt * d;
     int2 *rc = reinterpret_cast<int2 *>(vR + p.tab.nt * d);
     R *cg = reinterpret_cast<R *>(rc + p.cu);
     R *ca = cg + 4;
     R *cb = cg + 8;
-    int *tab = reinterpret_cast<int *>(cg + 12);
+    const int njt = p.tab.nt - __popc(p.tab.jdiag);   // jump terms with an offset
+    const bool jcache = REALJ && p.jcache;
+    R *jc = cg + 12;                             // [njt][cu] when jcache
+    int *tab = reinterpret_cast<int *>(jc + (jcache ? njt * p.cu : 0));
     const int rstride = p.ncl + 1;
     uint32_t *rowtab = reinterpret_cast<uint32_t *>(tab + p.htab_len);
     short *nbad = reinterpret_cast<short *>(rowtab + p.rt_rows * rstride);
@@ -458,6 +525,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     const size_t soff = (size_t)state * d2;
     const int nth = blockDim.x;
     const int hb = p.hb;
+    const bool bulk = p.bulk && stage_store;
 
     for (int i = threadIdx.x; i < p.htab_len; i += nth) tab[i] = __ldg(&p.htab[i]);
     const V vzero = Num::zero();
@@ -482,7 +550,8 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     const int *ofs = tab + tab[GRAPE_HTAB_LISTS(p.ncl) + rank];
     const int *kfl = tab + tab[GRAPE_HTAB_LISTS(p.ncl) + p.ncl];   // kfirst[d], klast[d]
     // (row, column) of the owned upper entries (row-major offset of row i is
-    // i d - i (i - 1) / 2) and their neighbours' window addresses
+    // i d - i (i - 1) / 2), their neighbours' window addresses and, for real
+    // jump tables, their jump coefficients (fixed for the whole sweep)
     for (int u = u0 + threadIdx.x; u < u1; u += nth) {
         const double b2 = 2.0 * d + 1.0;
         int i = (int)floor(0.5 * (b2 - sqrt(b2 * b2 - 8.0 * (double)u)));
@@ -504,6 +573,14 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
             const int r = i + p.tab.joL[q], c = j + p.tab.joR[q];
             na[2 * p.tab.nb + q] =
                 (r >= 0 && r < d && c >= 0 && c < d) ? (short)(ofs[r - wr0] + (c - cs_of(r, hb))) : zs;
+        }
+        if (jcache) {
+            int qq = 0;
+            for (int q = 0; q < p.tab.nt; ++q) {
+                if ((p.tab.jdiag >> q) & 1) continue;
+                jc[qq * p.cu + (u - u0)] = jump_real<Num, false>(p.tab, q, i, j, d, vL, vR, nullptr);
+                ++qq;
+            }
         }
     }
     // push targets of the rows this CTA writes: its own rows and, for the
@@ -543,14 +620,18 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
         const V x = Num::load(x_in[soff + (size_t)ij.x * d + ij.y]);
         xs[u - u0] = Num::store(x);
         const V z = Num::scale(cg[0], x);
+        if (bulk) stg[u - u0] = Num::store(z);
         hpush_pre(rowtab, rstride, ij.x - rfirst, ij.y, 0u, Num::store(z));
         if (ij.y > ij.x && ij.y - ij.x <= hb)
             hpush_pre(rowtab, rstride, ij.y - rfirst, ij.x, 0u, conj_store<Num>(z));
     }
+    if (bulk) fence_proxy_async_cta();
     cluster_sync_all();
 
     const bool unit_g = (p.g[1] == 1.0 && p.g[2] == 1.0 && p.g[3] == 1.0);   // forward RK4
+    const bool copier = bulk && threadIdx.x == 0 && u1 > u0;
     int tb = 0;
+    int gp = 0;                                  // staging row holding the current stage input
     bool dfresh = true;                          // D table to (re)build for this slice
     for (long long it = 0; it < nsub; ++it) {
         const long long n = p.reverse ? p.sub_end - 1 - it : p.sub_begin + it;
@@ -567,19 +648,24 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
         for (int s = 0; s < 4; ++s) {
             const S *cur = (s & 1) ? buf1 : buf0;
             const uint32_t boff = (s & 1) ? 0u : boff1;          // next buffer
-            S *st = nullptr;
+            S *st = nullptr;                     // packed stage storage of this state
             if (stage_store)
-                st = stage_store + ((size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states) * d2 + soff;
+                st = stage_store + ((size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states + state) * NU;
+            if (copier) {
+                bulk_store(st + u0, smem_u32(stg + gp * p.cu), (uint32_t)((u1 - u0) * (int)sizeof(S)));
+                bulk_commit();
+            }
+            S *stn = stg + (gp ^ 1) * p.cu;      // staging row of the next stage input
             const R as_ = ca[s];
 #pragma unroll 1
             for (int u = u0 + threadIdx.x; u < u1; u += nth) {
                 const int li = u - u0;
                 const int2 ij = rc[li];
                 const short *na = nbad + (size_t)li * nstride;
-                // the stage input itself, stored first so that the global store
-                // completes while the entry is computed (the barrier's release
-                // at the end of the stage waits for it)
-                if (st) store_herm<Num>(st, d, ij.x, ij.y, cur[na[ns]]);
+                // without the bulk copies: the stage input itself, stored first so
+                // that the global store completes while the entry is computed (the
+                // barrier's release at the end of the stage waits for it)
+                if (st && !bulk) st[u] = cur[na[ns]];
                 // own-entry coefficient: cached per slice (the entry is thread-private,
                 // so no barrier is needed) or recomputed when there is no room
                 V dij;
@@ -589,7 +675,8 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                 } else {
                     dij = diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR, uj);
                 }
-                const V w = lindblad_h_at<Num, REALJ>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij, uj);
+                const V w = lindblad_h_at<Num, REALJ>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij, uj,
+                                                      jcache ? jc + li : nullptr, p.cu);
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
                 V z;
@@ -601,6 +688,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                     xs[li] = Num::store(nx);
                     z = Num::scale(cg[0], nx);
                 }
+                if (bulk) stn[li] = Num::store(z);
                 hpush_pre(rowtab, rstride, ij.x - rfirst, ij.y, boff, Num::store(z));
                 if (ij.y > ij.x && ij.y - ij.x <= hb)
                     hpush_pre(rowtab, rstride, ij.y - rfirst, ij.x, boff, conj_store<Num>(z));
@@ -614,14 +702,18 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                     flip = true;
                 }
             }
+            if (bulk) fence_proxy_async_cta();   // the staging row before the next copy reads it
+            if (copier) bulk_wait_read();        // this stage's row is rewritten in the next stage
             // a one-CTA cluster needs only the CTA barrier (it orders the CTA's own
             // shared-memory stores, whatever window address they used)
             if (p.ncl == 1) __syncthreads();
             else cluster_sync_all();
+            gp ^= 1;
         }
         if (flip) tb ^= 1;
         dfresh = flip;
     }
+    if (copier) bulk_wait_all();
     const long long tend = p.reverse ? p.sub_begin : p.sub_end;
     if (bound_store && ((tend - p.sub_begin) % p.bound_step) == 0) {
         S *dst = bound_store + ((size_t)((tend - p.sub_begin) / p.bound_step) * p.n_states) * d2 + soff;
@@ -688,16 +780,19 @@ __device__ __forceinline__ typename Num::val lindblad_g_at(const typename Num::s
                                                            const typename Num::store_t *vL,
                                                            const typename Num::store_t *vR,
                                                            const double *uj) {
-    // same terms in the same order as lindblad_h_at (identical bits)
+    // same terms in the same order as lindblad_h_at (identical bits; a
+    // neighbour outside the matrix contributes an exact zero there)
     typename Num::acc w = Num::acc_zero();
-#pragma unroll 1
-    for (int b = 0; b < t.nb; ++b) {
-        if (b == t.b0) continue;
-        const int o = t.off[b], r = i + o, c = j + o;
-        if (r >= 0 && r < d) Num::mac(w, Num::load(A[b * d + i]), Num::load(__ldcg(&cur[(size_t)r * d + j])));
-        if (c >= 0 && c < d)
-            Num::mac_conj_neg(w, Num::load(A[b * d + j]), Num::load(__ldcg(&cur[(size_t)i * d + c])));
-    }
+    const typename Num::val vz = Num::zero();
+    band_terms<Num>(w, t, A, i, j, d,
+                    [&](int b) {
+                        const int r = i + t.off[b];
+                        return (r >= 0 && r < d) ? Num::load(__ldcg(&cur[(size_t)r * d + j])) : vz;
+                    },
+                    [&](int b) {
+                        const int c = j + t.off[b];
+                        return (c >= 0 && c < d) ? Num::load(__ldcg(&cur[(size_t)i * d + c])) : vz;
+                    });
     w = Num::acc_minus_i(w);
     Num::mac(w, diag_coef<Num, REALJ>(i, j, d, t, A, vL, vR, uj), Num::load(__ldcg(&cur[(size_t)i * d + j])));
     auto jumps = [&](auto rate) {
@@ -776,7 +871,7 @@ __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const Pro
         while (i > 0 && (long long)i * d - (long long)i * (i - 1) / 2 > u) --i;
         while (i + 1 < d && (long long)(i + 1) * d - (long long)(i + 1) * i / 2 <= u) ++i;
         const int j = i + (int)(u - ((long long)i * d - (long long)i * (i - 1) / 2));
-        ent[e - e0] = make_int4(i, j, st, 0);
+        ent[e - e0] = make_int4(i, j, st, (int)u);
         const V x = Num::load(x_in[(size_t)st * d2 + (size_t)i * d + j]);
         xs[e - e0] = Num::store(x);
         store_herm<Num>(gb0 + (size_t)st * d2, d, i, j, Num::store(Num::scale(cg[0], x)));
@@ -801,9 +896,9 @@ __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const Pro
         for (int s = 0; s < 4; ++s) {
             const S *cur = (s & 1) ? gb1 : gb0;
             S *nxt = (s & 1) ? gb0 : gb1;
-            S *stg = nullptr;
+            S *stg = nullptr;                    // packed stage storage (all states)
             if (stage_store)
-                stg = stage_store + (size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states * d2;
+                stg = stage_store + (size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states * NU;
             const R as_ = ca[s];
 #pragma unroll 1
             for (long long e = e0 + threadIdx.x; e < e1; e += nth) {
@@ -812,7 +907,7 @@ __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const Pro
                 const S *cs = cur + (size_t)q.z * d2;
                 const V w = lindblad_g_at<Num, REALJ>(cs, q.x, q.y, d, p.tab, A, vL, vR,
                                                       p.u + (size_t)jcur * p.R);
-                if (stg) store_herm<Num>(stg + (size_t)q.z * d2, d, q.x, q.y, __ldcg(&cs[(size_t)q.x * d + q.y]));
+                if (stg) stg[(size_t)q.z * NU + q.w] = __ldcg(&cs[(size_t)q.x * d + q.y]);
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
                 V z;
@@ -964,6 +1059,153 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
     }
 }
 
+// Trace products on packed (upper-triangle) storage, exact gradient.  CTA
+// (row, state s, chunk c) takes the upper entries u of its chunk, one per
+// thread and pass, and for each distinct control offset o sums over the
+// state's pairs (K, Y) of the row, in pair order,
+//   S_o(i, j) = sum conj(Y_ij) K_{i+o, j},  T_o(i, j) = sum Y_ij conj(K_{i, j+o})  (i < j)
+// (a neighbour below the diagonal is read as the conjugate of its mirror),
+// then adds H_o[i] S_o + H_o[j] T_o per control band of that offset:
+// Sum over the entries gives Tr(K Y H_k) per pair (see TraceArgs).  The
+// rate-control sandwich terms come the same way from
+//   conj(K_ij) vL[i] conj(vR[j]) Y_{i+oL, j+oR} + (i < j) K_ij vL[j] conj(vR[i]) Y_{j+oL, i+oR}.
+// Lane sums reduce by warp shuffles and a fixed-order tree; the row's
+// n_states * nchunk partials are added in order by trace_finish_kernel, so
+// no bit depends on the launch grouping or the propagation tile.
+template <class Num>
+__device__ __forceinline__ typename Num::val conj_if(typename Num::val v, bool c) {
+    if (c) v.im = Num::neg_real(v.im);
+    return v;
+}
+__device__ __forceinline__ int packed_index(int r, int c, int d) { return r * d - r * (r - 1) / 2 + (c - r); }
+
+template <class Num>
+__global__ void __launch_bounds__(256) trace_packed_kernel(const TraceArgs p) {
+    using S = typename Num::store_t;
+    using V = typename Num::val;
+    const int d = p.d;
+    const int NU = d * (d + 1) / 2;
+    const int nsplit = p.nsplit;
+    const int row = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
+    const int state = split / p.nchunk, chunk = split % p.nchunk;
+    const long long pps = p.npairs / p.n_states;    // pairs of this state in the row
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const S *Kb = static_cast<const S *>(p.K);
+    const S *Yb = static_cast<const S *>(p.Y);
+    typename Num::acc Z[GRAPE_MAXCB];
+#pragma unroll
+    for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = Num::acc_zero();
+    typename Num::acc Zs[GRAPE_MAXST];
+#pragma unroll
+    for (int t = 0; t < GRAPE_MAXST; ++t) Zs[t] = Num::acc_zero();
+    const size_t row_base = (size_t)row * p.npairs;
+
+#pragma unroll 1
+    for (int e = 0; e < p.epc; ++e) {
+        const int u = (chunk * p.epc + e) * 256 + threadIdx.x;
+        if (u >= NU) break;
+        const double b2 = 2.0 * d + 1.0;
+        int i = (int)floor(0.5 * (b2 - sqrt(b2 * b2 - 8.0 * (double)u)));
+        i = max(0, min(d - 1, i));
+        while (i > 0 && packed_index(i, i, d) > u) --i;
+        while (i + 1 < d && packed_index(i + 1, i + 1, d) <= u) ++i;
+        const int j = i + (u - packed_index(i, i, d));
+#pragma unroll 1
+        for (int oi = 0; oi < p.ndo; ++oi) {
+            const int o = p.do_off[oi];
+            const int r1 = i + o, c2 = j + o;
+            const bool v1 = r1 >= 0 && r1 < d;
+            const bool v2 = i < j && c2 >= 0 && c2 < d;
+            const bool cj1 = v1 && r1 > j, cj2 = v2 && c2 < i;
+            const int x1 = !v1 ? 0 : (cj1 ? packed_index(j, r1, d) : packed_index(r1, j, d));
+            const int x2 = !v2 ? 0 : (cj2 ? packed_index(c2, i, d) : packed_index(i, c2, d));
+            typename Num::acc Sa = Num::acc_zero(), Ta = Num::acc_zero();
+#pragma unroll 1
+            for (long long qs = 0; qs < pps; ++qs) {
+                const size_t moff = (row_base + (size_t)qs * p.n_states + state) * NU;
+                const V y = Num::load(Yb[moff + u]);
+                if (v1) Num::mac_conjb(Sa, conj_if<Num>(Num::load(Kb[moff + x1]), cj1), y);
+                if (v2) Num::mac_conjb(Ta, y, conj_if<Num>(Num::load(Kb[moff + x2]), cj2));
+            }
+            const V Sv = Num::done(Sa), Tv = Num::done(Ta);
+#pragma unroll
+            for (int c = 0; c < GRAPE_MAXCB; ++c) {
+                if (c < p.ncb && p.cb_do[c] == oi) {
+                    Num::mac(Z[c], Num::from_double2(__ldg(&p.cb_val[c * d + i])), Sv);
+                    if (i < j) Num::mac(Z[c], Num::from_double2(__ldg(&p.cb_val[c * d + j])), Tv);
+                }
+            }
+        }
+        // rate controls: the sandwich part of Re Tr(kb gamma D[c] y)
+#pragma unroll 1
+        for (int t = 0; t < p.nst; ++t) {
+            const int oL = p.st_oL[t], oR = p.st_oR[t];
+            const int ra = i + oL, ca_ = j + oR;            // Y_{i+oL, j+oR}
+            const int rb = j + oL, cb_ = i + oR;            // Y_{j+oL, i+oR} (i < j)
+            const bool va = ra >= 0 && ra < d && ca_ >= 0 && ca_ < d;
+            const bool vb = i < j && rb >= 0 && rb < d && cb_ >= 0 && cb_ < d;
+            const bool cja = va && ra > ca_, cjb = vb && rb > cb_;
+            const int xa = !va ? 0 : (cja ? packed_index(ca_, ra, d) : packed_index(ra, ca_, d));
+            const int xb = !vb ? 0 : (cjb ? packed_index(cb_, rb, d) : packed_index(rb, cb_, d));
+            typename Num::acc Pa = Num::acc_zero(), Pb = Num::acc_zero();
+#pragma unroll 1
+            for (long long qs = 0; qs < pps; ++qs) {
+                const size_t moff = (row_base + (size_t)qs * p.n_states + state) * NU;
+                const V k = Num::load(Kb[moff + u]);
+                if (va) Num::mac_conjb(Pa, conj_if<Num>(Num::load(Yb[moff + xa]), cja), k);   // Y conj(K)
+                if (vb) Num::mac(Pb, k, conj_if<Num>(Num::load(Yb[moff + xb]), cjb));        // K Y
+            }
+            typename Num::acc cL = Num::acc_zero(), cR = Num::acc_zero();
+            Num::mac_conjb(cL, Num::from_double2(__ldg(&p.st_vL[t * d + i])),
+                           Num::from_double2(__ldg(&p.st_vR[t * d + j])));               // vL[i] conj(vR[j])
+            Num::mac_conjb(cR, Num::from_double2(__ldg(&p.st_vL[t * d + j])),
+                           Num::from_double2(__ldg(&p.st_vR[t * d + i])));               // vL[j] conj(vR[i])
+            Num::mac(Zs[t], Num::done(cL), Num::done(Pa));
+            if (vb) Num::mac(Zs[t], Num::done(cR), Num::done(Pb));
+        }
+    }
+    // deterministic reduction: warp shuffles, then warps in index order (FP64)
+    __shared__ double red[GRAPE_MAXCB][32];
+    __shared__ double reds[GRAPE_MAXST][32];
+#pragma unroll
+    for (int c = 0; c < GRAPE_MAXCB; ++c) {
+        double v = Num::to_double2(Num::done(Z[c])).y;
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
+        if (lane == 0) red[c][warp] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < GRAPE_MAXST; ++t) {
+        double v = Num::to_double2(Num::done(Zs[t])).x;
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
+        if (lane == 0) reds[t][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < GRAPE_MAXR) {
+        const int k = threadIdx.x;
+        if (k < p.R) {
+            double s = 0.0;
+            for (int c = 0; c < p.ncb; ++c) {
+                if (p.cb_k[c] != k) continue;
+                double t = 0.0;
+                for (int w = 0; w < nwarps; ++w) t += red[c][w];
+                s += t;
+            }
+            double sw = 0.0;
+            for (int t = 0; t < p.nst; ++t) {
+                if (p.st_k[t] != k) continue;
+                double a = 0.0;
+                for (int w = 0; w < nwarps; ++w) a += reds[t][w];
+                sw += a;
+            }
+            const double v = p.weight * (-2.0 * s + sw);
+            if (nsplit == 1) p.G[(size_t)row * p.R + k] = v;
+            else p.part[((size_t)row * nsplit + split) * p.R + k] = v;
+        }
+    }
+}
+
 // G[row][k] = sum over the row's splits, in split order (deterministic)
 static __global__ void __launch_bounds__(256) trace_finish_kernel(const TraceArgs p) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -988,19 +1230,22 @@ __global__ void __launch_bounds__(256) add_diag_kernel(void *x_v, const double *
 
 // out[row] = sum over states and i of diag[i] Re x_row[s][i][i], states then
 // rows in index order (FP64); x_row = x + row * row_stride entries
+// (packed: the states are upper triangles of d(d+1)/2 entries)
 template <class Num>
 __global__ void __launch_bounds__(128) penalty_rows_kernel(const void *x_v, long long row_stride, int rows,
                                                            int n_states, int d, const double *diag,
-                                                           double *out) {
+                                                           double *out, int packed) {
     using S = typename Num::store_t;
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= rows) return;
     const S *x = static_cast<const S *>(x_v) + (size_t)row * row_stride;
-    const size_t d2 = (size_t)d * d;
+    const size_t m = packed ? (size_t)d * (d + 1) / 2 : (size_t)d * d;
     double acc = 0.0;
     for (int st = 0; st < n_states; ++st)
-        for (int i = 0; i < d; ++i)
-            acc = fma(diag[i], Num::to_double2(Num::load(x[st * d2 + (size_t)i * d + i])).x, acc);
+        for (int i = 0; i < d; ++i) {
+            const size_t ii = packed ? (size_t)packed_index(i, i, d) : (size_t)i * d + i;
+            acc = fma(diag[i], Num::to_double2(Num::load(x[st * m + ii])).x, acc);
+        }
     out[row] = acc;
 }
 
@@ -1169,6 +1414,10 @@ cudaError_t max_clusters(int threads, int variant, size_t smem, int ncl, int n_b
 template <class Num>
 cudaError_t launch_trace(const TraceArgs &p, cudaStream_t s) {
     if (p.n_rows <= 0) return cudaSuccess;
+    if (p.packed) {
+        trace_packed_kernel<Num><<<p.n_rows * max(1, p.nsplit), 256, 0, s>>>(p);
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)(p.ncb + 2 * p.nst) * p.d * sizeof(typename Num::store_t);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(trace_kernel<Num>,
@@ -1208,9 +1457,9 @@ cudaError_t launch_add_diag(void *x, const double *src, int d, int ns, cudaStrea
 }
 template <class Num>
 cudaError_t launch_penalty_rows(const void *x, long long stride, int rows, int ns, int d,
-                                const double *diag, double *out, cudaStream_t s) {
+                                const double *diag, double *out, int packed, cudaStream_t s) {
     if (rows <= 0) return cudaSuccess;
-    penalty_rows_kernel<Num><<<(rows + 127) / 128, 128, 0, s>>>(x, stride, rows, ns, d, diag, out);
+    penalty_rows_kernel<Num><<<(rows + 127) / 128, 128, 0, s>>>(x, stride, rows, ns, d, diag, out, packed);
     return cudaGetLastError();
 }
 static cudaError_t launch_penalty_finish(const double *pen, long long count, double scale, double *F,
@@ -1261,8 +1510,9 @@ static cudaError_t launch_penalty_finish(const double *pen, long long count, dou
     }                                                                                           \
     cudaError_t grape_launch_penalty_rows_##SUFFIX(const void *x, long long row_stride, int rows, \
                                                    int n_states, int d, const double *diag,     \
-                                                   double *out, cudaStream_t s) {               \
-        return grape_k::launch_penalty_rows<NUM>(x, row_stride, rows, n_states, d, diag, out, s); \
+                                                   double *out, int packed, cudaStream_t s) {   \
+        return grape_k::launch_penalty_rows<NUM>(x, row_stride, rows, n_states, d, diag, out,   \
+                                                 packed, s);                                    \
     }                                                                                           \
     cudaError_t grape_launch_penalty_finish_##SUFFIX(const double *pen, long long count,        \
                                                      double scale, double *F, cudaStream_t s) {  \

@@ -107,6 +107,8 @@ struct NumD {
     struct acc { double re, im; };
 
     static __device__ __forceinline__ val load(const store_t &s) { return {s.x, s.y}; }
+    // the real part alone (8-byte load)
+    static __device__ __forceinline__ real_t load_re(const store_t &s) { return s.x; }
     static __device__ __forceinline__ store_t store(val v) { return make_double2(v.re, v.im); }
     static __device__ __forceinline__ val zero() { return {0.0, 0.0}; }
     static __device__ __forceinline__ acc acc_zero() { return {0.0, 0.0}; }
@@ -166,6 +168,11 @@ struct NumF {
     struct acc { lacc re, im; };
 
     static __device__ __forceinline__ val load(const store_t &s) { return {{s.x, s.y}, {s.z, s.w}}; }
+    // the real part alone (8-byte load of re.h, re.l)
+    static __device__ __forceinline__ real_t load_re(const store_t &s) {
+        const float2 v = *reinterpret_cast<const float2 *>(&s);
+        return {v.x, v.y};
+    }
     static __device__ __forceinline__ store_t store(val v) {
         return make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
     }
