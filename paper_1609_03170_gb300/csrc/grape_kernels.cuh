@@ -1206,6 +1206,108 @@ __global__ void __launch_bounds__(256) trace_packed_kernel(const TraceArgs p) {
     }
 }
 
+// The same sums for problems without rate-controlled dissipators and with
+// at most NDO distinct control offsets: the pairs are the outer loop (each
+// Y entry is loaded once per pair) and every offset's sums stay in
+// registers.  Each sum adds the same terms in the same order as
+// trace_packed_kernel, so both give the same bits.
+template <class Num, int NDO>
+__global__ void __launch_bounds__(256) trace_packed_fast_kernel(const TraceArgs p) {
+    using S = typename Num::store_t;
+    using V = typename Num::val;
+    const int d = p.d;
+    const int NU = d * (d + 1) / 2;
+    const int nsplit = p.nsplit;
+    const int row = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
+    const int state = split / p.nchunk, chunk = split % p.nchunk;
+    const long long pps = p.npairs / p.n_states;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const S *Kb = static_cast<const S *>(p.K);
+    const S *Yb = static_cast<const S *>(p.Y);
+    typename Num::acc Z[GRAPE_MAXCB];
+#pragma unroll
+    for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = Num::acc_zero();
+    const size_t row_base = (size_t)row * p.npairs;
+    const size_t pstride = (size_t)p.n_states * NU;      // between a state's consecutive pairs
+
+#pragma unroll 1
+    for (int e = 0; e < p.epc; ++e) {
+        const int u = (chunk * p.epc + e) * 256 + threadIdx.x;
+        if (u >= NU) break;
+        const double b2 = 2.0 * d + 1.0;
+        int i = (int)floor(0.5 * (b2 - sqrt(b2 * b2 - 8.0 * (double)u)));
+        i = max(0, min(d - 1, i));
+        while (i > 0 && packed_index(i, i, d) > u) --i;
+        while (i + 1 < d && packed_index(i + 1, i + 1, d) <= u) ++i;
+        const int j = i + (u - packed_index(i, i, d));
+        int x1[NDO], x2[NDO];
+        bool v1[NDO], v2[NDO], cj1[NDO], cj2[NDO];
+        typename Num::acc Sa[NDO], Ta[NDO];
+#pragma unroll
+        for (int oi = 0; oi < NDO; ++oi) {
+            const int o = oi < p.ndo ? p.do_off[oi] : 0;
+            const int r1 = i + o, c2 = j + o;
+            v1[oi] = oi < p.ndo && r1 >= 0 && r1 < d;
+            v2[oi] = oi < p.ndo && i < j && c2 >= 0 && c2 < d;
+            cj1[oi] = v1[oi] && r1 > j;
+            cj2[oi] = v2[oi] && c2 < i;
+            x1[oi] = !v1[oi] ? u : (cj1[oi] ? packed_index(j, r1, d) : packed_index(r1, j, d));
+            x2[oi] = !v2[oi] ? u : (cj2[oi] ? packed_index(c2, i, d) : packed_index(i, c2, d));
+            Sa[oi] = Num::acc_zero();
+            Ta[oi] = Num::acc_zero();
+        }
+        const S *Yp = Yb + (row_base + state) * NU;
+        const S *Kp = Kb + (row_base + state) * NU;
+#pragma unroll 2
+        for (long long qs = 0; qs < pps; ++qs) {
+            const size_t moff = (size_t)qs * pstride;
+            const V y = Num::load(Yp[moff + u]);
+#pragma unroll
+            for (int oi = 0; oi < NDO; ++oi) {
+                if (v1[oi]) Num::mac_conjb(Sa[oi], conj_if<Num>(Num::load(Kp[moff + x1[oi]]), cj1[oi]), y);
+                if (v2[oi]) Num::mac_conjb(Ta[oi], y, conj_if<Num>(Num::load(Kp[moff + x2[oi]]), cj2[oi]));
+            }
+        }
+#pragma unroll
+        for (int oi = 0; oi < NDO; ++oi) {
+            if (oi >= p.ndo) break;
+            const V Sv = Num::done(Sa[oi]), Tv = Num::done(Ta[oi]);
+#pragma unroll
+            for (int c = 0; c < GRAPE_MAXCB; ++c) {
+                if (c < p.ncb && p.cb_do[c] == oi) {
+                    Num::mac(Z[c], Num::from_double2(__ldg(&p.cb_val[c * d + i])), Sv);
+                    if (i < j) Num::mac(Z[c], Num::from_double2(__ldg(&p.cb_val[c * d + j])), Tv);
+                }
+            }
+        }
+    }
+    __shared__ double red[GRAPE_MAXCB][32];
+#pragma unroll
+    for (int c = 0; c < GRAPE_MAXCB; ++c) {
+        double v = Num::to_double2(Num::done(Z[c])).y;
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
+        if (lane == 0) red[c][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < GRAPE_MAXR) {
+        const int k = threadIdx.x;
+        if (k < p.R) {
+            double s = 0.0;
+            for (int c = 0; c < p.ncb; ++c) {
+                if (p.cb_k[c] != k) continue;
+                double t = 0.0;
+                for (int w = 0; w < nwarps; ++w) t += red[c][w];
+                s += t;
+            }
+            const double sw = 0.0;                      // no rate-controlled dissipators
+            const double v = p.weight * (-2.0 * s + sw);
+            if (nsplit == 1) p.G[(size_t)row * p.R + k] = v;
+            else p.part[((size_t)row * nsplit + split) * p.R + k] = v;
+        }
+    }
+}
+
 // G[row][k] = sum over the row's splits, in split order (deterministic)
 static __global__ void __launch_bounds__(256) trace_finish_kernel(const TraceArgs p) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1415,7 +1517,10 @@ template <class Num>
 cudaError_t launch_trace(const TraceArgs &p, cudaStream_t s) {
     if (p.n_rows <= 0) return cudaSuccess;
     if (p.packed) {
-        trace_packed_kernel<Num><<<p.n_rows * max(1, p.nsplit), 256, 0, s>>>(p);
+        const int grid = p.n_rows * max(1, p.nsplit);
+        if (p.nst == 0 && p.ndo <= 2) trace_packed_fast_kernel<Num, 2><<<grid, 256, 0, s>>>(p);
+        else if (p.nst == 0 && p.ndo <= 4) trace_packed_fast_kernel<Num, 4><<<grid, 256, 0, s>>>(p);
+        else trace_packed_kernel<Num><<<grid, 256, 0, s>>>(p);
         return cudaGetLastError();
     }
     const size_t smem = (size_t)(p.ncb + 2 * p.nst) * p.d * sizeof(typename Num::store_t);
