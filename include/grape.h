@@ -198,10 +198,13 @@ grape_status grape_problem_set_tile(grape_problem_t problem, int32_t cluster, in
  * grid, for states too large for a cluster's shared memory). */
 grape_status grape_problem_kernel(grape_problem_t problem, int32_t *kind);
 
-/* Waits for the device and reports whether a grid barrier of the grid
- * kernel gave up waiting since the last check (GRAPE_ETIMEOUT; the results
- * of that call are invalid).  Calls that return results to host memory do
- * this check themselves.  GRAPE_OK for the cluster kernels. */
+/* Waits for the device and reports whether a bounded wait of the
+ * propagation kernels gave up since the last check (GRAPE_ETIMEOUT; the
+ * results of that call are invalid): a grid barrier of the grid kernel, or
+ * a window wait of the Hermitian cluster kernel (which waits on mbarriers
+ * for the values its peers push into its shared memory).  The flag is
+ * cleared by the report.  Calls that return results to host memory do this
+ * check themselves. */
 grape_status grape_problem_status(grape_problem_t problem);
 
 /* Per-launch timing with CUDA events recorded on the caller's stream around

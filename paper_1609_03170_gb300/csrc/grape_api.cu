@@ -274,8 +274,8 @@ struct grape_problem {
     int variant = 0;                 // bit 0 = real jump tables, bit 1 = Hermitian kernel
     int hb = 0, cu = 0, maxwin = 0, htab_len = 0, rt_rows = 0;   // Hermitian kernel geometry
     int fold = 0;                    // Hermitian kernel: own-entry coefficients cached in shared memory
-    int bulk = 0;                    // Hermitian kernel: stage storage through staging rows and bulk copies
     int jcache = 0;                  // Hermitian kernel: jump coefficients cached per entry
+    int defer = 0;                   // Hermitian kernel: cluster wait after the compute
     int omax = 0;                    // largest band offset of either Lindbladian
     int hb_h = 0;                    // lower entries the Hermitian stencil reads
     std::map<int, int *> htabs;      // Hermitian tables per cluster width
@@ -651,42 +651,46 @@ grape_status plan_h(grape_problem *P, int ncl, int threads) {
     const std::vector<int> tab = hermitian_table(d, ncl, P->omax, hb, &maxwin, &cu, &rt_rows);
     if (maxwin >= 32767) return fail(GRAPE_EINVAL, "state window too large for 16-bit addresses");
     // shared memory without windows, own-entry and jump-coefficient tables
-    const size_t base = (2 * (size_t)cu + 2 * (size_t)nb * d + 2 * (size_t)nt * d) * sizeof(double2) +
+    // two mbarriers; base values, accumulators and next values of the owned
+    // entries; bands, jump tables; (row, column), RK coefficients, the
+    // window table, the row push table (address and mbarrier per target)
+    // and the neighbour addresses
+    const size_t base = 16 + (2 * (size_t)cu + 2 * (size_t)nb * d + 2 * (size_t)nt * d) * sizeof(double2) +
                         (size_t)cu * sizeof(int2) + 12 * sizeof(double) + tab.size() * sizeof(int) +
-                        (size_t)rt_rows * (ncl + 1) * sizeof(uint32_t) +
+                        (size_t)rt_rows * (2 * ncl + 1) * sizeof(uint32_t) +
                         (size_t)cu * (2 * nb + nt + 1) * sizeof(short);
     const int variant = (P->variant & 1) | 2;
     // Options, each kept only when the tile still fits (the same values, so
     // the same bits, either way): the own-entry coefficients cached per slice
-    // (16 B per owned entry) instead of recomputed every stage; two staging
-    // rows of the owned entries (32 B per owned entry), through which the
-    // stage inputs reach the stage storage by bulk asynchronous copies
-    // instead of per-thread stores; the jump coefficients of real jump
-    // tables cached per entry (8 B per term with an offset and owned entry).
-    bool want_fold = true, want_bulk = true, want_jc = (variant & 1) != 0;
+    // (16 B per owned entry) instead of recomputed every stage; the next
+    // values of the owned entries kept in a row (16 B per owned entry) so
+    // that the cluster wait before the pushes comes after the compute; the
+    // jump coefficients of real jump tables cached per entry (8 B per term
+    // with an offset and owned entry).
+    bool want_fold = true, want_defer = false, want_jc = (variant & 1) != 0;
     if (const char *env = std::getenv("GRAPE_FOLD")) want_fold = std::atoi(env) != 0;
-    if (const char *env = std::getenv("GRAPE_BULK")) want_bulk = std::atoi(env) != 0;
+    if (const char *env = std::getenv("GRAPE_DEFER")) want_defer = std::atoi(env) != 0;   // off: measured slower
     if (const char *env = std::getenv("GRAPE_JCACHE")) want_jc = want_jc && std::atoi(env) != 0;
     int njt = 0;
     for (int q = 0; q < P->tab[0].nt; ++q) njt += ((P->tab[0].jdiag >> q) & 1) ? 0 : 1;
     int njt_d = 0;
     for (int q = 0; q < P->tab[1].nt; ++q) njt_d += ((P->tab[1].jdiag >> q) & 1) ? 0 : 1;
     njt = std::max(njt, njt_d);
-    struct Opt { bool fold, bulk, jc; };
-    const Opt opts[] = {{true, true, true}, {true, true, false}, {true, false, true},
-                        {true, false, false}, {false, true, false}, {false, false, false}};
+    struct Opt { bool fold, defer, jc; };
+    const Opt opts[] = {{true, true, true}, {true, true, false}, {true, false, true}, {true, false, false},
+                        {false, true, false}, {false, false, false}};
     size_t use = 0;
-    bool found = false, fold = false, bulk = false, jcache = false;
+    bool found = false, fold = false, defer = false, jcache = false;
     for (const Opt &o : opts) {
-        if ((o.fold && !want_fold) || (o.bulk && !want_bulk) || (o.jc && !want_jc)) continue;
+        if ((o.fold && !want_fold) || (o.defer && !want_defer) || (o.jc && !want_jc)) continue;
         const size_t sm = base + 2 * (size_t)(maxwin + 1) * sizeof(double2) +
                           (o.fold ? (size_t)cu * sizeof(double2) : 0) +
-                          (o.bulk ? 2 * (size_t)cu * sizeof(double2) : 0) +
+                          (o.defer ? (size_t)cu * sizeof(double2) : 0) +
                           (o.jc ? (size_t)njt * cu * sizeof(double) : 0);
         if (sm + 1024 > (size_t)max_smem || !cluster_fits(P, variant, threads, sm, ncl)) continue;
         use = sm;
         fold = o.fold;
-        bulk = o.bulk;
+        defer = o.defer;
         jcache = o.jc;
         found = true;
         break;
@@ -713,8 +717,9 @@ grape_status plan_h(grape_problem *P, int ncl, int threads) {
     P->rt_rows = rt_rows;
     P->smem = use;
     P->fold = fold ? 1 : 0;
-    P->bulk = bulk ? 1 : 0;
+
     P->jcache = jcache ? 1 : 0;
+    P->defer = defer ? 1 : 0;
     P->threads = threads;
     P->chunk = cu;
     P->halo = 0;
@@ -772,10 +777,7 @@ grape_status choose_geometry_grid(grape_problem *P) {
     const size_t smem = smem_for(ce);
     if (smem + 1024 > (size_t)max_smem) return fail(GRAPE_EINVAL, "problem too large for the grid propagation kernel");
     P->d_gbuf = static_cast<double2 *>(P->alloc((size_t)2 * P->ns * P->d2 * sizeof(double2)));
-    P->d_gbar = static_cast<unsigned *>(P->alloc(4 * sizeof(unsigned)));
-    if (!P->d_gbuf || !P->d_gbar) return fail(GRAPE_ENOMEM, "cudaMalloc failed for the grid kernel buffers");
-    GRAPE_CUDA_TRY(cudaMemset(P->d_gbar, 0, 4 * sizeof(unsigned)));
-    GRAPE_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));   // before non-blocking streams use it
+    if (!P->d_gbuf) return fail(GRAPE_ENOMEM, "cudaMalloc failed for the grid kernel buffers");
     if (const char *env = std::getenv("GRAPE_SPIN_LIMIT")) P->spin_limit = std::atoll(env);
     P->grid = true;
     P->nblocks = nblocks;
@@ -824,8 +826,9 @@ PropArgs base_args(const grape_problem *P, int dir, const double *u) {
     a.maxwin = P->maxwin;
     a.rt_rows = P->rt_rows;
     a.fold = (P->variant & 2) ? P->fold : 0;
-    a.bulk = (P->variant & 2) ? P->bulk : 0;
+
     a.jcache = (P->variant & 2) ? P->jcache : 0;
+    a.defer = (P->variant & 2) ? P->defer : 0;
     a.src = P->penalty ? P->d_src : nullptr;
     a.gbuf = P->d_gbuf;
     a.gbar = P->d_gbar;
@@ -1335,6 +1338,14 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
         for (int c : jcf) real_jumps = real_jumps && c < 0;
         P->variant = real_jumps ? 1 : 0;
     }
+    // error word of the bounded waits (grid barrier arrivals, generation, flag)
+    P->d_gbar = static_cast<unsigned *>(P->alloc(4 * sizeof(unsigned)));
+    if (!P->d_gbar) return bail(fail(GRAPE_ENOMEM, "cudaMalloc failed for the error word"));
+    if (cudaMemset(P->d_gbar, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {   // before non-blocking streams use it
+        cudaGetLastError();
+        return bail(fail(GRAPE_ECUDA, "cudaMemset of the error word failed"));
+    }
     if ((st = upload_dir(P, hf, &P->tab[0])) != GRAPE_OK) return bail(st);
     if ((st = upload_dir(P, ha, &P->tab[1])) != GRAPE_OK) return bail(st);
     int omax = 0;
@@ -1388,6 +1399,7 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
     }
     P->trace = tr;
     trace_layout(P, &P->trace);
+
     P->d_x = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
     P->d_mu = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
     P->d_out = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
@@ -1482,7 +1494,6 @@ grape_status grape_problem_set_tile(grape_problem_t P, int32_t cluster, int32_t 
 
 grape_status grape_problem_status(grape_problem_t P) {
     if (!P) return fail(GRAPE_EINVAL, "NULL problem");
-    if (!P->grid) return GRAPE_OK;
     DeviceGuard g(P->device);
     unsigned flag[3] = {0, 0, 0};
     GRAPE_CUDA_TRY(cudaDeviceSynchronize());
@@ -1490,7 +1501,9 @@ grape_status grape_problem_status(grape_problem_t P) {
     if (flag[2] != 0u) {
         GRAPE_CUDA_TRY(cudaMemset(P->d_gbar, 0, 4 * sizeof(unsigned)));
         GRAPE_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
-        return fail(GRAPE_ETIMEOUT, "a grid barrier of the propagation kernel gave up waiting");
+        return fail(GRAPE_ETIMEOUT, flag[2] == 2u
+                                        ? "a window wait of the cluster propagation kernel gave up waiting"
+                                        : "a grid barrier of the propagation kernel gave up waiting");
     }
     return GRAPE_OK;
 }
@@ -1591,7 +1604,7 @@ grape_status grape_forward(grape_problem_t P, const double *u, double *F, double
     }
     if (sync) {
         GRAPE_CUDA_TRY(cudaStreamSynchronize(s));
-        if (P->grid) return grape_problem_status(P);
+        return grape_problem_status(P);
     }
     return GRAPE_OK;
 }
@@ -1732,7 +1745,7 @@ grape_status grape_gradient(grape_problem_t P, const double *u, double *F, doubl
     }
     if (sync) {
         GRAPE_CUDA_TRY(cudaStreamSynchronize(s));
-        if (P->grid) return grape_problem_status(P);
+        return grape_problem_status(P);
     }
     return GRAPE_OK;
 }

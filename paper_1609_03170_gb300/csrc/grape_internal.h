@@ -73,14 +73,15 @@ struct PropArgs {
     int maxwin;                         // largest window (entries) of the cluster
     int rt_rows;                        // rows of the largest push table
     int fold;                           // Hermitian kernel: own-entry coefficients folded (D table)
-    int bulk;                           // Hermitian kernel: stage inputs reach the stage storage
-                                        // through a staging copy and bulk asynchronous copies
     int jcache;                         // Hermitian kernel, real jump tables: coefficients of the
                                         // jump terms cached per owned entry
+    int defer;                          // Hermitian kernel: next values kept until the cluster
+                                        // wait before the pushes (hides its latency)
     const double *src;                  // adjoint source on the diagonal per row (App. B), or null
     // grid kernel (state windows in global memory, one grid barrier per stage)
     void *gbuf;                         // [2][n_states][d*d] stage-input buffers
-    unsigned *gbar;                     // [0] arrivals, [1] generation, [2] error flag
+    unsigned *gbar;                     // [0] arrivals, [1] generation (grid kernel), [2] error
+                                        // word: 1 a grid barrier, 2 a window wait gave up
     int ce;                             // entries (state, upper entry) per CTA
     long long spin_limit;               // polls of the grid barrier before it gives up
 };

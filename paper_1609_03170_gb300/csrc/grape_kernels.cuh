@@ -367,22 +367,24 @@ __device__ __forceinline__ typename Num::val diag_coef(int i, int j, int d, cons
 // (real multiply-adds: the same bits as the complex ones with a zero
 // imaginary part, half the work), the offset-0 band is last and excluded
 // (it is part of the own-entry coefficient).  x1(b), x2(b): the neighbours
-// (i + o_b, j) and (i, j + o_b).
+// (i + o_b, j) and (i, j + o_b).  The A X terms and the X A^+ terms go to
+// two accumulators (two independent dependency chains), added at the end.
 template <class Num, class X1, class X2>
-__device__ __forceinline__ void band_terms(typename Num::acc &w, const PropTables &t,
-                                           const typename Num::store_t *A, int i, int j, int d,
-                                           X1 &&x1, X2 &&x2) {
+__device__ __forceinline__ typename Num::acc band_terms(const PropTables &t, const typename Num::store_t *A,
+                                                        int i, int j, int d, X1 &&x1, X2 &&x2) {
+    typename Num::acc wa = Num::acc_zero(), wb = Num::acc_zero();
     const int nbo = (t.b0 >= 0) ? t.nb - 1 : t.nb;
 #pragma unroll 1
     for (int b = 0; b < t.nbr; ++b) {
-        Num::mac_real(w, Num::load_re(A[b * d + i]), x1(b));
-        Num::mac_real(w, Num::neg_real(Num::load_re(A[b * d + j])), x2(b));
+        Num::mac_real(wa, Num::load_re(A[b * d + i]), x1(b));
+        Num::mac_real(wb, Num::neg_real(Num::load_re(A[b * d + j])), x2(b));
     }
 #pragma unroll 2
     for (int b = t.nbr; b < nbo; ++b) {
-        Num::mac(w, Num::load(A[b * d + i]), x1(b));
-        Num::mac_conj_neg(w, Num::load(A[b * d + j]), x2(b));
+        Num::mac(wa, Num::load(A[b * d + i]), x1(b));
+        Num::mac_conj_neg(wb, Num::load(A[b * d + j]), x2(b));
     }
+    return Num::acc_add(wa, wb);
 }
 
 // jc: null, or the entry's cached coefficients of the jump terms with an
@@ -401,10 +403,8 @@ __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::s
     // every term is accumulated without a branch (adding 0 changes no bit).
     // The terms on the entry itself - the offset-0 band and the jump terms
     // with both offsets 0 - come as one coefficient D_ij (diag_coef).
-    typename Num::acc w = Num::acc_zero();
-    band_terms<Num>(w, t, A, i, j, d,
-                    [&](int b) { return Num::load(cur[nb_ad[2 * b]]); },
-                    [&](int b) { return Num::load(cur[nb_ad[2 * b + 1]]); });
+    typename Num::acc w = band_terms<Num>(t, A, i, j, d, [&](int b) { return Num::load(cur[nb_ad[2 * b]]); },
+                                          [&](int b) { return Num::load(cur[nb_ad[2 * b + 1]]); });
     w = Num::acc_minus_i(w);
     Num::mac(w, dij, Num::load(cur[nb_ad[2 * t.nb + t.nt]]));
     if (REALJ && jc) {
@@ -451,56 +451,132 @@ __device__ __forceinline__ void hpush_pre(const uint32_t *rowtab, int rstride, i
     for (int t = 1; t <= n; ++t) st_cluster_addr(e[t] + boff + (uint32_t)c * (uint32_t)sizeof(S), v);
 }
 
-// Bulk asynchronous copies shared::cta -> global (the copy engine reads the
-// source while the CTA computes; the cluster barrier's release does not wait
-// for them).  Addresses 16-byte aligned, sizes multiples of 16 bytes.
-__device__ __forceinline__ void bulk_store(void *gdst, uint32_t ssrc, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc),
+// Distributed-shared-memory pushes with transaction counting: st.async
+// writes 16 bytes into a peer CTA's window and counts them on the peer's
+// mbarrier of that window (complete_tx), so the writer never waits for the
+// store to complete; the reader waits on its own mbarrier until every byte
+// its window expects in the phase has arrived.  Pushes into the CTA's own
+// window are ordinary shared-memory stores (ordered by the CTA barrier).
+__device__ __forceinline__ void st_async16(uint32_t addr, float4 v, uint32_t mbar) {
+    asm volatile("st.async.weak.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+                 ::"r"(addr), "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+                 "r"(__float_as_uint(v.w)), "r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async16(uint32_t addr, double2 v, uint32_t mbar) {
+    asm volatile("st.async.weak.shared::cluster.mbarrier::complete_tx::bytes.v2.b64 [%0], {%1, %2}, [%3];"
+                 ::"r"(addr), "l"(__double_as_longlong(v.x)), "l"(__double_as_longlong(v.y)), "r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_local16(uint32_t addr, float4 v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void st_local16(uint32_t addr, double2 v) {
+    asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(v.x), "d"(v.y) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// the one arrival of a phase, announcing the bytes the phase expects
+__device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\t"
+                 "mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mbar),
                  "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// the sources of every committed copy have been read
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// every committed copy has completed
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-// orders this thread's shared-memory writes before later async-proxy reads
-__device__ __forceinline__ void fence_proxy_async_cta() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+// bounded wait for the phase of the given parity: false when it gave up
+// after `cycles` SM clock cycles (about a second for 2^31)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long cycles) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (clock64() - t0 > cycles) return false;
+    }
+}
+// the two halves of the cluster barrier without memory ordering: they only
+// keep a CTA from overwriting a window a peer may still be reading
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_only() {
+    asm volatile("barrier.cluster.wait;" ::: "memory");
 }
 
-// Shared memory: buf0, buf1 [maxwin + 1] (the last entry of each stays
-// zero); xs, as [cu]; D [cu] when p.fold; stg [2][cu] when p.bulk;
-// bands [2][nb][d]; vL, vR [nt][d]; rc [cu] (int2); 12 RK coefficients; jump
+// push value v of entry (r, c) to every window holding row r: rowtab holds,
+// per row, the target count and per target the address of (r, 0) in buf0
+// (shared::cluster for a peer, shared::cta for the own CTA) and the peer's
+// mbarrier of buf0 (0 for the own CTA); boff selects the next window and
+// moff its mbarrier
+template <class S>
+__device__ __forceinline__ void hpush_async(const uint32_t *rowtab, int rstride, int rrow, int c, uint32_t boff,
+                                            uint32_t moff, S v) {
+    const uint32_t *e = rowtab + rrow * rstride;
+    const int n = (int)e[0];
+    for (int t = 0; t < n; ++t) {
+        const uint32_t a = e[1 + 2 * t] + boff + (uint32_t)c * (uint32_t)sizeof(S);
+        const uint32_t m = e[2 + 2 * t];
+        if (m) st_async16(a, v, m + moff);
+        else st_local16(a, v);
+    }
+}
+
+// Shared memory: two mbarriers (16 B); buf0, buf1 [maxwin + 1] (the last
+// entry of each stays zero); xs, as [cu]; D [cu] when p.fold; z [cu] when
+// p.defer; bands
+// [2][nb][d]; vL, vR [nt][d]; rc [cu] (int2); 12 RK coefficients; jump
 // coefficients [njt][cu] (real_t) when p.jcache; htab copy (ints); row push
-// table [rt_rows][ncl + 1] (u32); neighbour addresses [cu][ns + 1] (i16).
+// table [rt_rows][2 ncl + 1] (u32); neighbour addresses [cu][ns + 1] (i16).
 //
-// Stage inputs go to the stage storage as packed upper triangles: a CTA's
-// owned entries [u0, u1) are one contiguous range of it.  With p.bulk every
-// thread also writes the next stage input of its entries, in that order,
-// into one of two staging rows; after the stage's barrier one thread copies
-// the row to HBM with one bulk asynchronous copy and makes sure, before the
-// next barrier, that the copy has read it (the row is rewritten one stage
-// later).  The barrier's release then orders only the distributed-shared-
-// memory pushes.  Without p.bulk (tiles where the staging rows do not fit)
-// each thread stores its entries' stage inputs itself, before computing them.
+// Stage g reads window g mod 2 and pushes the next stage's input into
+// window (g + 1) mod 2.  Synchronisation per stage (cluster of ncl > 1):
+//  - wait on the window's mbarrier: every byte that peers push into it for
+//    this stage has landed (one thread announced the count when the phase
+//    began, 16 B per window slot a peer owns); own-CTA pushes are ordered by
+//    the CTA barrier that ends the previous stage;
+//  - compute the owned entries (their next values wait in the z row);
+//  - wait on the cluster barrier that every thread arrived at after
+//    computing the previous stage: no peer still reads the window the
+//    pushes below overwrite.  Its latency is hidden behind the compute
+//    (tiles without room for the z row wait before computing and push each
+//    entry as it is computed: the same values);
+//  - push, arrive at the cluster barrier (relaxed: it orders nothing), CTA
+//    barrier.
+// No release fence waits for the pushes or the stage stores.  Every
+// mbarrier wait is bounded: when one gives up, the error word gbar[2] is set
+// to 2, later waits are skipped and the results are invalid (the host
+// reports GRAPE_ETIMEOUT).  A one-CTA cluster pushes only into itself and
+// needs only the CTA barrier.
 template <class Num, bool REALJ>
 __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const PropArgs p) {
     using S = typename Num::store_t;
     using V = typename Num::val;
     using R = typename Num::real_t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_count, s_err;
     const int d = p.d, d2 = d * d;
     const int NU = d * (d + 1) / 2;
     const int nbd = p.tab.nb * d;
     const int wst = p.maxwin + 1;                // window stride; slot maxwin is the zero slot
-    S *buf0 = reinterpret_cast<S *>(smem_raw);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);
+    S *buf0 = reinterpret_cast<S *>(smem_raw + 16);
     S *buf1 = buf0 + wst;
     S *xs = buf1 + wst;
     S *as = xs + p.cu;
     S *Dt = as + p.cu;                           // [cu] own-entry coefficients when p.fold
-    S *stg = Dt + (p.fold ? p.cu : 0);           // [2][cu] staging rows when p.bulk
-    S *bands = stg + (p.bulk ? 2 * p.cu : 0);
+    S *zr = Dt + (p.fold ? p.cu : 0);            // [cu] next stage values when p.defer
+    S *bands = zr + (p.defer ? p.cu : 0);
     S *vL = bands + 2 * nbd;
     S *vR = vL + p.tab.nt * d;
     int2 *rc = reinterpret_cast<int2 *>(vR + p.tab.nt * d);
@@ -511,7 +587,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     const bool jcache = REALJ && p.jcache;
     R *jc = cg + 12;                             // [njt][cu] when jcache
     int *tab = reinterpret_cast<int *>(jc + (jcache ? njt * p.cu : 0));
-    const int rstride = p.ncl + 1;
+    const int rstride = 2 * p.ncl + 1;
     uint32_t *rowtab = reinterpret_cast<uint32_t *>(tab + p.htab_len);
     short *nbad = reinterpret_cast<short *>(rowtab + p.rt_rows * rstride);
     const int ns = 2 * p.tab.nb + p.tab.nt;     // neighbour slots; slot ns = own address
@@ -525,8 +601,16 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     const size_t soff = (size_t)state * d2;
     const int nth = blockDim.x;
     const int hb = p.hb;
-    const bool bulk = p.bulk && stage_store;
+    const bool clu = p.ncl > 1;
+    const uint32_t mbar_sa = smem_u32(mbar);
 
+    if (threadIdx.x == 0) {
+        s_count = 0;
+        s_err = 0;
+        mbar_init(mbar_sa, 1);
+        mbar_init(mbar_sa + 8, 1);
+        mbar_init_fence();
+    }
     for (int i = threadIdx.x; i < p.htab_len; i += nth) tab[i] = __ldg(&p.htab[i]);
     const V vzero = Num::zero();
     for (int i = threadIdx.x; i < 2 * wst; i += nth) buf0[i] = Num::store(vzero);
@@ -546,7 +630,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     build_bands<Num>(bands, p, jcur);
     __syncthreads();
     const int u0 = tab[GRAPE_HTAB_CTA(rank) + 0], u1 = tab[GRAPE_HTAB_CTA(rank) + 1];
-    const int wr0 = tab[GRAPE_HTAB_CTA(rank) + 2];
+    const int wr0 = tab[GRAPE_HTAB_CTA(rank) + 2], nrows = tab[GRAPE_HTAB_CTA(rank) + 3];
     const int *ofs = tab + tab[GRAPE_HTAB_LISTS(p.ncl) + rank];
     const int *kfl = tab + tab[GRAPE_HTAB_LISTS(p.ncl) + p.ncl];   // kfirst[d], klast[d]
     // (row, column) of the owned upper entries (row-major offset of row i is
@@ -583,6 +667,21 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
             }
         }
     }
+    // window slots written by peers each stage (16 B each): slot (r, c) of
+    // the window holds the upper entry (r, c), c >= r, or the mirror of
+    // (c, r); its writer is the owner of that upper entry
+    if (clu) {
+        const int cu = p.cu;
+        int cnt = 0;
+        for (int lr = threadIdx.x; lr < nrows; lr += nth) {
+            const int r = wr0 + lr;
+            for (int c = cs_of(r, hb); c < d; ++c) {
+                const int ur = c >= r ? r * d - r * (r - 1) / 2 + (c - r) : c * d - c * (c - 1) / 2 + (r - c);
+                if (ur / cu != rank) ++cnt;
+            }
+        }
+        if (cnt) atomicAdd(&s_count, cnt);
+    }
     // push targets of the rows this CTA writes: its own rows and, for the
     // mirrors, up to hb rows below
     int rfirst = 0, rlast = -1;
@@ -608,30 +707,40 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
             const int wk = tab[GRAPE_HTAB_CTA(k) + 2];
             const int *ofk = tab + tab[GRAPE_HTAB_LISTS(p.ncl) + k];
             const int base = ofk[r - wk] - cs_of(r, hb);       // entry index of (r, 0), may be < 0
-            e[1 + n++] = map_to_rank(buf0_sa, (uint32_t)k) + (uint32_t)(base * (int)sizeof(S));
+            const uint32_t boffs = (uint32_t)(base * (int)sizeof(S));
+            if (k == rank) {
+                e[1 + 2 * n] = buf0_sa + boffs;
+                e[2 + 2 * n] = 0u;
+            } else {
+                e[1 + 2 * n] = map_to_rank(buf0_sa, (uint32_t)k) + boffs;
+                e[2 + 2 * n] = map_to_rank(mbar_sa, (uint32_t)k);
+            }
+            ++n;
         }
         e[0] = (uint32_t)n;
     }
-    cluster_sync_all();   // every CTA runs, windows zeroed, tables built
+    cluster_sync_all();   // every CTA runs, windows zeroed, mbarriers initialised, tables built
+    const uint32_t expect = (uint32_t)s_count * (uint32_t)sizeof(S);
+    const long long limit = 1LL << 31;          // SM cycles a window wait may take
     const uint32_t boff1 = (uint32_t)(wst * (int)sizeof(S));
 
+    // the initial stage input (window 0)
+    if (clu && threadIdx.x == 0) mbar_expect(mbar_sa, expect);
     for (int u = u0 + threadIdx.x; u < u1; u += nth) {
         const int2 ij = rc[u - u0];
         const V x = Num::load(x_in[soff + (size_t)ij.x * d + ij.y]);
         xs[u - u0] = Num::store(x);
         const V z = Num::scale(cg[0], x);
-        if (bulk) stg[u - u0] = Num::store(z);
-        hpush_pre(rowtab, rstride, ij.x - rfirst, ij.y, 0u, Num::store(z));
+        hpush_async(rowtab, rstride, ij.x - rfirst, ij.y, 0u, 0u, Num::store(z));
         if (ij.y > ij.x && ij.y - ij.x <= hb)
-            hpush_pre(rowtab, rstride, ij.y - rfirst, ij.x, 0u, conj_store<Num>(z));
+            hpush_async(rowtab, rstride, ij.y - rfirst, ij.x, 0u, 0u, conj_store<Num>(z));
     }
-    if (bulk) fence_proxy_async_cta();
-    cluster_sync_all();
+    if (clu) cluster_arrive_relaxed();
+    __syncthreads();
 
     const bool unit_g = (p.g[1] == 1.0 && p.g[2] == 1.0 && p.g[3] == 1.0);   // forward RK4
-    const bool copier = bulk && threadIdx.x == 0 && u1 > u0;
     int tb = 0;
-    int gp = 0;                                  // staging row holding the current stage input
+    uint32_t g = 0;                              // stages done in this launch
     bool dfresh = true;                          // D table to (re)build for this slice
     for (long long it = 0; it < nsub; ++it) {
         const long long n = p.reverse ? p.sub_end - 1 - it : p.sub_begin + it;
@@ -647,25 +756,26 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
 #pragma unroll 1
         for (int s = 0; s < 4; ++s) {
             const S *cur = (s & 1) ? buf1 : buf0;
-            const uint32_t boff = (s & 1) ? 0u : boff1;          // next buffer
+            const uint32_t boff = (s & 1) ? 0u : boff1;          // next window
+            const uint32_t moff = (s & 1) ? 0u : 8u;             // its mbarrier
+            if (clu) {
+                if (!s_err && !mbar_wait(mbar_sa + (g & 1) * 8, (g >> 1) & 1, limit)) {
+                    s_err = 1;
+                    atomicExch(&p.gbar[2], 2u);
+                }
+                if (threadIdx.x == 0 && !s_err) mbar_expect(mbar_sa + moff, expect);
+            }
             S *st = nullptr;                     // packed stage storage of this state
             if (stage_store)
                 st = stage_store + ((size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states + state) * NU;
-            if (copier) {
-                bulk_store(st + u0, smem_u32(stg + gp * p.cu), (uint32_t)((u1 - u0) * (int)sizeof(S)));
-                bulk_commit();
-            }
-            S *stn = stg + (gp ^ 1) * p.cu;      // staging row of the next stage input
             const R as_ = ca[s];
+            if (clu && !p.defer) cluster_wait_only();
 #pragma unroll 1
             for (int u = u0 + threadIdx.x; u < u1; u += nth) {
                 const int li = u - u0;
                 const int2 ij = rc[li];
                 const short *na = nbad + (size_t)li * nstride;
-                // without the bulk copies: the stage input itself, stored first so
-                // that the global store completes while the entry is computed (the
-                // barrier's release at the end of the stage waits for it)
-                if (st && !bulk) st[u] = cur[na[ns]];
+                if (st) st[u] = cur[na[ns]];     // the stage input itself, packed
                 // own-entry coefficient: cached per slice (the entry is thread-private,
                 // so no barrier is needed) or recomputed when there is no room
                 V dij;
@@ -688,10 +798,25 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                     xs[li] = Num::store(nx);
                     z = Num::scale(cg[0], nx);
                 }
-                if (bulk) stn[li] = Num::store(z);
-                hpush_pre(rowtab, rstride, ij.x - rfirst, ij.y, boff, Num::store(z));
-                if (ij.y > ij.x && ij.y - ij.x <= hb)
-                    hpush_pre(rowtab, rstride, ij.y - rfirst, ij.x, boff, conj_store<Num>(z));
+                if (p.defer) {
+                    zr[li] = Num::store(z);
+                } else {
+                    hpush_async(rowtab, rstride, ij.x - rfirst, ij.y, boff, moff, Num::store(z));
+                    if (ij.y > ij.x && ij.y - ij.x <= hb)
+                        hpush_async(rowtab, rstride, ij.y - rfirst, ij.x, boff, moff, conj_store<Num>(z));
+                }
+            }
+            if (p.defer) {
+                if (clu) cluster_wait_only();    // no peer still reads the next window
+#pragma unroll 1
+                for (int u = u0 + threadIdx.x; u < u1; u += nth) {
+                    const int li = u - u0;
+                    const int2 ij = rc[li];
+                    const S z = zr[li];
+                    hpush_async(rowtab, rstride, ij.x - rfirst, ij.y, boff, moff, z);
+                    if (ij.y > ij.x && ij.y - ij.x <= hb)
+                        hpush_async(rowtab, rstride, ij.y - rfirst, ij.x, boff, moff, conj_store<Num>(Num::load(z)));
+                }
             }
             if (s == 3 && it + 1 < nsub) {
                 const long long nn = p.reverse ? n - 1 : n + 1;
@@ -702,18 +827,19 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                     flip = true;
                 }
             }
-            if (bulk) fence_proxy_async_cta();   // the staging row before the next copy reads it
-            if (copier) bulk_wait_read();        // this stage's row is rewritten in the next stage
-            // a one-CTA cluster needs only the CTA barrier (it orders the CTA's own
-            // shared-memory stores, whatever window address they used)
-            if (p.ncl == 1) __syncthreads();
-            else cluster_sync_all();
-            gp ^= 1;
+            if (clu) cluster_arrive_relaxed();
+            __syncthreads();
+            ++g;
         }
         if (flip) tb ^= 1;
         dfresh = flip;
     }
-    if (copier) bulk_wait_all();
+    if (clu) {
+        // the last pushes: the matching cluster wait, then every byte peers
+        // pushed into this CTA has landed before it exits
+        cluster_wait_only();
+        if (!s_err && !mbar_wait(mbar_sa + (g & 1) * 8, (g >> 1) & 1, limit)) atomicExch(&p.gbar[2], 2u);
+    }
     const long long tend = p.reverse ? p.sub_begin : p.sub_end;
     if (bound_store && ((tend - p.sub_begin) % p.bound_step) == 0) {
         S *dst = bound_store + ((size_t)((tend - p.sub_begin) / p.bound_step) * p.n_states) * d2 + soff;
@@ -782,9 +908,8 @@ __device__ __forceinline__ typename Num::val lindblad_g_at(const typename Num::s
                                                            const double *uj) {
     // same terms in the same order as lindblad_h_at (identical bits; a
     // neighbour outside the matrix contributes an exact zero there)
-    typename Num::acc w = Num::acc_zero();
     const typename Num::val vz = Num::zero();
-    band_terms<Num>(w, t, A, i, j, d,
+    typename Num::acc w = band_terms<Num>(t, A, i, j, d,
                     [&](int b) {
                         const int r = i + t.off[b];
                         return (r >= 0 && r < d) ? Num::load(__ldcg(&cur[(size_t)r * d + j])) : vz;

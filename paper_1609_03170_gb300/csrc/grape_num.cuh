@@ -131,6 +131,7 @@ struct NumD {
     static __device__ __forceinline__ val done(acc c) { return {c.re, c.im}; }
     static __device__ __forceinline__ val raw(acc c) { return {c.re, c.im}; }
     static __device__ __forceinline__ acc acc_minus_i(acc c) { return {c.im, -c.re}; }
+    static __device__ __forceinline__ acc acc_add(acc a, acc b) { return {a.re + b.re, a.im + b.im}; }
     // a - conj(b), a + b, a + c (c real)
     static __device__ __forceinline__ val sub_conj(val a, val b) { return {a.re - b.re, a.im + b.im}; }
     static __device__ __forceinline__ val add(val a, val b) { return {a.re + b.re, a.im + b.im}; }
@@ -204,6 +205,12 @@ struct NumF {
     // consumers that multiply keep every cross term, so nothing is lost)
     static __device__ __forceinline__ val raw(acc c) { return {{c.re.h, c.re.l}, {c.im.h, c.im.l}}; }
     static __device__ __forceinline__ acc acc_minus_i(acc c) { return {c.im, {-c.re.h, -c.re.l}}; }
+    // a + b of two accumulators: the high parts with TwoSum, every error in
+    // the low part (still unnormalised)
+    static __device__ __forceinline__ acc acc_add(acc a, acc b) {
+        const ff r = two_sum(a.re.h, b.re.h), i = two_sum(a.im.h, b.im.h);
+        return {{r.h, __fadd_rn(r.l, __fadd_rn(a.re.l, b.re.l))}, {i.h, __fadd_rn(i.l, __fadd_rn(a.im.l, b.im.l))}};
+    }
     static __device__ __forceinline__ val sub_conj(val a, val b) {
         return {ff_sum(a.re, {-b.re.h, -b.re.l}), ff_sum(a.im, b.im)};
     }
