@@ -280,7 +280,10 @@ struct grape_problem {
     int hb_h = 0;                    // lower entries the Hermitian stencil reads
     std::map<int, int *> htabs;      // Hermitian tables per cluster width
     bool grid = false;               // grid kernel (state windows in global memory)
-    int nblocks = 0, ce = 0;         // its CTAs and entries per CTA
+    int nblocks = 0;                 // its CTAs (n_states x ncl)
+    unsigned *d_gflag = nullptr;     // its per-CTA round flags
+    int *d_ntab = nullptr;           // its neighbour lists
+    int ntab_stride = 0;
     long long spin_limit = 1LL << 22;   // grid-barrier polls (~0.3 s) before giving up
     double2 *d_gbuf = nullptr;
     unsigned *d_gbar = nullptr;
@@ -405,6 +408,8 @@ grape_status upload(grape_problem *P, const std::vector<T> &h, T **out) {
     return GRAPE_OK;
 }
 
+double2 encode(const grape_problem *P, cplx v);
+
 grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
     const int d = P->d;
     if ((int)h.off.size() > GRAPE_MAXB)
@@ -445,6 +450,15 @@ grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
     t->vL = p;
     if ((s = upload(P, cvt(h.vR), &p)) != GRAPE_OK) return s;
     t->vR = p;
+    auto enc = [&](const std::vector<cplx> &v) {
+        std::vector<double2> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = encode(P, v[i]);
+        return o;
+    };
+    if ((s = upload(P, enc(h.vL), &p)) != GRAPE_OK) return s;
+    t->vLs = p;
+    if ((s = upload(P, enc(h.vR), &p)) != GRAPE_OK) return s;
+    t->vRs = p;
     return GRAPE_OK;
 }
 
@@ -453,7 +467,9 @@ cudaError_t k_prop(const grape_problem *P, const PropArgs &a, cudaStream_t s) {
     if (P->grid) {
         // arrivals and generation restart at zero; the error flag is kept
         // until grape_problem_status reads it
-        const cudaError_t e = cudaMemsetAsync(P->d_gbar, 0, 2 * sizeof(unsigned), s);
+        // round flags restart at zero; the error word is kept until
+        // grape_problem_status reads it
+        const cudaError_t e = cudaMemsetAsync(P->d_gflag, 0, (size_t)P->nblocks * sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
         return P->prec == GRAPE_PREC_FP64 ? grape_launch_grid_f64(a, P->nblocks, P->variant, P->smem, s)
                                           : grape_launch_grid_df(a, P->nblocks, P->variant, P->smem, s);
@@ -747,45 +763,128 @@ grape_status choose_geometry_h(grape_problem *P) {
     return fail(GRAPE_EINVAL, "problem too large for the Hermitian cluster kernel");
 }
 
-// Grid kernel: all states' upper triangles over at most one CTA per SM.
-grape_status choose_geometry_grid(grape_problem *P) {
-    int max_smem = 0;
-    GRAPE_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
-    const long long NU = (long long)P->d * (P->d + 1) / 2;
-    const long long E = NU * P->ns;
-    const int nb = std::max(P->tab[0].nb, P->tab[1].nb), nt = std::max(P->tab[0].nt, P->tab[1].nt);
-    auto smem_for = [&](long long ce) {
-        return ((size_t)2 * ce + 2 * (size_t)nb * P->d + 2 * (size_t)nt * P->d) * sizeof(double2) +
-               (size_t)ce * sizeof(int4) + 12 * sizeof(double);
+// Neighbour lists of the grid kernel's CTAs (of one state): a and b are
+// neighbours when one writes a row the other's window holds.  The rows a
+// CTA writes lie in [first own row, last own row + hb] (its own rows and
+// the mirror rows of its entries near the diagonal).  Row k of the table:
+// the count, then the ranks; *stride = 1 + the largest count.
+std::vector<int> neighbour_table(const std::vector<int> &tab, int d, int nct, int hb, int *stride) {
+    auto row_start = [d](long long i) { return i * d - i * (i - 1) / 2; };
+    auto row_of = [&](long long u) {
+        long long lo = 0, hi = d - 1;
+        while (lo < hi) {
+            const long long mid = (lo + hi + 1) / 2;
+            if (row_start(mid) <= u) lo = mid; else hi = mid - 1;
+        }
+        return (int)lo;
     };
-    int max_blocks = 0;
-    const size_t probe = smem_for((E + 151) / 152);
-    cudaError_t e = P->prec == GRAPE_PREC_FP64
-                        ? grape_prepare_grid_f64(P->variant, (size_t)max_smem, probe, &max_blocks)
-                        : grape_prepare_grid_df(P->variant, (size_t)max_smem, probe, &max_blocks);
-    if (e != cudaSuccess || max_blocks < 1) {
-        cudaGetLastError();
-        return fail(GRAPE_EINVAL, "problem too large for the grid propagation kernel");
+    std::vector<int> r0(nct, 1), r1(nct, 0), w0(nct), w1(nct);
+    for (int k = 0; k < nct; ++k) {
+        const long long u0 = tab[GRAPE_HTAB_CTA(k) + 0], u1 = tab[GRAPE_HTAB_CTA(k) + 1];
+        if (u1 > u0) {
+            r0[k] = row_of(u0);
+            r1[k] = std::min(d - 1, row_of(u1 - 1) + hb);
+        }
+        w0[k] = tab[GRAPE_HTAB_CTA(k) + 2];
+        w1[k] = w0[k] + tab[GRAPE_HTAB_CTA(k) + 3] - 1;
     }
-    long long want = std::max<long long>(1, (E + 63) / 64);    // >= 64 entries per CTA
+    auto writes_into = [&](int a, int b) { return r0[a] <= r1[a] && w0[b] <= w1[b] && r0[a] <= w1[b] && w0[b] <= r1[a]; };
+    std::vector<std::vector<int>> nbrs(nct);
+    size_t mx = 0;
+    for (int a = 0; a < nct; ++a) {
+        for (int b = 0; b < nct; ++b)
+            if (a != b && (writes_into(a, b) || writes_into(b, a))) nbrs[a].push_back(b);
+        mx = std::max(mx, nbrs[a].size());
+    }
+    *stride = (int)mx + 1;
+    std::vector<int> out((size_t)nct * *stride, 0);
+    for (int a = 0; a < nct; ++a) {
+        out[(size_t)a * *stride] = (int)nbrs[a].size();
+        for (size_t t = 0; t < nbrs[a].size(); ++t) out[(size_t)a * *stride + 1 + t] = nbrs[a][t];
+    }
+    return out;
+}
+
+// Grid kernel: nct CTAs per state, one per SM (all resident), the
+// Hermitian kernel's ownership and window tables over nct CTAs.
+grape_status choose_geometry_grid(grape_problem *P) {
+    int max_smem = 0, sms = 0;
+    GRAPE_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+    GRAPE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device));
+    const int d = P->d, hb = P->hb_h;
+    const int nb = std::max(P->tab[0].nb, P->tab[1].nb), nt = std::max(P->tab[0].nt, P->tab[1].nt);
+    int nct = std::max(1, sms / P->ns);
     if (const char *env = std::getenv("GRAPE_GRID_BLOCKS")) {
         const long long v = std::atoll(env);
-        if (v > 0) want = v;
+        if (v > 0) nct = (int)std::max<long long>(1, std::min<long long>(v / P->ns, sms / P->ns));
     }
-    const int nblocks = (int)std::min<long long>(want, max_blocks);
-    const long long ce = (E + nblocks - 1) / nblocks;
-    const size_t smem = smem_for(ce);
-    if (smem + 1024 > (size_t)max_smem) return fail(GRAPE_EINVAL, "problem too large for the grid propagation kernel");
+    int maxwin = 0, cu = 0, rt_rows = 0;
+    const std::vector<int> tab = hermitian_table(d, nct, P->omax, hb, &maxwin, &cu, &rt_rows);
+    if (maxwin >= 32767) return fail(GRAPE_EINVAL, "state window too large for the grid propagation kernel");
+    const int variant = P->variant & 1;
+    int njt = 0;
+    for (int dir = 0; dir < 2; ++dir) {
+        int n = 0;
+        for (int q = 0; q < P->tab[dir].nt; ++q) n += ((P->tab[dir].jdiag >> q) & 1) ? 0 : 1;
+        njt = std::max(njt, n);
+    }
+    // one window, base values and accumulators, one band table (the jump
+    // tables stay in global memory)
+    const size_t base = ((size_t)(maxwin + 1) + 2 * (size_t)cu + (size_t)nb * d) * sizeof(double2) +
+                        (size_t)cu * sizeof(int2) + 12 * sizeof(double) + tab.size() * sizeof(int) +
+                        (size_t)cu * (2 * nb + nt + 1) * sizeof(short);
+    bool want_fold = true, want_jc = variant != 0;
+    if (const char *env = std::getenv("GRAPE_FOLD")) want_fold = std::atoi(env) != 0;
+    if (const char *env = std::getenv("GRAPE_JCACHE")) want_jc = want_jc && std::atoi(env) != 0;
+    struct Opt { bool fold, jc; };
+    const Opt opts[] = {{true, true}, {true, false}, {false, true}, {false, false}};
+    size_t smem = 0;
+    bool found = false, fold = false, jcache = false;
+    for (const Opt &o : opts) {
+        if ((o.fold && !want_fold) || (o.jc && !want_jc)) continue;
+        const size_t sm = base + (o.fold ? (size_t)cu * sizeof(double2) : 0) +
+                          (o.jc ? (size_t)njt * cu * sizeof(double) : 0);
+        if (sm + 1024 > (size_t)max_smem) continue;
+        int max_blocks = 0;
+        const cudaError_t e = P->prec == GRAPE_PREC_FP64
+                                  ? grape_prepare_grid_f64(variant, (size_t)max_smem, sm, &max_blocks)
+                                  : grape_prepare_grid_df(variant, (size_t)max_smem, sm, &max_blocks);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (max_blocks < nct * P->ns) continue;   // every CTA must be resident
+        smem = sm;
+        fold = o.fold;
+        jcache = o.jc;
+        found = true;
+        break;
+    }
+    if (!found) return fail(GRAPE_EINVAL, "problem too large for the grid propagation kernel");
+    int stride = 0;
+    const std::vector<int> ntab = neighbour_table(tab, d, nct, hb, &stride);
+    grape_status st;
+    if ((st = upload(P, tab, &P->d_htab)) != GRAPE_OK) return st;
+    if ((st = upload(P, ntab, &P->d_ntab)) != GRAPE_OK) return st;
     P->d_gbuf = static_cast<double2 *>(P->alloc((size_t)2 * P->ns * P->d2 * sizeof(double2)));
-    if (!P->d_gbuf) return fail(GRAPE_ENOMEM, "cudaMalloc failed for the grid kernel buffers");
+    P->d_gflag = static_cast<unsigned *>(P->alloc((size_t)nct * P->ns * sizeof(unsigned)));
+    if (!P->d_gbuf || !P->d_gflag) return fail(GRAPE_ENOMEM, "cudaMalloc failed for the grid kernel buffers");
     if (const char *env = std::getenv("GRAPE_SPIN_LIMIT")) P->spin_limit = std::atoll(env);
     P->grid = true;
-    P->nblocks = nblocks;
-    P->ce = (int)ce;
+    P->variant = variant;
+    P->nblocks = nct * P->ns;
+    P->ncl = nct;
+    P->cu = cu;
+    P->maxwin = maxwin;
+    P->hb = hb;
+    P->htab_len = (int)tab.size();
+    P->rt_rows = rt_rows;
+    P->fold = fold ? 1 : 0;
+    P->jcache = jcache ? 1 : 0;
+    P->ntab_stride = stride;
     P->smem = smem;
     P->threads = GRAPE_GRID_THREADS;
-    P->ncl = 1;
-    P->chunk = (int)ce;
+    P->chunk = cu;
     return GRAPE_OK;
 }
 
@@ -825,14 +924,16 @@ PropArgs base_args(const grape_problem *P, int dir, const double *u) {
     a.cu = P->cu;
     a.maxwin = P->maxwin;
     a.rt_rows = P->rt_rows;
-    a.fold = (P->variant & 2) ? P->fold : 0;
+    a.fold = ((P->variant & 2) || P->grid) ? P->fold : 0;
 
-    a.jcache = (P->variant & 2) ? P->jcache : 0;
+    a.jcache = ((P->variant & 2) || P->grid) ? P->jcache : 0;
     a.defer = (P->variant & 2) ? P->defer : 0;
     a.src = P->penalty ? P->d_src : nullptr;
     a.gbuf = P->d_gbuf;
     a.gbar = P->d_gbar;
-    a.ce = P->ce;
+    a.gflag = P->d_gflag;
+    a.ntab = P->d_ntab;
+    a.ntab_stride = P->ntab_stride;
     a.spin_limit = P->spin_limit;
     rk_coefficients(P->T / P->n_slices / P->n_rk, dir == 1, &a);
     return a;

@@ -36,6 +36,8 @@ struct PropTables {
     const double2 *Ak;          // [R][nb][d]
     const double2 *vL;          // [nt][d]
     const double2 *vR;          // [nt][d]
+    const void *vLs, *vRs;      // the same in the kernels' storage format (read from global
+                                // memory by the grid kernel)
 };
 
 // One RK4 sweep over substeps [sub_begin, sub_end) of one segment.  The
@@ -78,12 +80,16 @@ struct PropArgs {
     int defer;                          // Hermitian kernel: next values kept until the cluster
                                         // wait before the pushes (hides its latency)
     const double *src;                  // adjoint source on the diagonal per row (App. B), or null
-    // grid kernel (state windows in global memory, one grid barrier per stage)
+    // grid kernel (stage values in global memory, windows loaded per stage;
+    // ncl = CTAs per state, htab/maxwin/cu/hb as for the Hermitian kernel)
     void *gbuf;                         // [2][n_states][d*d] stage-input buffers
-    unsigned *gbar;                     // [0] arrivals, [1] generation (grid kernel), [2] error
-                                        // word: 1 a grid barrier, 2 a window wait gave up
-    int ce;                             // entries (state, upper entry) per CTA
-    long long spin_limit;               // polls of the grid barrier before it gives up
+    unsigned *gbar;                     // [2]: error word, 1 a grid kernel wait gave up, 2 a
+                                        // window wait of the Hermitian kernel gave up
+    unsigned *gflag;                    // [n_states][ncl] finished push rounds per CTA (zeroed
+                                        // before every launch)
+    const int *ntab;                    // [ncl][ntab_stride]: count and ranks of a CTA's neighbours
+    int ntab_stride;
+    long long spin_limit;               // polls of a grid-kernel wait before it gives up
 };
 
 #define GRAPE_GRID_THREADS 512

@@ -851,14 +851,29 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
 }
 
 // ---------------------------------------------------------------------------
-// Grid kernel for states too large for a cluster's shared memory: one
-// cooperative grid of CTAs (at most one per SM) shares all states' upper
-// triangles in contiguous chunks; the stage inputs live as full matrices in
-// global memory (L2-resident; read with ld.global.cg so stale L1 lines are
-// never used), every upper entry written together with its conjugate
-// mirror; a grid barrier separates RK stages.  The barrier's wait is
-// bounded: after spin_limit polls it raises the error flag and every CTA
-// leaves its loop, so a fault cannot hang the GPU.
+// Grid kernel for states too large for a cluster's shared memory (d = 600:
+// rho is 5.76 MB): nct CTAs per state, at most one per SM, all resident (a
+// cooperative launch).  The CTAs share a state's upper triangle as the
+// Hermitian cluster kernel's CTAs do (contiguous entry ranges, compact row
+// windows of rows first - omax .. last + omax, the same neighbour address
+// tables and the same per-entry arithmetic, so the same bits), but a window
+// lives in the CTA's shared memory only while one stage is computed: the
+// stage values themselves live as full matrices in two global buffers
+// (L2-resident), each upper entry written with its conjugate mirror.  Per
+// stage a CTA
+//  - waits until every neighbour CTA - one that writes a row of its window
+//    or holds a row it writes - has finished the previous stage (a flag per
+//    CTA counting finished push rounds, release/acquire at GPU scope): the
+//    rows it reads are complete, and no neighbour still reads the buffer it
+//    is about to write;
+//  - loads its window rows from the buffer (cp.async through L2 only: the
+//    non-coherent L1 could hold lines of two stages ago);
+//  - computes its entries from shared memory and writes them, with their
+//    mirrors, to the other buffer; then raises its flag.
+// Only neighbours wait for one another (no grid-wide barrier).  Every wait
+// is bounded: after spin_limit polls the error word gbar[2] is set to 1 and
+// later waits are skipped (results invalid, GRAPE_ETIMEOUT on the host), so
+// a fault cannot hang the GPU.
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -867,115 +882,65 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
 __device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
+__device__ __forceinline__ void cp_async_cg16(void *smem_dst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
 }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// returns false when the barrier gave up (error flag set)
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, long long limit,
-                                             int *abort_flag) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned gen = ld_acquire_gpu(&bar[1]);
-        const unsigned old = atom_add_acq_rel_gpu(&bar[0], 1u);
-        if (old == nblocks - 1) {
-            bar[0] = 0u;                        // ordered before the release below
-            st_release_gpu(&bar[1], gen + 1u);
-        } else {
-            long long it = 0;
-            while (ld_acquire_gpu(&bar[1]) == gen) {
-                if (ld_acquire_gpu(&bar[2]) != 0u || ++it > limit) {
-                    atomicExch(&bar[2], 1u);
-                    *abort_flag = 1;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-    }
-    __syncthreads();
-    return *abort_flag == 0;
-}
-
-template <class Num, bool REALJ>
-__device__ __forceinline__ typename Num::val lindblad_g_at(const typename Num::store_t *cur, int i,
-                                                           int j, int d, const PropTables &t,
-                                                           const typename Num::store_t *A,
-                                                           const typename Num::store_t *vL,
-                                                           const typename Num::store_t *vR,
-                                                           const double *uj) {
-    // same terms in the same order as lindblad_h_at (identical bits; a
-    // neighbour outside the matrix contributes an exact zero there)
-    const typename Num::val vz = Num::zero();
-    typename Num::acc w = band_terms<Num>(t, A, i, j, d,
-                    [&](int b) {
-                        const int r = i + t.off[b];
-                        return (r >= 0 && r < d) ? Num::load(__ldcg(&cur[(size_t)r * d + j])) : vz;
-                    },
-                    [&](int b) {
-                        const int c = j + t.off[b];
-                        return (c >= 0 && c < d) ? Num::load(__ldcg(&cur[(size_t)i * d + c])) : vz;
-                    });
-    w = Num::acc_minus_i(w);
-    Num::mac(w, diag_coef<Num, REALJ>(i, j, d, t, A, vL, vR, uj), Num::load(__ldcg(&cur[(size_t)i * d + j])));
-    auto jumps = [&](auto rate) {
-        constexpr bool RT = decltype(rate)::value;
-#pragma unroll 1
-        for (int q = 0; q < t.nt; ++q) {
-            if ((t.jdiag >> q) & 1) continue;
-            const int r = i + t.joL[q], c = j + t.joR[q];
-            if (r < 0 || r >= d || c < 0 || c >= d) continue;
-            const typename Num::val zv = Num::load(__ldcg(&cur[(size_t)r * d + c]));
-            if (REALJ) Num::mac_real(w, jump_real<Num, RT>(t, q, i, j, d, vL, vR, uj), zv);
-            else Num::mac(w, jump_cplx<Num, RT>(t, q, i, j, d, vL, vR, uj), zv);
-        }
-    };
-    if (!REALJ && t.jrate) jumps(std::true_type{});
-    else jumps(std::false_type{});
-    return Num::raw(w);
-}
-
-// Shared memory: xs, as [ce]; bands [2][nb][d]; vL, vR [nt][d];
-// ent [ce] (int4: row, column, state); 12 RK coefficients.
+// Shared memory: win [maxwin + 1] (the last entry stays zero); xs, as [cu];
+// D [cu] when p.fold; bands [nb][d] (one table: at a slice change it is
+// rebuilt at the start of the next stage, while no thread reads it); rc
+// [cu] (int2); 12 RK coefficients; jump coefficients [njt][cu] when
+// p.jcache; htab copy (ints); neighbour addresses [cu][ns + 1] (i16).  The
+// jump tables are read from global memory.
 template <class Num, bool REALJ>
 __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const PropArgs p) {
     using S = typename Num::store_t;
     using V = typename Num::val;
     using R = typename Num::real_t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int abort_flag;
+    __shared__ int s_err;
     const int d = p.d;
     const size_t d2 = (size_t)d * d;
+    const int NU = d * (d + 1) / 2;
     const int nbd = p.tab.nb * d;
-    S *xs = reinterpret_cast<S *>(smem_raw);
-    S *as = xs + p.ce;
-    S *bands = as + p.ce;
-    S *vL = bands + 2 * nbd;
-    S *vR = vL + p.tab.nt * d;
-    int4 *ent = reinterpret_cast<int4 *>(vR + p.tab.nt * d);
-    R *cg = reinterpret_cast<R *>(ent + p.ce);
+    const int wst = p.maxwin + 1;
+    S *win = reinterpret_cast<S *>(smem_raw);
+    S *xs = win + wst;
+    S *as = xs + p.cu;
+    S *Dt = as + p.cu;
+    S *bands = Dt + (p.fold ? p.cu : 0);
+    const S *vL = static_cast<const S *>(p.tab.vLs);
+    const S *vR = static_cast<const S *>(p.tab.vRs);
+    int2 *rc = reinterpret_cast<int2 *>(bands + nbd);
+    R *cg = reinterpret_cast<R *>(rc + p.cu);
     R *ca = cg + 4;
     R *cb = cg + 8;
-    S *gb0 = static_cast<S *>(p.gbuf);
-    S *gb1 = gb0 + (size_t)p.n_states * d2;
-    const S *x_in = static_cast<const S *>(p.x_in);
-    S *x_out = static_cast<S *>(p.x_out);
+    const int njt = p.tab.nt - __popc(p.tab.jdiag);
+    const bool jcache = REALJ && p.jcache;
+    R *jc = cg + 12;
+    int *tab = reinterpret_cast<int *>(jc + (jcache ? njt * p.cu : 0));
+    short *nbad = reinterpret_cast<short *>(tab + p.htab_len);
+    const int ns = 2 * p.tab.nb + p.tab.nt;
+    const int nstride = ns + 1;
+    const int nct = p.ncl;                       // CTAs per state
+    const int rank = blockIdx.x % nct;
+    const int state = blockIdx.x / nct;
+    S *gb0 = static_cast<S *>(p.gbuf) + (size_t)state * d2;
+    S *gb1 = static_cast<S *>(p.gbuf) + (size_t)(p.n_states + state) * d2;
+    const S *x_in = static_cast<const S *>(p.x_in) + (size_t)state * d2;
+    S *x_out = static_cast<S *>(p.x_out) + (size_t)state * d2;
     S *stage_store = static_cast<S *>(p.stage_store);
     S *bound_store = static_cast<S *>(p.bound_store);
-    const long long NU = (long long)d * (d + 1) / 2;
-    const long long E = NU * p.n_states;
-    const long long e0 = (long long)blockIdx.x * p.ce;
-    const long long e1 = min(E, e0 + p.ce);
+    unsigned *flags = p.gflag + (size_t)state * nct;   // finished push rounds per CTA of the state
+    const int *nbr = p.ntab + (size_t)rank * p.ntab_stride;   // [count, ranks...]
     const int nth = blockDim.x;
-    const unsigned nblocks = gridDim.x;
+    const int hb = p.hb;
 
-    if (threadIdx.x == 0) abort_flag = 0;
-    for (int i = threadIdx.x; i < p.tab.nt * d; i += nth) {
-        vL[i] = Num::store(Num::from_double2(__ldg(&p.tab.vL[i])));
-        vR[i] = Num::store(Num::from_double2(__ldg(&p.tab.vR[i])));
-    }
+    if (threadIdx.x == 0) s_err = 0;
+    for (int i = threadIdx.x; i < p.htab_len; i += nth) tab[i] = __ldg(&p.htab[i]);
+    const V vzero = Num::zero();
+    for (int i = threadIdx.x; i < wst; i += nth) win[i] = Num::store(vzero);
     if (threadIdx.x < 4) {
         cg[threadIdx.x] = Num::real_const(p.g[threadIdx.x]);
         ca[threadIdx.x] = Num::real_const(p.a[threadIdx.x]);
@@ -986,53 +951,128 @@ __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const Pro
     if (nsub <= 0) n_first = p.sub_begin;
     int jcur = (int)(n_first / p.n_rk);
     build_bands<Num>(bands, p, jcur);
-    __syncthreads();   // coefficients, tables and bands are read below
-    for (long long e = e0 + threadIdx.x; e < e1; e += nth) {
-        const int st = (int)(e / NU);
-        const long long u = e - (long long)st * NU;
+    __syncthreads();
+    const int u0 = tab[GRAPE_HTAB_CTA(rank) + 0], u1 = tab[GRAPE_HTAB_CTA(rank) + 1];
+    const int wr0 = tab[GRAPE_HTAB_CTA(rank) + 2], nrows = tab[GRAPE_HTAB_CTA(rank) + 3];
+    const int *ofs = tab + tab[GRAPE_HTAB_LISTS(nct) + rank];
+    for (int u = u0 + threadIdx.x; u < u1; u += nth) {
         const double b2 = 2.0 * d + 1.0;
         int i = (int)floor(0.5 * (b2 - sqrt(b2 * b2 - 8.0 * (double)u)));
         i = max(0, min(d - 1, i));
         while (i > 0 && (long long)i * d - (long long)i * (i - 1) / 2 > u) --i;
         while (i + 1 < d && (long long)(i + 1) * d - (long long)(i + 1) * i / 2 <= u) ++i;
         const int j = i + (int)(u - ((long long)i * d - (long long)i * (i - 1) / 2));
-        ent[e - e0] = make_int4(i, j, st, (int)u);
-        const V x = Num::load(x_in[(size_t)st * d2 + (size_t)i * d + j]);
-        xs[e - e0] = Num::store(x);
-        store_herm<Num>(gb0 + (size_t)st * d2, d, i, j, Num::store(Num::scale(cg[0], x)));
+        rc[u - u0] = make_int2(i, j);
+        short *na = nbad + (size_t)(u - u0) * nstride;
+        const int own = ofs[i - wr0] + (j - cs_of(i, hb));
+        na[ns] = (short)own;
+        const short zs = (short)p.maxwin;
+        for (int b = 0; b < p.tab.nb; ++b) {
+            const int o = p.tab.off[b], r = i + o, c = j + o;
+            na[2 * b] = (r >= 0 && r < d) ? (short)(ofs[r - wr0] + (j - cs_of(r, hb))) : zs;
+            na[2 * b + 1] = (c >= 0 && c < d) ? (short)(own + o) : zs;
+        }
+        for (int q = 0; q < p.tab.nt; ++q) {
+            const int r = i + p.tab.joL[q], c = j + p.tab.joR[q];
+            na[2 * p.tab.nb + q] =
+                (r >= 0 && r < d && c >= 0 && c < d) ? (short)(ofs[r - wr0] + (c - cs_of(r, hb))) : zs;
+        }
+        if (jcache) {
+            int qq = 0;
+            for (int q = 0; q < p.tab.nt; ++q) {
+                if ((p.tab.jdiag >> q) & 1) continue;
+                jc[qq * p.cu + (u - u0)] = jump_real<Num, false>(p.tab, q, i, j, d, vL, vR, nullptr);
+                ++qq;
+            }
+        }
     }
-    if (!grid_barrier(p.gbar, nblocks, p.spin_limit, &abort_flag)) return;
+    // the initial stage input (push round 1, buffer 0)
+    for (int u = u0 + threadIdx.x; u < u1; u += nth) {
+        const int2 ij = rc[u - u0];
+        const V x = Num::load(x_in[(size_t)ij.x * d + ij.y]);
+        xs[u - u0] = Num::store(x);
+        store_herm<Num>(gb0, d, ij.x, ij.y, Num::store(Num::scale(cg[0], x)));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release_gpu(&flags[rank], 1u);
+    }
+    // waits until every neighbour has finished `round` push rounds (thread 0),
+    // then loads the window rows from `src` (the stage's input buffer)
+    const int nnb = nbr[0];
+    int band_next = -1;                          // slice whose bands are rebuilt at the next stage
+    auto wait_and_load = [&](unsigned round, const S *src) {
+        if (threadIdx.x == 0 && !s_err && p.spin_limit <= 0) {   // a limit of zero polls gives up at once
+            atomicExch(&p.gbar[2], 1u);
+            s_err = 1;
+        }
+        __syncthreads();                         // s_err as thread 0 left it
+        if (threadIdx.x < nnb && !s_err) {       // one thread per neighbour, all at once
+            const unsigned *f = &flags[nbr[1 + threadIdx.x]];
+            long long it = 0;
+            while (ld_acquire_gpu(f) < round) {
+                if (ld_acquire_gpu(&p.gbar[2]) != 0u || ++it > p.spin_limit) {
+                    atomicExch(&p.gbar[2], 1u);
+                    s_err = 1;
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        if (band_next >= 0) {                    // no thread reads the table now
+            build_bands<Num>(bands, p, band_next);
+            band_next = -1;
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = nth >> 5;
+        for (int lr = warp; lr < nrows; lr += nwarps) {
+            const int r = wr0 + lr;
+            const int c0 = cs_of(r, hb), n = d - c0;
+            S *dst = win + ofs[lr];
+            const S *srow = src + (size_t)r * d + c0;
+            for (int c = lane; c < n; c += 32) cp_async_cg16(dst + c, srow + c);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    };
 
     const bool unit_g = (p.g[1] == 1.0 && p.g[2] == 1.0 && p.g[3] == 1.0);
-    int tb = 0;
+    unsigned round = 1;                          // push rounds finished by this CTA
+    bool dfresh = true;
     for (long long it = 0; it < nsub; ++it) {
         const long long n = p.reverse ? p.sub_end - 1 - it : p.sub_begin + it;
         const long long tidx = p.reverse ? n + 1 : n;
         if (bound_store && ((tidx - p.sub_begin) % p.bound_step) == 0) {
-            S *dst = bound_store + (size_t)((tidx - p.sub_begin) / p.bound_step) * p.n_states * d2;
-            for (long long e = e0 + threadIdx.x; e < e1; e += nth) {
-                const int4 q = ent[e - e0];
-                store_herm<Num>(dst + (size_t)q.z * d2, d, q.x, q.y, xs[e - e0]);
-            }
+            S *dst = bound_store + ((size_t)((tidx - p.sub_begin) / p.bound_step) * p.n_states + state) * d2;
+            for (int u = u0 + threadIdx.x; u < u1; u += nth)
+                store_herm<Num>(dst, d, rc[u - u0].x, rc[u - u0].y, xs[u - u0]);
         }
-        const S *A = bands + tb * nbd;
+        const S *A = bands;
+        const double *uj = p.u + (size_t)jcur * p.R;
         bool flip = false;
 #pragma unroll 1
         for (int s = 0; s < 4; ++s) {
-            const S *cur = (s & 1) ? gb1 : gb0;
-            S *nxt = (s & 1) ? gb0 : gb1;
-            S *stg = nullptr;                    // packed stage storage (all states)
+            wait_and_load(round, (round & 1) ? gb0 : gb1);   // round r filled buffer (r - 1) mod 2
+            S *nxt = (round & 1) ? gb1 : gb0;
+            S *st = nullptr;
             if (stage_store)
-                stg = stage_store + (size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states * NU;
+                st = stage_store + ((size_t)((n - p.sub_begin) * 4 + p.store_map[s]) * p.n_states + state) * NU;
             const R as_ = ca[s];
 #pragma unroll 1
-            for (long long e = e0 + threadIdx.x; e < e1; e += nth) {
-                const int li = (int)(e - e0);
-                const int4 q = ent[li];
-                const S *cs = cur + (size_t)q.z * d2;
-                const V w = lindblad_g_at<Num, REALJ>(cs, q.x, q.y, d, p.tab, A, vL, vR,
-                                                      p.u + (size_t)jcur * p.R);
-                if (stg) stg[(size_t)q.z * NU + q.w] = __ldcg(&cs[(size_t)q.x * d + q.y]);
+            for (int u = u0 + threadIdx.x; u < u1; u += nth) {
+                const int li = u - u0;
+                const int2 ij = rc[li];
+                const short *na = nbad + (size_t)li * nstride;
+                if (st) st[u] = win[na[ns]];
+                V dij;
+                if (p.fold) {
+                    if (s == 0 && dfresh) Dt[li] = Num::store(diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR, uj));
+                    dij = Num::load(Dt[li]);
+                } else {
+                    dij = diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR, uj);
+                }
+                const V w = lindblad_h_at<Num, REALJ>(win, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij, uj,
+                                                      jcache ? jc + li : nullptr, p.cu);
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
                 V z;
@@ -1040,37 +1080,38 @@ __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const Pro
                     as[li] = Num::store(acc);
                     z = unit_g ? Num::axpy(cb[s + 1], w, x) : Num::lin2(cg[s + 1], x, cb[s + 1], w);
                 } else {
-                    const V nx = with_source<Num>(p, n, q.x, q.y, acc);
+                    const V nx = with_source<Num>(p, n, ij.x, ij.y, acc);
                     xs[li] = Num::store(nx);
                     z = Num::scale(cg[0], nx);
                 }
-                store_herm<Num>(nxt + (size_t)q.z * d2, d, q.x, q.y, Num::store(z));
+                store_herm<Num>(nxt, d, ij.x, ij.y, Num::store(z));
             }
             if (s == 3 && it + 1 < nsub) {
                 const long long nn = p.reverse ? n - 1 : n + 1;
                 const int jn = (int)(nn / p.n_rk);
                 if (jn != jcur) {
-                    build_bands<Num>(bands + (tb ^ 1) * nbd, p, jn);
+                    band_next = jn;
                     jcur = jn;
                     flip = true;
                 }
             }
-            if (!grid_barrier(p.gbar, nblocks, p.spin_limit, &abort_flag)) return;
+            __syncthreads();
+            ++round;
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release_gpu(&flags[rank], round);
+            }
         }
-        if (flip) tb ^= 1;
+        dfresh = flip;
     }
     const long long tend = p.reverse ? p.sub_begin : p.sub_end;
     if (bound_store && ((tend - p.sub_begin) % p.bound_step) == 0) {
-        S *dst = bound_store + (size_t)((tend - p.sub_begin) / p.bound_step) * p.n_states * d2;
-        for (long long e = e0 + threadIdx.x; e < e1; e += nth) {
-            const int4 q = ent[e - e0];
-            store_herm<Num>(dst + (size_t)q.z * d2, d, q.x, q.y, xs[e - e0]);
-        }
+        S *dst = bound_store + ((size_t)((tend - p.sub_begin) / p.bound_step) * p.n_states + state) * d2;
+        for (int u = u0 + threadIdx.x; u < u1; u += nth)
+            store_herm<Num>(dst, d, rc[u - u0].x, rc[u - u0].y, xs[u - u0]);
     }
-    for (long long e = e0 + threadIdx.x; e < e1; e += nth) {
-        const int4 q = ent[e - e0];
-        store_herm<Num>(x_out + (size_t)q.z * d2, d, q.x, q.y, xs[e - e0]);
-    }
+    for (int u = u0 + threadIdx.x; u < u1; u += nth)
+        store_herm<Num>(x_out, d, rc[u - u0].x, rc[u - u0].y, xs[u - u0]);
 }
 
 template <class Num>
