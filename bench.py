@@ -63,7 +63,7 @@ def parse():
                     choices=["d120", "d20", "d120f", "d120p", "sweep", "batch256", "d600", "serve", "peaks"])
     ap.add_argument("--scale", type=float, default=None,
                     help="slice-count multiplier of the batch256/serve/d600 workloads")
-    ap.add_argument("--jobs", type=int, default=64, help="serve: jobs in the trace")
+    ap.add_argument("--jobs", type=int, default=32, help="serve: jobs in the trace")
     ap.add_argument("--sample", type=int, default=256,
                     help="batch256: problems timed one at a time (256 = all, no scaling)")
     ap.add_argument("--lanes", type=int, default=0, help="batch256: concurrent lanes (0 = automatic)")
@@ -596,10 +596,12 @@ def run_sweep(args):
 def serve_trace(n_jobs, scale, rate, seed=1609):
     """Seeded trace: (arrival time, workload); 88% batch-distribution problems,
     10% d=120 / N_t=2000 problems, 2% d=300 / N_t=10000 problems (slice
-    counts times `scale`)."""
+    counts times `scale`).  The job mix comes from one seeded stream and the
+    Poisson arrival times (mean rate `rate`) from another, so a trace at a
+    different rate has the same jobs in the same order."""
     import workloads
     rng = np.random.default_rng(seed)
-    t = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
+    t = np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / rate, size=n_jobs))
     out = []
     for k in range(n_jobs):
         r = rng.uniform()
@@ -654,15 +656,17 @@ def run_serve_once(trace, max_slots):
 
 
 def run_serve(args):
-    scale = 0.1 if args.scale is None else args.scale
+    scale = 1.0 if args.scale is None else args.scale
     trace = serve_trace(args.jobs, scale, 50.0)
     batched = run_serve_once(trace, 24)
     serial = run_serve_once(trace, 1)
-    trace08 = serve_trace(args.jobs, scale, 0.8 * batched["jobs_per_s"], seed=1610)
+    # the same jobs arriving at 0.8x the measured capacity
+    trace08 = serve_trace(args.jobs, scale, 0.8 * batched["jobs_per_s"])
     at08 = run_serve_once(trace08, 24)
     print(json.dumps(_base_line(args, "serve", batched["jobs_per_s"], "jobs/s",
                                 1000 * batched["makespan_s"], {
         "config": {"workload": "serve", "jobs": args.jobs, "arrivals": "Poisson 50 jobs/s",
+                   "mix_by_job": [f"{w.name}:d{w.d}:Nt{w.n_slices}" for _, w in trace],
                    "slice_scale": scale, "iterations": 50, "box": 5.0,
                    "mix": "88% batch-distribution, 10% d=120/N_t=2000, 2% d=300/N_t=10000 "
                           "(slice counts x scale)"},

@@ -1424,7 +1424,7 @@ __global__ void __launch_bounds__(256) trace_packed_fast_kernel(const TraceArgs 
         }
         const S *Yp = Yb + (row_base + state) * NU;
         const S *Kp = Kb + (row_base + state) * NU;
-#pragma unroll 2
+#pragma unroll 4
         for (long long qs = 0; qs < pps; ++qs) {
             const size_t moff = (size_t)qs * pstride;
             const V y = Num::load(Yp[moff + u]);
