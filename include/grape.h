@@ -199,10 +199,12 @@ grape_status grape_problem_set_tile(grape_problem_t problem, int32_t cluster, in
 grape_status grape_problem_kernel(grape_problem_t problem, int32_t *kind);
 
 /* Waits for the device and reports whether a bounded wait of the
- * propagation kernels gave up since the last check (GRAPE_ETIMEOUT; the
- * results of that call are invalid): a grid barrier of the grid kernel, or
- * a window wait of the Hermitian cluster kernel (which waits on mbarriers
- * for the values its peers push into its shared memory).  The flag is
+ * problem's kernels gave up since the last check (GRAPE_ETIMEOUT; the
+ * results of that call are invalid): a grid barrier of the grid kernel, a
+ * window wait of the Hermitian cluster kernel (which waits on mbarriers
+ * for the values its peers push into its shared memory), or a copy wait of
+ * the staged gradient-trace kernel (which waits on mbarriers for the bulk
+ * copies of its operands into shared memory).  The flag is
  * cleared by the report.  Calls that return results to host memory do this
  * check themselves. */
 grape_status grape_problem_status(grape_problem_t problem);
@@ -238,10 +240,11 @@ grape_status grape_phase_times(grape_problem_t problem, double ms[4], int32_t la
  * every buffer is written before it is read), so calls whose GPU work
  * overlaps - on two streams, or from two threads - race and give wrong
  * results: serialise them.  Results equal those of grape_gradient bit for
- * bit (the traces are split and summed in the same order).  Grid-kernel
- * problems (grape_problem_kernel == 2): this call cannot wait for the
- * device, so after the stream has completed call grape_problem_status; on
- * GRAPE_ETIMEOUT a grid barrier gave up and F and grad are invalid. */
+ * bit (the traces are split and summed in the same order).  This call
+ * cannot wait for the device, so after the stream has completed call
+ * grape_problem_status: on GRAPE_ETIMEOUT a bounded wait of one of the
+ * kernels (grid barrier, window wait, trace copy wait) gave up and F and
+ * grad are invalid. */
 grape_status grape_gradient_static(grape_problem_t problem, const double *u, double *F,
                                    double *grad, void *stream);
 

@@ -442,10 +442,6 @@ grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
     };
     double2 *p;
     grape_status s;
-    if ((s = upload(P, cvt(h.A0), &p)) != GRAPE_OK) return s;
-    t->A0 = p;
-    if ((s = upload(P, cvt(h.Ak), &p)) != GRAPE_OK) return s;
-    t->Ak = p;
     if ((s = upload(P, cvt(h.vL), &p)) != GRAPE_OK) return s;
     t->vL = p;
     if ((s = upload(P, cvt(h.vR), &p)) != GRAPE_OK) return s;
@@ -455,6 +451,10 @@ grape_status upload_dir(grape_problem *P, const HostDir &h, PropTables *t) {
         for (size_t i = 0; i < v.size(); ++i) o[i] = encode(P, v[i]);
         return o;
     };
+    if ((s = upload(P, enc(h.A0), &p)) != GRAPE_OK) return s;
+    t->A0s = p;
+    if ((s = upload(P, enc(h.Ak), &p)) != GRAPE_OK) return s;
+    t->Aks = p;
     if ((s = upload(P, enc(h.vL), &p)) != GRAPE_OK) return s;
     t->vLs = p;
     if ((s = upload(P, enc(h.vR), &p)) != GRAPE_OK) return s;
@@ -998,6 +998,131 @@ void trace_layout(const grape_problem *P, TraceArgs *t) {
     t->nsplit = (int)std::max<long long>(1, (npairs + per - 1) / per);
 }
 
+// Tables of the packed trace kernels: the row and column of every packed
+// entry, and for the staged kernel (no rate-controlled dissipators, at most 4
+// distinct control offsets): per 256-entry block of
+// the packed triangle, the runs of packed K positions its entries'
+// neighbours (i+o, j) and (i, j+o) fall in (gaps of up to 8 entries are
+// copied along, so one run can span the end of a row and the start of the
+// next), and per entry the neighbours' indices in the block's K buffer.
+// Left off (the fast kernel runs) when GRAPE_TRACE=fast or the buffers do
+// not fit shared memory.
+grape_status trace_tiles(grape_problem *P, TraceArgs *t) {
+    t->err = P->d_gbar + 2;
+    t->tile = 0;
+    if (!t->packed) return GRAPE_OK;
+    const int d = P->d;
+    if (d > 65535) return fail(GRAPE_EINVAL, "d above 65535 (16-bit row and column indices)");
+    const long long NU = (long long)d * (d + 1) / 2;
+    // row and column of every packed entry (all packed trace kernels)
+    std::vector<unsigned> ij((size_t)NU);
+    {
+        size_t u = 0;
+        for (int i = 0; i < d; ++i)
+            for (int j = i; j < d; ++j) ij[u++] = (unsigned)i | ((unsigned)j << 16);
+    }
+    {
+        unsigned *dij = nullptr;
+        const grape_status st = upload(P, ij, &dij);
+        if (st != GRAPE_OK) return st;
+        t->tij = dij;
+    }
+    if (t->nst != 0 || t->ndo <= 0 || t->ndo > 4) return GRAPE_OK;
+    if (const char *env = std::getenv("GRAPE_TRACE"))
+        if (std::string(env) == "fast") return GRAPE_OK;
+    auto pk = [d](long long r, long long c) { return r * d - r * (r - 1) / 2 + (c - r); };
+    const long long nblk = (NU + 255) / 256;
+    std::vector<int4> blk((size_t)nblk), runs;
+    std::vector<uint4> nb((size_t)NU);
+    std::vector<long long> pos;
+    std::vector<long long> rs, rl, ro;                       // the block's runs: start, length, offset
+    int kcap = 0;
+    for (long long b = 0; b < nblk; ++b) {
+        const long long u0 = b * 256, u1 = std::min(NU, u0 + 256);
+        // stored position of neighbour `which` (0: (i+o, j), 1: (i, j+o)) of
+        // entry u at offset index oi, -1 when outside; *cj: the mirror is stored
+        auto nbpos = [&](long long u, int oi, int which, bool *cj) -> long long {
+            const int i = (int)(ij[u] & 0xffffu), j = (int)(ij[u] >> 16);
+            const int o = t->do_off[oi];
+            *cj = false;
+            if (which == 0) {
+                const int r1 = i + o;
+                if (r1 < 0 || r1 >= d) return -1;
+                *cj = r1 > j;
+                return *cj ? pk(j, r1) : pk(r1, j);
+            }
+            const int c2 = j + o;
+            if (i >= j || c2 < 0 || c2 >= d) return -1;
+            *cj = c2 < i;
+            return *cj ? pk(c2, i) : pk(i, c2);
+        };
+        pos.clear();
+        for (long long u = u0; u < u1; ++u)
+            for (int oi = 0; oi < t->ndo; ++oi)
+                for (int w = 0; w < 2; ++w) {
+                    bool cj;
+                    const long long x = nbpos(u, oi, w, &cj);
+                    if (x >= 0) pos.push_back(x);
+                }
+        std::sort(pos.begin(), pos.end());
+        pos.erase(std::unique(pos.begin(), pos.end()), pos.end());
+        rs.clear();
+        rl.clear();
+        ro.clear();
+        long long klen = 0;
+        for (long long x : pos) {
+            if (!rs.empty() && x - (rs.back() + rl.back()) <= 8) {
+                klen += x + 1 - (rs.back() + rl.back());
+                rl.back() = x - rs.back() + 1;
+            } else {
+                rs.push_back(x);
+                rl.push_back(1);
+                ro.push_back(klen);
+                klen += 1;
+            }
+        }
+        if (klen > 32767) return GRAPE_OK;                    // 15-bit buffer indices
+        kcap = std::max(kcap, (int)klen);
+        blk[(size_t)b] = make_int4((int)runs.size(), (int)rs.size(), (int)klen, 0);
+        for (size_t r = 0; r < rs.size(); ++r) runs.push_back(make_int4((int)rs[r], (int)rl[r], (int)ro[r], 0));
+        for (long long u = u0; u < u1; ++u) {
+            unsigned w16[8];
+            for (int k = 0; k < 8; ++k) {
+                w16[k] = 0xffffu;
+                const int oi = k >> 1;
+                if (oi >= t->ndo) continue;
+                bool cj;
+                const long long x = nbpos(u, oi, k & 1, &cj);
+                if (x < 0) continue;
+                const size_t r = (size_t)(std::upper_bound(rs.begin(), rs.end(), x) - rs.begin()) - 1;
+                w16[k] = (unsigned)(ro[r] + (x - rs[r])) | (cj ? 0x8000u : 0u);
+            }
+            nb[(size_t)u] = make_uint4(w16[0] | w16[1] << 16, w16[2] | w16[3] << 16, w16[4] | w16[5] << 16,
+                                       w16[6] | w16[7] << 16);
+        }
+    }
+    // buffers: as many (2 to 4) as keep two CTAs per SM, else two at one CTA per SM
+    const size_t stage = (size_t)(256 + kcap) * 16;
+    int nbuf = 0;
+    for (int n = 4; n >= 2 && !nbuf; --n)
+        if (64 + n * stage <= 100 * 1024) nbuf = n;
+    if (!nbuf && 64 + 2 * stage + 4096 <= (size_t)max_smem_optin(P)) nbuf = 2;
+    if (!nbuf) return GRAPE_OK;
+    int4 *dblk = nullptr, *drun = nullptr;
+    uint4 *dnb = nullptr;
+    grape_status st;
+    if ((st = upload(P, blk, &dblk)) != GRAPE_OK) return st;
+    if ((st = upload(P, runs, &drun)) != GRAPE_OK) return st;
+    if ((st = upload(P, nb, &dnb)) != GRAPE_OK) return st;
+    t->tblk = dblk;
+    t->trun = drun;
+    t->tnb = dnb;
+    t->kcap = kcap;
+    t->nbuf = nbuf;
+    t->tile = 1;
+    return GRAPE_OK;
+}
+
 // largest segment (halving from the whole problem) whose storage fits the budget
 long long seg_for_budget(const grape_problem *P, size_t budget) {
     long long seg = P->n_slices;
@@ -1488,18 +1613,26 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
         if ((st = upload(P, r, &P->d_rho0)) != GRAPE_OK) return bail(st);
         if ((st = upload(P, g2, &P->d_sigma)) != GRAPE_OK) return bail(st);
     }
-    double2 *cb = nullptr;
-    if ((st = upload(P, cbv, &cb)) != GRAPE_OK) return bail(st);
-    tr.cb_val = cb;
+    // the kernels read the tables in their storage format (no conversion
+    // from FP64 in the double-float build)
+    auto to_store = [&](const std::vector<double2> &v) {
+        std::vector<double2> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = encode(P, cplx(v[i].x, v[i].y));
+        return o;
+    };
+    double2 *cbs = nullptr;
+    if ((st = upload(P, to_store(cbv), &cbs)) != GRAPE_OK) return bail(st);
+    tr.cb_s = cbs;
     if (tr.nst > 0) {
-        double2 *a = nullptr, *b = nullptr;
-        if ((st = upload(P, stv_l, &a)) != GRAPE_OK) return bail(st);
-        if ((st = upload(P, stv_r, &b)) != GRAPE_OK) return bail(st);
-        tr.st_vL = a;
-        tr.st_vR = b;
+        double2 *as = nullptr, *bs = nullptr;
+        if ((st = upload(P, to_store(stv_l), &as)) != GRAPE_OK) return bail(st);
+        if ((st = upload(P, to_store(stv_r), &bs)) != GRAPE_OK) return bail(st);
+        tr.st_vLs = as;
+        tr.st_vRs = bs;
     }
     P->trace = tr;
     trace_layout(P, &P->trace);
+    if ((st = trace_tiles(P, &P->trace)) != GRAPE_OK) return bail(st);
 
     P->d_x = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
     P->d_mu = static_cast<double2 *>(P->alloc(d2 * P->ns * sizeof(double2)));
@@ -1602,9 +1735,9 @@ grape_status grape_problem_status(grape_problem_t P) {
     if (flag[2] != 0u) {
         GRAPE_CUDA_TRY(cudaMemset(P->d_gbar, 0, 4 * sizeof(unsigned)));
         GRAPE_CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
-        return fail(GRAPE_ETIMEOUT, flag[2] == 2u
-                                        ? "a window wait of the cluster propagation kernel gave up waiting"
-                                        : "a grid barrier of the propagation kernel gave up waiting");
+        return fail(GRAPE_ETIMEOUT, flag[2] == 3u   ? "a copy wait of the staged trace kernel gave up waiting"
+                                    : flag[2] == 2u ? "a window wait of the cluster propagation kernel gave up waiting"
+                                                    : "a grid barrier of the propagation kernel gave up waiting");
     }
     return GRAPE_OK;
 }

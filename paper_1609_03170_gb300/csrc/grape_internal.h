@@ -32,8 +32,8 @@ struct PropTables {
     int jdiag;                  // bit t set: jump term t has oL_t = oR_t = 0
     int jrate;                  // bit t set: jump term t is scaled by a control (its rate is a control)
     int jctl[GRAPE_MAXT];       // that control, -1: fixed
-    const double2 *A0;          // [nb][d]
-    const double2 *Ak;          // [R][nb][d]
+    const void *A0s;            // [nb][d], the kernels' storage format
+    const void *Aks;            // [R][nb][d], the kernels' storage format
     const double2 *vL;          // [nt][d]
     const double2 *vR;          // [nt][d]
     const void *vLs, *vRs;      // the same in the kernels' storage format (read from global
@@ -119,7 +119,7 @@ struct TraceArgs {
     int cb_k[GRAPE_MAXCB];      // control of band entry c
     int cb_do[GRAPE_MAXCB];     // distinct-offset index of band entry c
     int do_off[GRAPE_MAXDO];    // distinct offsets
-    const double2 *cb_val;      // [ncb][d]  Hk_b[m]
+    const void *cb_s;           // [ncb][d]  Hk_b[m], storage format of the number type
     const void *K;              // adjoint-side matrices (storage format)
     const void *Y;              // forward-side matrices (storage format)
     long long npairs;           // matrices per output row
@@ -139,7 +139,18 @@ struct TraceArgs {
     int nst;
     int st_k[GRAPE_MAXST];
     int st_oL[GRAPE_MAXST], st_oR[GRAPE_MAXST];
-    const double2 *st_vL, *st_vR;   // [nst][d]
+    const void *st_vLs, *st_vRs;    // [nst][d], storage format
+    // staged trace (packed storage, nst == 0, ndo <= 4): per 256-entry block
+    // b of the packed triangle, the runs of K its entries' neighbours fall in
+    // are copied to shared memory with Y's block, per pair, into nbuf buffers
+    // of 256 + kcap entries
+    int tile, kcap, nbuf;
+    const int4 *tblk;               // [blocks]: first run, run count, K entries copied
+    const int4 *trun;               // runs: packed start, length, offset in the buffer's K part
+    const uint4 *tnb;               // [NU]: per distinct offset (i+o, j) and (i, j+o) as 16-bit
+                                    // buffer indices (bit 15: conjugate of the mirror; 0xffff: none)
+    const unsigned *tij;            // [NU]: i | j << 16 of packed entry u
+    unsigned *err;                  // error word: 3 when a copy wait gave up
 };
 
 // Launchers, one set per number type: _f64 native FP64, _df double-float.

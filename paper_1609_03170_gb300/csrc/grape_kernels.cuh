@@ -72,21 +72,26 @@ __device__ __forceinline__ void st_remote(uint32_t addr, float4 v) {
                  : "memory");
 }
 
-// A(u_j) = A0 + sum_k u_k(j) Ak (FP64), stored in the number type.
+// A(u_j) = A0 + sum_k u_k(j) Ak in the number type, from tables in its
+// storage format: in the double-float build every operation runs on the FP32
+// pipes (the slice's R controls are split into float pairs once per CTA, in
+// shared memory).  Called by every thread of the CTA (it holds a barrier).
 template <class Num>
 __device__ __forceinline__ void build_bands(typename Num::store_t *dst, const PropArgs &p,
                                             int slice) {
+    using S = typename Num::store_t;
+    using R = typename Num::real_t;
+    __shared__ R ucv[GRAPE_MAXR];
     const int nbd = p.tab.nb * p.d;
     const double *uj = p.u + (size_t)slice * p.R;
+    if (threadIdx.x < p.R) ucv[threadIdx.x] = Num::real_const(__ldg(&uj[threadIdx.x]));
+    __syncthreads();
+    const S *A0 = static_cast<const S *>(p.tab.A0s);
+    const S *Ak = static_cast<const S *>(p.tab.Aks);
     for (int idx = threadIdx.x; idx < nbd; idx += blockDim.x) {
-        double2 v = __ldg(&p.tab.A0[idx]);
-        for (int k = 0; k < p.R; ++k) {
-            const double uk = __ldg(&uj[k]);
-            const double2 h = __ldg(&p.tab.Ak[(size_t)k * nbd + idx]);
-            v.x = fma(uk, h.x, v.x);
-            v.y = fma(uk, h.y, v.y);
-        }
-        dst[idx] = Num::store(Num::from_double2(v));
+        typename Num::val v = Num::load(A0[idx]);
+        for (int k = 0; k < p.R; ++k) v = Num::axpy(ucv[k], Num::load(Ak[(size_t)k * nbd + idx]), v);
+        dst[idx] = Num::store(v);
     }
 }
 
@@ -503,6 +508,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long l
         if (done) return true;
         if (clock64() - t0 > cycles) return false;
     }
+}
+// bulk asynchronous copy (TMA engine) of `bytes` from global memory into the
+// CTA's shared memory, counted on its mbarrier; both addresses and the size
+// are multiples of 16 bytes
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
 }
 // the two halves of the cluster barrier without memory ordering: they only
 // keep a CTA from overwriting a window a peer may still be reading
@@ -1114,6 +1127,68 @@ __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const Pro
         store_herm<Num>(x_out, d, rc[u - u0].x, rc[u - u0].y, xs[u - u0]);
 }
 
+// Real-part arithmetic of the trace epilogue in the kernel's own number
+// type (double-float on the FP32 pipes, or FP64): the sums never touch the
+// FP64 pipe in the double-float build.
+__device__ __forceinline__ grape_num::ff r_add(grape_num::ff a, grape_num::ff b) { return grape_num::ff_sum(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return a + b; }
+__device__ __forceinline__ grape_num::ff r_m2(grape_num::ff a) { return {-2.0f * a.h, -2.0f * a.l}; }
+__device__ __forceinline__ double r_m2(double a) { return -2.0 * a; }
+__device__ __forceinline__ grape_num::ff r_shfl_down(grape_num::ff a, int sh) {
+    return {__shfl_down_sync(0xffffffffu, a.h, sh), __shfl_down_sync(0xffffffffu, a.l, sh)};
+}
+__device__ __forceinline__ double r_shfl_down(double a, int sh) { return __shfl_down_sync(0xffffffffu, a, sh); }
+__device__ __forceinline__ double r_double(grape_num::ff a) { return grape_num::ff_to_double(a); }
+__device__ __forceinline__ double r_double(double a) { return a; }
+__device__ __forceinline__ void r_zero(grape_num::ff &a) { a = {0.0f, 0.0f}; }
+__device__ __forceinline__ void r_zero(double &a) { a = 0.0; }
+
+// Epilogue of the trace kernels: per control k, each thread forms
+// -2 Im(sum of its band sums of k, in band order) + Re(sum of its sandwich
+// sums of k) (ST), the CTA adds the threads by warp shuffles and then the
+// warps in index order, all in the number type, and thread k writes
+// weight * sum to G (one split) or to its split's partial.  The order is
+// fixed by the thread layout alone, so no bit depends on the launch
+// grouping or the propagation tile.
+template <class Num, bool ST>
+__device__ __forceinline__ void trace_store(const TraceArgs &p, typename Num::acc (&Z)[GRAPE_MAXCB],
+                                            typename Num::acc (&Zs)[GRAPE_MAXST], int row, int split) {
+    using R = typename Num::real_t;
+    __shared__ R redk[GRAPE_MAXR][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < GRAPE_MAXR; ++k) {
+        if (k >= p.R) break;
+        R t;
+        r_zero(t);
+#pragma unroll
+        for (int c = 0; c < GRAPE_MAXCB; ++c)
+            if (c < p.ncb && p.cb_k[c] == k) t = r_add(t, Num::done(Z[c]).im);
+        R r = r_m2(t);
+        if constexpr (ST) {
+            R w;
+            r_zero(w);
+#pragma unroll
+            for (int q = 0; q < GRAPE_MAXST; ++q)
+                if (q < p.nst && p.st_k[q] == k) w = r_add(w, Num::done(Zs[q]).re);
+            r = r_add(r, w);
+        }
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) r = r_add(r, r_shfl_down(r, sh));
+        if (lane == 0) redk[k][warp] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < p.R) {
+        const int k = threadIdx.x;
+        R sum = redk[k][0];
+        for (int w = 1; w < nwarps; ++w) sum = r_add(sum, redk[k][w]);
+        const double v = p.weight * r_double(sum);
+        const int nsplit = max(1, p.nsplit);
+        if (nsplit == 1) p.G[(size_t)row * p.R + k] = v;
+        else p.part[((size_t)row * nsplit + split) * p.R + k] = v;
+    }
+}
+
 template <class Num>
 __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
     using S = typename Num::store_t;
@@ -1129,10 +1204,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
     S *svL = hv + p.ncb * d;                         // [nst][d] sandwich tables
     S *svR = svL + p.nst * d;
     for (int i = threadIdx.x; i < p.ncb * d; i += blockDim.x)
-        hv[i] = Num::store(Num::from_double2(__ldg(&p.cb_val[i])));
+        hv[i] = static_cast<const S *>(p.cb_s)[i];
     for (int i = threadIdx.x; i < p.nst * d; i += blockDim.x) {
-        svL[i] = Num::store(Num::from_double2(__ldg(&p.st_vL[i])));
-        svR[i] = Num::store(Num::from_double2(__ldg(&p.st_vR[i])));
+        svL[i] = static_cast<const S *>(p.st_vLs)[i];
+        svR[i] = static_cast<const S *>(p.st_vRs)[i];
     }
     __syncthreads();
     typename Num::acc Z[GRAPE_MAXCB];                // lane-private, in the number type
@@ -1183,46 +1258,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
             }
         }
     }
-    // deterministic reduction: warp shuffles, then warps in index order (FP64)
-    __shared__ double red[GRAPE_MAXCB][32];
-    __shared__ double reds[GRAPE_MAXST][32];
-#pragma unroll
-    for (int c = 0; c < GRAPE_MAXCB; ++c) {
-        double v = Num::to_double2(Num::done(Z[c])).y;
-#pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
-        if (lane == 0) red[c][warp] = v;
-    }
-#pragma unroll
-    for (int t = 0; t < GRAPE_MAXST; ++t) {
-        double v = Num::to_double2(Num::done(Zs[t])).x;   // real part: Re Tr(kb gamma c y c^+)
-#pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
-        if (lane == 0) reds[t][warp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < GRAPE_MAXR) {
-        const int k = threadIdx.x;
-        if (k < p.R) {
-            double s = 0.0;
-            for (int c = 0; c < p.ncb; ++c) {
-                if (p.cb_k[c] != k) continue;
-                double t = 0.0;
-                for (int w = 0; w < nwarps; ++w) t += red[c][w];
-                s += t;
-            }
-            double sw = 0.0;
-            for (int t = 0; t < p.nst; ++t) {
-                if (p.st_k[t] != k) continue;
-                double a = 0.0;
-                for (int w = 0; w < nwarps; ++w) a += reds[t][w];
-                sw += a;
-            }
-            const double v = p.weight * (-2.0 * s + sw);
-            if (nsplit == 1) p.G[(size_t)row * p.R + k] = v;
-            else p.part[((size_t)row * nsplit + split) * p.R + k] = v;
-        }
-    }
+    trace_store<Num, true>(p, Z, Zs, row, split);
 }
 
 // Trace products on packed (upper-triangle) storage, exact gradient.  CTA
@@ -1258,6 +1294,9 @@ __global__ void __launch_bounds__(256) trace_packed_kernel(const TraceArgs p) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const S *Kb = static_cast<const S *>(p.K);
     const S *Yb = static_cast<const S *>(p.Y);
+    const S *cbs = static_cast<const S *>(p.cb_s);
+    const S *svLs = static_cast<const S *>(p.st_vLs);
+    const S *svRs = static_cast<const S *>(p.st_vRs);
     typename Num::acc Z[GRAPE_MAXCB];
 #pragma unroll
     for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = Num::acc_zero();
@@ -1270,12 +1309,8 @@ __global__ void __launch_bounds__(256) trace_packed_kernel(const TraceArgs p) {
     for (int e = 0; e < p.epc; ++e) {
         const int u = (chunk * p.epc + e) * 256 + threadIdx.x;
         if (u >= NU) break;
-        const double b2 = 2.0 * d + 1.0;
-        int i = (int)floor(0.5 * (b2 - sqrt(b2 * b2 - 8.0 * (double)u)));
-        i = max(0, min(d - 1, i));
-        while (i > 0 && packed_index(i, i, d) > u) --i;
-        while (i + 1 < d && packed_index(i + 1, i + 1, d) <= u) ++i;
-        const int j = i + (u - packed_index(i, i, d));
+        const unsigned ij = __ldg(&p.tij[u]);         // row and column of packed entry u
+        const int i = (int)(ij & 0xffffu), j = (int)(ij >> 16);
 #pragma unroll 1
         for (int oi = 0; oi < p.ndo; ++oi) {
             const int o = p.do_off[oi];
@@ -1297,8 +1332,8 @@ __global__ void __launch_bounds__(256) trace_packed_kernel(const TraceArgs p) {
 #pragma unroll
             for (int c = 0; c < GRAPE_MAXCB; ++c) {
                 if (c < p.ncb && p.cb_do[c] == oi) {
-                    Num::mac(Z[c], Num::from_double2(__ldg(&p.cb_val[c * d + i])), Sv);
-                    if (i < j) Num::mac(Z[c], Num::from_double2(__ldg(&p.cb_val[c * d + j])), Tv);
+                    Num::mac(Z[c], Num::load(cbs[c * d + i]), Sv);
+                    if (i < j) Num::mac(Z[c], Num::load(cbs[c * d + j]), Tv);
                 }
             }
         }
@@ -1322,54 +1357,15 @@ __global__ void __launch_bounds__(256) trace_packed_kernel(const TraceArgs p) {
                 if (vb) Num::mac(Pb, k, conj_if<Num>(Num::load(Yb[moff + xb]), cjb));        // K Y
             }
             typename Num::acc cL = Num::acc_zero(), cR = Num::acc_zero();
-            Num::mac_conjb(cL, Num::from_double2(__ldg(&p.st_vL[t * d + i])),
-                           Num::from_double2(__ldg(&p.st_vR[t * d + j])));               // vL[i] conj(vR[j])
-            Num::mac_conjb(cR, Num::from_double2(__ldg(&p.st_vL[t * d + j])),
-                           Num::from_double2(__ldg(&p.st_vR[t * d + i])));               // vL[j] conj(vR[i])
+            Num::mac_conjb(cL, Num::load(svLs[t * d + i]),
+                           Num::load(svRs[t * d + j]));               // vL[i] conj(vR[j])
+            Num::mac_conjb(cR, Num::load(svLs[t * d + j]),
+                           Num::load(svRs[t * d + i]));               // vL[j] conj(vR[i])
             Num::mac(Zs[t], Num::done(cL), Num::done(Pa));
             if (vb) Num::mac(Zs[t], Num::done(cR), Num::done(Pb));
         }
     }
-    // deterministic reduction: warp shuffles, then warps in index order (FP64)
-    __shared__ double red[GRAPE_MAXCB][32];
-    __shared__ double reds[GRAPE_MAXST][32];
-#pragma unroll
-    for (int c = 0; c < GRAPE_MAXCB; ++c) {
-        double v = Num::to_double2(Num::done(Z[c])).y;
-#pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
-        if (lane == 0) red[c][warp] = v;
-    }
-#pragma unroll
-    for (int t = 0; t < GRAPE_MAXST; ++t) {
-        double v = Num::to_double2(Num::done(Zs[t])).x;
-#pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
-        if (lane == 0) reds[t][warp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < GRAPE_MAXR) {
-        const int k = threadIdx.x;
-        if (k < p.R) {
-            double s = 0.0;
-            for (int c = 0; c < p.ncb; ++c) {
-                if (p.cb_k[c] != k) continue;
-                double t = 0.0;
-                for (int w = 0; w < nwarps; ++w) t += red[c][w];
-                s += t;
-            }
-            double sw = 0.0;
-            for (int t = 0; t < p.nst; ++t) {
-                if (p.st_k[t] != k) continue;
-                double a = 0.0;
-                for (int w = 0; w < nwarps; ++w) a += reds[t][w];
-                sw += a;
-            }
-            const double v = p.weight * (-2.0 * s + sw);
-            if (nsplit == 1) p.G[(size_t)row * p.R + k] = v;
-            else p.part[((size_t)row * nsplit + split) * p.R + k] = v;
-        }
-    }
+    trace_store<Num, true>(p, Z, Zs, row, split);
 }
 
 // The same sums for problems without rate-controlled dissipators and with
@@ -1390,6 +1386,7 @@ __global__ void __launch_bounds__(256) trace_packed_fast_kernel(const TraceArgs 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const S *Kb = static_cast<const S *>(p.K);
     const S *Yb = static_cast<const S *>(p.Y);
+    const S *cbs = static_cast<const S *>(p.cb_s);
     typename Num::acc Z[GRAPE_MAXCB];
 #pragma unroll
     for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = Num::acc_zero();
@@ -1400,12 +1397,8 @@ __global__ void __launch_bounds__(256) trace_packed_fast_kernel(const TraceArgs 
     for (int e = 0; e < p.epc; ++e) {
         const int u = (chunk * p.epc + e) * 256 + threadIdx.x;
         if (u >= NU) break;
-        const double b2 = 2.0 * d + 1.0;
-        int i = (int)floor(0.5 * (b2 - sqrt(b2 * b2 - 8.0 * (double)u)));
-        i = max(0, min(d - 1, i));
-        while (i > 0 && packed_index(i, i, d) > u) --i;
-        while (i + 1 < d && packed_index(i + 1, i + 1, d) <= u) ++i;
-        const int j = i + (u - packed_index(i, i, d));
+        const unsigned ij = __ldg(&p.tij[u]);         // row and column of packed entry u
+        const int i = (int)(ij & 0xffffu), j = (int)(ij >> 16);
         int x1[NDO], x2[NDO];
         bool v1[NDO], v2[NDO], cj1[NDO], cj2[NDO];
         typename Num::acc Sa[NDO], Ta[NDO];
@@ -1441,37 +1434,174 @@ __global__ void __launch_bounds__(256) trace_packed_fast_kernel(const TraceArgs 
 #pragma unroll
             for (int c = 0; c < GRAPE_MAXCB; ++c) {
                 if (c < p.ncb && p.cb_do[c] == oi) {
-                    Num::mac(Z[c], Num::from_double2(__ldg(&p.cb_val[c * d + i])), Sv);
-                    if (i < j) Num::mac(Z[c], Num::from_double2(__ldg(&p.cb_val[c * d + j])), Tv);
+                    Num::mac(Z[c], Num::load(cbs[c * d + i]), Sv);
+                    if (i < j) Num::mac(Z[c], Num::load(cbs[c * d + j]), Tv);
                 }
             }
         }
     }
-    __shared__ double red[GRAPE_MAXCB][32];
-#pragma unroll
-    for (int c = 0; c < GRAPE_MAXCB; ++c) {
-        double v = Num::to_double2(Num::done(Z[c])).y;
-#pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
-        if (lane == 0) red[c][warp] = v;
+    typename Num::acc Z_unused[GRAPE_MAXST];       // no sandwich terms
+    trace_store<Num, false>(p, Z, Z_unused, row, split);
+}
+
+// The same sums as trace_packed_fast_kernel with the operands staged in
+// shared memory.  The CTA of (row, state, chunk) walks its 256-entry blocks
+// b = chunk * epc + e and, per block, the state's pairs q in order; for each
+// (block, pair) step one warp copies the block's Y entries and the runs of K
+// that hold the block's neighbours (host table trun: packed start, length,
+// shared offset; gaps of a few entries are copied along) into one of nbuf
+// buffers with bulk asynchronous copies counted on that buffer's mbarrier,
+// nbuf - 1 steps ahead of the computation.  Each thread reads its entry's
+// neighbour positions in the buffer from the host table tnb (15-bit index,
+// bit 15: read the conjugate of the mirror, 0xffff: outside the matrix), so
+// every term, and the order of the sums, is that of the fast kernel: the
+// same bits.  A copy wait is bounded: when one gives up, the error word is
+// set to 3, the CTA stops computing and issuing, waits (bounded) for the
+// copies it issued and writes no result (the host reports GRAPE_ETIMEOUT).
+template <class Num, int NDO>
+__global__ void __launch_bounds__(256, 2) trace_tile_kernel(const TraceArgs p) {
+    using S = typename Num::store_t;
+    using V = typename Num::val;
+    extern __shared__ __align__(128) unsigned char tsm[];
+    const int d = p.d;
+    const int NU = d * (d + 1) / 2;
+    const int nsplit = p.nsplit;
+    const int row = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
+    const int state = split / p.nchunk, chunk = split % p.nchunk;
+    const int pps = (int)(p.npairs / p.n_states);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int nbuf = p.nbuf;
+    const int stride = 256 + p.kcap;                       // entries per buffer: Y block, then K runs
+    const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(tsm);
+    S *bufs = reinterpret_cast<S *>(tsm + 64);
+    const uint32_t ba0 = mb0 + 64u;
+    const int nblk_all = (NU + 255) / 256;
+    const int b0 = chunk * p.epc;
+    const int nblk = max(0, min(p.epc, nblk_all - b0));
+    const int total = nblk * pps;
+    const size_t row_base = (size_t)row * p.npairs;
+    const size_t pstride = (size_t)p.n_states * NU;
+    const S *Yp = static_cast<const S *>(p.Y) + (row_base + state) * NU;
+    const S *Kp = static_cast<const S *>(p.K) + (row_base + state) * NU;
+    const S *cbs = static_cast<const S *>(p.cb_s);
+    const long long limit = 1LL << 31;
+
+    if (tid == 0) {
+        for (int b = 0; b < nbuf; ++b) mbar_init(mb0 + 8u * b, 1u);
+        mbar_init_fence();
     }
     __syncthreads();
-    if (threadIdx.x < GRAPE_MAXR) {
-        const int k = threadIdx.x;
-        if (k < p.R) {
-            double s = 0.0;
-            for (int c = 0; c < p.ncb; ++c) {
-                if (p.cb_k[c] != k) continue;
-                double t = 0.0;
-                for (int w = 0; w < nwarps; ++w) t += red[c][w];
-                s += t;
+    // one warp issues the copies of step st into buffer st mod nbuf
+    auto issue = [&](int st) {
+        const int e = st / pps, q = st - e * pps;
+        const int b = b0 + e;
+        const int4 bl = __ldg(&p.tblk[b]);                 // first run, runs, K entries
+        const int ny = min(256, NU - b * 256);
+        const int buf = st % nbuf;
+        const uint32_t mb = mb0 + 8u * buf;
+        const uint32_t dst = ba0 + (uint32_t)(buf * stride) * (uint32_t)sizeof(S);
+        const size_t moff = (size_t)q * pstride;
+        if (lane == 0) {
+            mbar_expect(mb, (uint32_t)(ny + bl.z) * (uint32_t)sizeof(S));
+            bulk_g2s(dst, Yp + moff + (size_t)b * 256, (uint32_t)ny * (uint32_t)sizeof(S), mb);
+        }
+        __syncwarp();
+        for (int r = lane; r < bl.y; r += 32) {
+            const int4 run = __ldg(&p.trun[bl.x + r]);       // packed start, length, shared offset
+            bulk_g2s(dst + (uint32_t)(256 + run.z) * (uint32_t)sizeof(S), Kp + moff + run.x,
+                     (uint32_t)run.y * (uint32_t)sizeof(S), mb);
+        }
+    };
+    int issued = 0;
+    if (warp == 0) {
+        for (int st = 0; st < min(nbuf, total); ++st) issue(st);
+    }
+    issued = min(nbuf, total);
+
+    typename Num::acc Z[GRAPE_MAXCB];
+#pragma unroll
+    for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = Num::acc_zero();
+    bool bad = false;
+
+#pragma unroll 1
+    for (int e = 0; e < nblk; ++e) {
+        const int u = (b0 + e) * 256 + tid;
+        const bool valid = u < NU;
+        uint4 nb = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+        unsigned ij = 0u;
+        if (valid) {
+            nb = __ldg(&p.tnb[u]);
+            ij = __ldg(&p.tij[u]);
+        }
+        const int i = (int)(ij & 0xffffu), j = (int)(ij >> 16);
+        const unsigned w16[8] = {nb.x & 0xffffu, nb.x >> 16, nb.y & 0xffffu, nb.y >> 16,
+                                 nb.z & 0xffffu, nb.z >> 16, nb.w & 0xffffu, nb.w >> 16};
+        int x1[NDO], x2[NDO];
+        bool v1[NDO], v2[NDO], cj1[NDO], cj2[NDO];
+        typename Num::acc Sa[NDO], Ta[NDO];
+#pragma unroll
+        for (int oi = 0; oi < NDO; ++oi) {
+            const unsigned a = w16[2 * oi], c = w16[2 * oi + 1];
+            v1[oi] = valid && a != 0xffffu;
+            v2[oi] = valid && c != 0xffffu;
+            cj1[oi] = (a & 0x8000u) != 0u;
+            cj2[oi] = (c & 0x8000u) != 0u;
+            x1[oi] = v1[oi] ? (int)(a & 0x7fffu) : 0;
+            x2[oi] = v2[oi] ? (int)(c & 0x7fffu) : 0;
+            Sa[oi] = Num::acc_zero();
+            Ta[oi] = Num::acc_zero();
+        }
+#pragma unroll 1
+        for (int q = 0; q < pps; ++q) {
+            const int st = e * pps + q;
+            const int buf = st % nbuf;
+            if (!bad && !mbar_wait(mb0 + 8u * buf, (uint32_t)((st / nbuf) & 1), limit)) {
+                bad = true;
+                atomicExch(p.err, 3u);
             }
-            const double sw = 0.0;                      // no rate-controlled dissipators
-            const double v = p.weight * (-2.0 * s + sw);
-            if (nsplit == 1) p.G[(size_t)row * p.R + k] = v;
-            else p.part[((size_t)row * nsplit + split) * p.R + k] = v;
+            if (!bad && valid) {
+                const S *Ys = bufs + (size_t)buf * stride;
+                const S *Ks = Ys + 256;
+                const V y = Num::load(Ys[tid]);
+#pragma unroll
+                for (int oi = 0; oi < NDO; ++oi) {
+                    if (v1[oi]) Num::mac_conjb(Sa[oi], conj_if<Num>(Num::load(Ks[x1[oi]]), cj1[oi]), y);
+                    if (v2[oi]) Num::mac_conjb(Ta[oi], y, conj_if<Num>(Num::load(Ks[x2[oi]]), cj2[oi]));
+                }
+            }
+            // buffer `buf` is free again, and every thread takes the same `bad`
+            bad = __syncthreads_or(bad ? 1 : 0) != 0;
+            if (!bad && issued < total) {
+                if (warp == 0) issue(issued);
+                ++issued;
+            }
+        }
+        if (valid && !bad) {
+#pragma unroll
+            for (int oi = 0; oi < NDO; ++oi) {
+                if (oi >= p.ndo) break;
+                const V Sv = Num::done(Sa[oi]), Tv = Num::done(Ta[oi]);
+#pragma unroll
+                for (int c = 0; c < GRAPE_MAXCB; ++c) {
+                    if (c < p.ncb && p.cb_do[c] == oi) {
+                        Num::mac(Z[c], Num::load(cbs[c * d + i]), Sv);
+                        if (i < j) Num::mac(Z[c], Num::load(cbs[c * d + j]), Tv);
+                    }
+                }
+            }
         }
     }
+    if (bad) {
+        // no CTA leaves while a copy it issued may still write its shared memory
+        if (tid == 0) {
+            const int first = max(0, issued - nbuf);
+            for (int st = first; st < issued; ++st)
+                mbar_wait(mb0 + 8u * (st % nbuf), (uint32_t)((st / nbuf) & 1), limit);
+        }
+        return;
+    }
+    typename Num::acc Z_unused[GRAPE_MAXST];       // no sandwich terms
+    trace_store<Num, false>(p, Z, Z_unused, row, split);
 }
 
 // G[row][k] = sum over the row's splits, in split order (deterministic)
@@ -1684,7 +1814,13 @@ cudaError_t launch_trace(const TraceArgs &p, cudaStream_t s) {
     if (p.n_rows <= 0) return cudaSuccess;
     if (p.packed) {
         const int grid = p.n_rows * max(1, p.nsplit);
-        if (p.nst == 0 && p.ndo <= 2) trace_packed_fast_kernel<Num, 2><<<grid, 256, 0, s>>>(p);
+        if (p.tile && p.nst == 0 && p.ndo <= 4) {
+            const size_t smem = 64 + (size_t)p.nbuf * (256 + p.kcap) * sizeof(typename Num::store_t);
+            void (*k)(const TraceArgs) = p.ndo <= 2 ? trace_tile_kernel<Num, 2> : trace_tile_kernel<Num, 4>;
+            const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k<<<grid, 256, smem, s>>>(p);
+        } else if (p.nst == 0 && p.ndo <= 2) trace_packed_fast_kernel<Num, 2><<<grid, 256, 0, s>>>(p);
         else if (p.nst == 0 && p.ndo <= 4) trace_packed_fast_kernel<Num, 4><<<grid, 256, 0, s>>>(p);
         else trace_packed_kernel<Num><<<grid, 256, 0, s>>>(p);
         return cudaGetLastError();
