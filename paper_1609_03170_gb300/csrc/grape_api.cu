@@ -496,7 +496,7 @@ double2 encode(const grape_problem *P, cplx v) {
     if (P->prec == GRAPE_PREC_FP64) return make_double2(v.real(), v.imag());
     const grape_num::ff re = grape_num::ff_from_double(v.real());
     const grape_num::ff im = grape_num::ff_from_double(v.imag());
-    const float4 f = make_float4(re.h, re.l, im.h, im.l);
+    const float4 f = make_float4(re.h, im.h, re.l, im.l);   // the kernels' pair layout
     double2 out;
     std::memcpy(&out, &f, sizeof(out));
     return out;

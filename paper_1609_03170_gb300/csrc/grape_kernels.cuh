@@ -334,8 +334,7 @@ __device__ __forceinline__ void hpush(S *buf, const HWin &h, int rank, int r, in
 
 template <class Num>
 __device__ __forceinline__ typename Num::store_t conj_store(typename Num::val v) {
-    v.im = Num::neg_real(v.im);
-    return Num::store(v);
+    return Num::store(Num::conj(v));
 }
 
 __device__ __forceinline__ void st_cluster_addr(uint32_t addr, double2 v) { st_remote(addr, v); }
@@ -1163,14 +1162,14 @@ __device__ __forceinline__ void trace_store(const TraceArgs &p, typename Num::ac
         r_zero(t);
 #pragma unroll
         for (int c = 0; c < GRAPE_MAXCB; ++c)
-            if (c < p.ncb && p.cb_k[c] == k) t = r_add(t, Num::done(Z[c]).im);
+            if (c < p.ncb && p.cb_k[c] == k) t = r_add(t, Num::im(Num::done(Z[c])));
         R r = r_m2(t);
         if constexpr (ST) {
             R w;
             r_zero(w);
 #pragma unroll
             for (int q = 0; q < GRAPE_MAXST; ++q)
-                if (q < p.nst && p.st_k[q] == k) w = r_add(w, Num::done(Zs[q]).re);
+                if (q < p.nst && p.st_k[q] == k) w = r_add(w, Num::re(Num::done(Zs[q])));
             r = r_add(r, w);
         }
 #pragma unroll
@@ -1276,7 +1275,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs p) {
 // no bit depends on the launch grouping or the propagation tile.
 template <class Num>
 __device__ __forceinline__ typename Num::val conj_if(typename Num::val v, bool c) {
-    if (c) v.im = Num::neg_real(v.im);
+    if (c) v = Num::conj(v);
     return v;
 }
 __device__ __forceinline__ int packed_index(int r, int c, int d) { return r * d - r * (r - 1) / 2 + (c - r); }
