@@ -1102,11 +1102,10 @@ grape_status trace_tiles(grape_problem *P, TraceArgs *t) {
         }
     }
     // buffers: as many (2 to 4) as keep two CTAs per SM, else two at one CTA per SM
-    const size_t stage = (size_t)(256 + kcap) * 16;
     int nbuf = 0;
     for (int n = 4; n >= 2 && !nbuf; --n)
-        if (64 + n * stage <= 100 * 1024) nbuf = n;
-    if (!nbuf && 64 + 2 * stage + 4096 <= (size_t)max_smem_optin(P)) nbuf = 2;
+        if (trace_tile_smem(n, kcap) <= 104 * 1024) nbuf = n;
+    if (!nbuf && trace_tile_smem(2, kcap) + 4096 <= (size_t)max_smem_optin(P)) nbuf = 2;
     if (!nbuf) return GRAPE_OK;
     int4 *dblk = nullptr, *drun = nullptr;
     uint4 *dnb = nullptr;

@@ -153,6 +153,12 @@ struct TraceArgs {
     unsigned *err;                  // error word: 3 when a copy wait gave up
 };
 
+// dynamic shared memory of the staged trace kernel: 8 mbarriers, the
+// per-band sums [8][256] (16 B each), nbuf buffers of 256 + kcap entries
+inline size_t trace_tile_smem(int nbuf, int kcap) {
+    return 64 + (size_t)GRAPE_MAXCB * 256 * 16 + (size_t)nbuf * (256 + kcap) * 16;
+}
+
 // Launchers, one set per number type: _f64 native FP64, _df double-float.
 #define GRAPE_DECLARE_LAUNCHERS(SUFFIX)                                                        \
     cudaError_t grape_launch_prop_##SUFFIX(const PropArgs &p, int threads, int variant,         \

@@ -1151,10 +1151,12 @@ __device__ __forceinline__ void r_zero(double &a) { a = 0.0; }
 // grouping or the propagation tile.
 template <class Num, bool ST>
 __device__ __forceinline__ void trace_store(const TraceArgs &p, typename Num::acc (&Z)[GRAPE_MAXCB],
-                                            typename Num::acc (&Zs)[GRAPE_MAXST], int row, int split) {
+                                            typename Num::acc (&Zs)[GRAPE_MAXST], int row, int split,
+                                            int nwarps = 0) {
     using R = typename Num::real_t;
     __shared__ R redk[GRAPE_MAXR][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (nwarps <= 0) nwarps = blockDim.x >> 5;      // warps whose sums count (in index order)
 #pragma unroll
     for (int k = 0; k < GRAPE_MAXR; ++k) {
         if (k >= p.R) break;
@@ -1174,7 +1176,7 @@ __device__ __forceinline__ void trace_store(const TraceArgs &p, typename Num::ac
         }
 #pragma unroll
         for (int sh = 16; sh > 0; sh >>= 1) r = r_add(r, r_shfl_down(r, sh));
-        if (lane == 0) redk[k][warp] = r;
+        if (lane == 0 && warp < nwarps) redk[k][warp] = r;
     }
     __syncthreads();
     if (threadIdx.x < p.R) {
@@ -1444,36 +1446,69 @@ __global__ void __launch_bounds__(256) trace_packed_fast_kernel(const TraceArgs 
 }
 
 // The same sums as trace_packed_fast_kernel with the operands staged in
-// shared memory.  The CTA of (row, state, chunk) walks its 256-entry blocks
-// b = chunk * epc + e and, per block, the state's pairs q in order; for each
-// (block, pair) step one warp copies the block's Y entries and the runs of K
-// that hold the block's neighbours (host table trun: packed start, length,
-// shared offset; gaps of a few entries are copied along) into one of nbuf
-// buffers with bulk asynchronous copies counted on that buffer's mbarrier,
-// nbuf - 1 steps ahead of the computation.  Each thread reads its entry's
-// neighbour positions in the buffer from the host table tnb (15-bit index,
-// bit 15: read the conjugate of the mirror, 0xffff: outside the matrix), so
-// every term, and the order of the sums, is that of the fast kernel: the
-// same bits.  A copy wait is bounded: when one gives up, the error word is
-// set to 3, the CTA stops computing and issuing, waits (bounded) for the
-// copies it issued and writes no result (the host reports GRAPE_ETIMEOUT).
+// shared memory by a warp-specialised pipeline.  The CTA of (row, state,
+// chunk) walks its 256-entry blocks b = chunk * epc + e and, per block, the
+// state's pairs q in order.  Warp 8 is the producer: for each (block, pair)
+// step it copies the block's Y entries and the runs of K that hold the
+// block's neighbours (host table trun: packed start, length, offset in the
+// buffer; gaps of a few entries come along) into one of nbuf buffers with
+// bulk asynchronous copies counted on the buffer's "full" mbarrier, after the
+// buffer's "empty" mbarrier shows that the eight consumer warps are done with
+// its previous use.  Warps 0..7 are the consumers, thread t owning entry
+// b * 256 + t: they read its neighbour positions in the buffer from the host
+// table tnb (15-bit index, bit 15: read the conjugate of the mirror, 0xffff:
+// outside the matrix) and release the buffer warp by warp, so no CTA-wide
+// barrier stands between pairs.  Every term and the order of every sum is
+// that of the fast kernel: the same bits.  Waits are bounded: one that gives
+// up sets the error word to 3 and a shared stop flag, the CTA stops, waits
+// (bounded) for the copies it issued and writes no result (the host reports
+// GRAPE_ETIMEOUT).
+#define GRAPE_TRACE_CONSUMERS 8
+#define GRAPE_TRACE_THREADS (32 * (GRAPE_TRACE_CONSUMERS + 1))
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("{\n\t.reg .b64 st;\n\t"
+                 "mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(mbar)
+                 : "memory");
+}
+// bounded wait that also gives up once *stop is set (by another thread)
+__device__ __forceinline__ bool mbar_wait_or_stop(uint32_t mbar, uint32_t parity, long long cycles,
+                                                  volatile int *stop) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (*stop || clock64() - t0 > cycles) return false;
+    }
+}
+
 template <class Num, int NDO>
-__global__ void __launch_bounds__(256, 2) trace_tile_kernel(const TraceArgs p) {
+__global__ void __launch_bounds__(GRAPE_TRACE_THREADS, 2) trace_tile_kernel(const TraceArgs p) {
     using S = typename Num::store_t;
     using V = typename Num::val;
+    using A = typename Num::acc;
     extern __shared__ __align__(128) unsigned char tsm[];
+    __shared__ int s_stop;
     const int d = p.d;
     const int NU = d * (d + 1) / 2;
     const int nsplit = p.nsplit;
     const int row = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
     const int state = split / p.nchunk, chunk = split % p.nchunk;
     const int pps = (int)(p.npairs / p.n_states);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nbuf = p.nbuf;
     const int stride = 256 + p.kcap;                       // entries per buffer: Y block, then K runs
-    const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(tsm);
-    S *bufs = reinterpret_cast<S *>(tsm + 64);
-    const uint32_t ba0 = mb0 + 64u;
+    const uint32_t full0 = (uint32_t)__cvta_generic_to_shared(tsm);     // [nbuf] "full" mbarriers
+    const uint32_t empty0 = full0 + 32u;                                // [nbuf] "empty" mbarriers
+    A *Zsm = reinterpret_cast<A *>(tsm + 64);                           // [GRAPE_MAXCB][256]
+    S *bufs = reinterpret_cast<S *>(tsm + 64 + GRAPE_MAXCB * 256 * sizeof(A));
+    const uint32_t ba0 = full0 + 64u + (uint32_t)(GRAPE_MAXCB * 256 * sizeof(A));
     const int nblk_all = (NU + 255) / 256;
     const int b0 = chunk * p.epc;
     const int nblk = max(0, min(p.epc, nblk_all - b0));
@@ -1486,121 +1521,146 @@ __global__ void __launch_bounds__(256, 2) trace_tile_kernel(const TraceArgs p) {
     const long long limit = 1LL << 31;
 
     if (tid == 0) {
-        for (int b = 0; b < nbuf; ++b) mbar_init(mb0 + 8u * b, 1u);
+        for (int b = 0; b < nbuf; ++b) {
+            mbar_init(full0 + 8u * b, 1u);
+            mbar_init(empty0 + 8u * b, GRAPE_TRACE_CONSUMERS);
+        }
         mbar_init_fence();
+        s_stop = 0;
     }
+    if (tid < 256)
+        for (int c = 0; c < GRAPE_MAXCB; ++c) Zsm[c * 256 + tid] = Num::acc_zero();
     __syncthreads();
-    // one warp issues the copies of step st into buffer st mod nbuf
-    auto issue = [&](int st) {
-        const int e = st / pps, q = st - e * pps;
-        const int b = b0 + e;
-        const int4 bl = __ldg(&p.tblk[b]);                 // first run, runs, K entries
-        const int ny = min(256, NU - b * 256);
-        const int buf = st % nbuf;
-        const uint32_t mb = mb0 + 8u * buf;
-        const uint32_t dst = ba0 + (uint32_t)(buf * stride) * (uint32_t)sizeof(S);
-        const size_t moff = (size_t)q * pstride;
-        if (lane == 0) {
-            mbar_expect(mb, (uint32_t)(ny + bl.z) * (uint32_t)sizeof(S));
-            bulk_g2s(dst, Yp + moff + (size_t)b * 256, (uint32_t)ny * (uint32_t)sizeof(S), mb);
-        }
-        __syncwarp();
-        for (int r = lane; r < bl.y; r += 32) {
-            const int4 run = __ldg(&p.trun[bl.x + r]);       // packed start, length, shared offset
-            bulk_g2s(dst + (uint32_t)(256 + run.z) * (uint32_t)sizeof(S), Kp + moff + run.x,
-                     (uint32_t)run.y * (uint32_t)sizeof(S), mb);
-        }
-    };
-    int issued = 0;
-    if (warp == 0) {
-        for (int st = 0; st < min(nbuf, total); ++st) issue(st);
-    }
-    issued = min(nbuf, total);
 
-    typename Num::acc Z[GRAPE_MAXCB];
-#pragma unroll
-    for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = Num::acc_zero();
-    bool bad = false;
-
-#pragma unroll 1
-    for (int e = 0; e < nblk; ++e) {
-        const int u = (b0 + e) * 256 + tid;
-        const bool valid = u < NU;
-        uint4 nb = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-        unsigned ij = 0u;
-        if (valid) {
-            nb = __ldg(&p.tnb[u]);
-            ij = __ldg(&p.tij[u]);
-        }
-        const int i = (int)(ij & 0xffffu), j = (int)(ij >> 16);
-        const unsigned w16[8] = {nb.x & 0xffffu, nb.x >> 16, nb.y & 0xffffu, nb.y >> 16,
-                                 nb.z & 0xffffu, nb.z >> 16, nb.w & 0xffffu, nb.w >> 16};
-        int x1[NDO], x2[NDO];
-        bool v1[NDO], v2[NDO], cj1[NDO], cj2[NDO];
-        typename Num::acc Sa[NDO], Ta[NDO];
-#pragma unroll
-        for (int oi = 0; oi < NDO; ++oi) {
-            const unsigned a = w16[2 * oi], c = w16[2 * oi + 1];
-            v1[oi] = valid && a != 0xffffu;
-            v2[oi] = valid && c != 0xffffu;
-            cj1[oi] = (a & 0x8000u) != 0u;
-            cj2[oi] = (c & 0x8000u) != 0u;
-            x1[oi] = v1[oi] ? (int)(a & 0x7fffu) : 0;
-            x2[oi] = v2[oi] ? (int)(c & 0x7fffu) : 0;
-            Sa[oi] = Num::acc_zero();
-            Ta[oi] = Num::acc_zero();
-        }
-#pragma unroll 1
-        for (int q = 0; q < pps; ++q) {
-            const int st = e * pps + q;
-            const int buf = st % nbuf;
-            if (!bad && !mbar_wait(mb0 + 8u * buf, (uint32_t)((st / nbuf) & 1), limit)) {
-                bad = true;
-                atomicExch(p.err, 3u);
-            }
-            if (!bad && valid) {
-                const S *Ys = bufs + (size_t)buf * stride;
-                const S *Ks = Ys + 256;
-                const V y = Num::load(Ys[tid]);
-#pragma unroll
-                for (int oi = 0; oi < NDO; ++oi) {
-                    if (v1[oi]) Num::mac_conjb(Sa[oi], conj_if<Num>(Num::load(Ks[x1[oi]]), cj1[oi]), y);
-                    if (v2[oi]) Num::mac_conjb(Ta[oi], y, conj_if<Num>(Num::load(Ks[x2[oi]]), cj2[oi]));
+    if (warp == GRAPE_TRACE_CONSUMERS) {
+        // ---- producer: one step per (block, pair), nbuf - 1 ahead of the slowest consumer
+        int buf = 0, use = 0, issued = 0;
+        bool stop = false;
+        for (int st = 0; st < total && !stop; ++st) {
+            const bool ok = use == 0 || mbar_wait_or_stop(empty0 + 8u * buf, (uint32_t)((use - 1) & 1), limit, &s_stop);
+            if (!__all_sync(0xffffffffu, ok)) {     // the warp decides as one
+                stop = true;
+                if (lane == 0) {
+                    s_stop = 1;
+                    atomicExch(p.err, 3u);
                 }
+                break;
             }
-            // buffer `buf` is free again, and every thread takes the same `bad`
-            bad = __syncthreads_or(bad ? 1 : 0) != 0;
-            if (!bad && issued < total) {
-                if (warp == 0) issue(issued);
-                ++issued;
+            const int e = st / pps, q = st - e * pps;
+            const int b = b0 + e;
+            const int4 bl = __ldg(&p.tblk[b]);             // first run, runs, K entries
+            const int ny = min(256, NU - b * 256);
+            const uint32_t mb = full0 + 8u * buf;
+            const uint32_t dst = ba0 + (uint32_t)(buf * stride) * (uint32_t)sizeof(S);
+            const size_t moff = (size_t)q * pstride;
+            if (lane == 0) {
+                mbar_expect(mb, (uint32_t)(ny + bl.z) * (uint32_t)sizeof(S));
+                bulk_g2s(dst, Yp + moff + (size_t)b * 256, (uint32_t)ny * (uint32_t)sizeof(S), mb);
+            }
+            __syncwarp();
+            for (int r = lane; r < bl.y; r += 32) {
+                const int4 run = __ldg(&p.trun[bl.x + r]);   // packed start, length, buffer offset
+                bulk_g2s(dst + (uint32_t)(256 + run.z) * (uint32_t)sizeof(S), Kp + moff + run.x,
+                         (uint32_t)run.y * (uint32_t)sizeof(S), mb);
+            }
+            ++issued;
+            if (++buf == nbuf) {
+                buf = 0;
+                ++use;
             }
         }
-        if (valid && !bad) {
+        if (stop && lane == 0) {
+            // no CTA leaves while a copy it issued may still write its shared memory
+            for (int st = max(0, issued - nbuf); st < issued; ++st)
+                mbar_wait(full0 + 8u * (st % nbuf), (uint32_t)((st / nbuf) & 1), limit);
+        }
+    } else {
+        // ---- consumers
+        int buf = 0, use = 0;
+        bool stop = false;
+        const S *Ys = bufs;
+#pragma unroll 1
+        for (int e = 0; e < nblk && !stop; ++e) {
+            const int u = (b0 + e) * 256 + tid;
+            const bool valid = u < NU;
+            uint4 nb = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+            unsigned ij = 0u;
+            if (valid) {
+                nb = __ldg(&p.tnb[u]);
+                ij = __ldg(&p.tij[u]);
+            }
+            const unsigned w16[8] = {nb.x & 0xffffu, nb.x >> 16, nb.y & 0xffffu, nb.y >> 16,
+                                     nb.z & 0xffffu, nb.z >> 16, nb.w & 0xffffu, nb.w >> 16};
+            int x1[NDO], x2[NDO];
+            bool v1[NDO], v2[NDO], cj1[NDO], cj2[NDO];
+            A Sa[NDO], Ta[NDO];
 #pragma unroll
             for (int oi = 0; oi < NDO; ++oi) {
-                if (oi >= p.ndo) break;
-                const V Sv = Num::done(Sa[oi]), Tv = Num::done(Ta[oi]);
+                const unsigned a = w16[2 * oi], c = w16[2 * oi + 1];
+                v1[oi] = valid && a != 0xffffu;
+                v2[oi] = valid && c != 0xffffu;
+                cj1[oi] = (a & 0x8000u) != 0u;
+                cj2[oi] = (c & 0x8000u) != 0u;
+                x1[oi] = 256 + (v1[oi] ? (int)(a & 0x7fffu) : 0);
+                x2[oi] = 256 + (v2[oi] ? (int)(c & 0x7fffu) : 0);
+                Sa[oi] = Num::acc_zero();
+                Ta[oi] = Num::acc_zero();
+            }
+#pragma unroll 1
+            for (int q = 0; q < pps; ++q) {
+                const bool ok = mbar_wait_or_stop(full0 + 8u * buf, (uint32_t)(use & 1), limit, &s_stop);
+                if (!__all_sync(0xffffffffu, ok)) {  // the warp decides as one
+                    stop = true;
+                    if (lane == 0) {
+                        s_stop = 1;
+                        atomicExch(p.err, 3u);
+                    }
+                    break;
+                }
+                if (valid) {
+                    const V y = Num::load(Ys[tid]);
 #pragma unroll
-                for (int c = 0; c < GRAPE_MAXCB; ++c) {
-                    if (c < p.ncb && p.cb_do[c] == oi) {
-                        Num::mac(Z[c], Num::load(cbs[c * d + i]), Sv);
-                        if (i < j) Num::mac(Z[c], Num::load(cbs[c * d + j]), Tv);
+                    for (int oi = 0; oi < NDO; ++oi) {
+                        if (v1[oi]) Num::mac_conjb(Sa[oi], conj_if<Num>(Num::load(Ys[x1[oi]]), cj1[oi]), y);
+                        if (v2[oi]) Num::mac_conjb(Ta[oi], y, conj_if<Num>(Num::load(Ys[x2[oi]]), cj2[oi]));
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty0 + 8u * buf);
+                if (++buf == nbuf) {
+                    buf = 0;
+                    ++use;
+                    Ys = bufs;
+                } else {
+                    Ys += stride;
+                }
+            }
+            if (valid && !stop) {
+                const int i = (int)(ij & 0xffffu), j = (int)(ij >> 16);
+#pragma unroll
+                for (int oi = 0; oi < NDO; ++oi) {
+                    if (oi >= p.ndo) break;
+                    const V Sv = Num::done(Sa[oi]), Tv = Num::done(Ta[oi]);
+#pragma unroll
+                    for (int c = 0; c < GRAPE_MAXCB; ++c) {
+                        if (c < p.ncb && p.cb_do[c] == oi) {
+                            A z = Zsm[c * 256 + tid];
+                            Num::mac(z, Num::load(cbs[c * d + i]), Sv);
+                            if (i < j) Num::mac(z, Num::load(cbs[c * d + j]), Tv);
+                            Zsm[c * 256 + tid] = z;
+                        }
                     }
                 }
             }
         }
     }
-    if (bad) {
-        // no CTA leaves while a copy it issued may still write its shared memory
-        if (tid == 0) {
-            const int first = max(0, issued - nbuf);
-            for (int st = first; st < issued; ++st)
-                mbar_wait(mb0 + 8u * (st % nbuf), (uint32_t)((st / nbuf) & 1), limit);
-        }
-        return;
-    }
-    typename Num::acc Z_unused[GRAPE_MAXST];       // no sandwich terms
-    trace_store<Num, false>(p, Z, Z_unused, row, split);
+    __syncthreads();
+    if (s_stop) return;
+    A Z[GRAPE_MAXCB];
+#pragma unroll
+    for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = tid < 256 ? Zsm[c * 256 + tid] : Num::acc_zero();
+    A Z_unused[GRAPE_MAXST];                        // no sandwich terms
+    trace_store<Num, false>(p, Z, Z_unused, row, split, GRAPE_TRACE_CONSUMERS);
 }
 
 // G[row][k] = sum over the row's splits, in split order (deterministic)
@@ -1814,11 +1874,11 @@ cudaError_t launch_trace(const TraceArgs &p, cudaStream_t s) {
     if (p.packed) {
         const int grid = p.n_rows * max(1, p.nsplit);
         if (p.tile && p.nst == 0 && p.ndo <= 4) {
-            const size_t smem = 64 + (size_t)p.nbuf * (256 + p.kcap) * sizeof(typename Num::store_t);
+            const size_t smem = trace_tile_smem(p.nbuf, p.kcap);
             void (*k)(const TraceArgs) = p.ndo <= 2 ? trace_tile_kernel<Num, 2> : trace_tile_kernel<Num, 4>;
             const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            k<<<grid, 256, smem, s>>>(p);
+            k<<<grid, GRAPE_TRACE_THREADS, smem, s>>>(p);
         } else if (p.nst == 0 && p.ndo <= 2) trace_packed_fast_kernel<Num, 2><<<grid, 256, 0, s>>>(p);
         else if (p.nst == 0 && p.ndo <= 4) trace_packed_fast_kernel<Num, 4><<<grid, 256, 0, s>>>(p);
         else trace_packed_kernel<Num><<<grid, 256, 0, s>>>(p);
