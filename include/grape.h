@@ -119,7 +119,12 @@ grape_status grape_forward(grape_problem_t problem, const double *u, double *F,
 
 /* Phi and its gradient dPhi/du_k(j) (Sec. 2.2 Eq. dphidu; Sec. 3), in the
  * problem's grad_mode.  grad: [n_slices][n_controls] doubles, host or
- * device.  Same pointer and stream rules as grape_forward. */
+ * device.  Same pointer and stream rules as grape_forward.  The cost is
+ * linear in rho, so the adjoint sweep does not read the forward states: in
+ * exact mode, with the whole problem in one segment on a cluster kernel, the
+ * two sweeps run at the same time on the problem's own streams and the
+ * trace of each chunk of slices waits for both (GRAPE_CONCURRENT=0: one
+ * after the other; the results are the same bits either way). */
 grape_status grape_gradient(grape_problem_t problem, const double *u, double *F,
                             double *grad, void *stream);
 

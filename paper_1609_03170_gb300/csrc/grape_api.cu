@@ -315,9 +315,11 @@ struct grape_problem {
     size_t bytes = 0;
     cudaStream_t s1 = nullptr;       // high-priority stream the gradient sweeps run on
     cudaStream_t s2 = nullptr;       // low-priority stream: traces overlap the adjoint sweep
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t s3 = nullptr;       // high-priority stream: the adjoint sweep beside the forward
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork3 = nullptr;
     static constexpr int kMaxChunks = 16;
     cudaEvent_t ev[kMaxChunks + 2] = {};
+    cudaEvent_t evF[kMaxChunks] = {};   // forward chunk c done (concurrent sweeps)
     bool profiling = false;
     struct Mark { int phase; cudaEvent_t a, b; };
     std::vector<Mark> marks;
@@ -381,6 +383,10 @@ struct grape_problem {
     ~grape_problem() {
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
+        for (auto &e : evF)
+            if (e) cudaEventDestroy(e);
+        if (ev_fork3) cudaEventDestroy(ev_fork3);
+        if (s3) cudaStreamDestroy(s3);
         if (s2) cudaStreamDestroy(s2);
         if (s1) cudaStreamDestroy(s1);
         if (ev_fork) cudaEventDestroy(ev_fork);
@@ -965,8 +971,13 @@ struct GradScratch {
     double2 *Y = nullptr, *K = nullptr, *ckpt = nullptr, *x = nullptr, *mu = nullptr;
     int seg = 0, nseg = 0;
     cudaStream_t s2 = nullptr;   // trace stream; null: traces run on the main stream
-    cudaEvent_t *ev = nullptr;   // kMaxChunks + 1 events when s2 is set
+    cudaEvent_t *ev = nullptr;   // kMaxChunks + 2 events when s2 is set
     double *part = nullptr;      // partial traces; null: one CTA per slice
+    // concurrent sweeps (see concurrent_sweeps): the adjoint's stream, its
+    // fork event and the forward chunks' events; null: one sweep after the other
+    cudaStream_t s3 = nullptr;
+    cudaEvent_t fork3 = nullptr;
+    cudaEvent_t *evF = nullptr;
 };
 
 long long trace_pairs(const grape_problem *P) {
@@ -1139,9 +1150,30 @@ int adjoint_chunks(const grape_problem *P, long long j0, long long j1) {
     return (int)std::min<long long>(n, j1 - j0);
 }
 
-int gradient_launch_count(const grape_problem *P, int seg, int nseg) {
+// Whether grape_gradient runs the forward and the adjoint sweep at the same
+// time.  The cost Phi = sum_s Re Tr(sigma_s rho_s(T)) and the running
+// penalty are linear in rho, so the adjoint's start value (sigma, plus the
+// penalty's constant diagonal) and the exact discrete adjoint recursion
+// (the transpose of the RK4 propagator, Eq. partialuk) never read the
+// forward states: only the traces pair the two sweeps.  The forward sweep
+// then runs in the adjoint's chunks, and the trace of chunk c waits for both
+// sweeps to pass it.  Exact mode with the whole problem in one segment, on a
+// cluster kernel (the grid kernel's per-problem stage buffers and flags admit
+// one sweep at a time); GRAPE_CONCURRENT=0 turns it off.  Same kernels, same
+// arithmetic: the same bits.
+bool concurrent_sweeps(const grape_problem *P, int nseg) {
+    if (P->mode != GRAPE_GRAD_EXACT || nseg != 1 || P->grid) return false;
+    if (const char *env = std::getenv("GRAPE_CONCURRENT"))
+        if (std::atoi(env) == 0) return false;
+    if (const char *env = std::getenv("GRAPE_TRACE_OVERLAP"))
+        if (std::atoi(env) == 0) return false;
+    return true;
+}
+
+int gradient_launch_count(const grape_problem *P, int seg, int nseg, bool concurrent = false) {
     if (nseg <= 0) return -1;
     int n = 2;                                    // forward sweep, cost
+    if (concurrent) n += adjoint_chunks(P, 0, P->n_slices) - 1;   // the forward in chunks
     if (P->penalty) n += 3;                       // adjoint start, final-state value, sum
     for (int gi = 0; gi < nseg; ++gi) {
         const long long j0 = (long long)gi * seg;
@@ -1251,16 +1283,118 @@ grape_status pen_finish(grape_problem *P, double *F, cudaStream_t s) {
     return GRAPE_OK;
 }
 
+// The trace kernels (Eq. dphidu) of slices [cA, cB), whose stage storage
+// starts kofs entries into S.Y and S.K, on stream ts.
+grape_status trace_chunk(grape_problem *P, const GradScratch &S, double *Gd, long long cA, long long cB,
+                         size_t kofs, cudaStream_t ts) {
+    grape_status st;
+    const bool exact = (P->mode == GRAPE_GRAD_EXACT);
+    const size_t mat = full_set(P);
+    TraceArgs t = P->trace;
+    t.n_rows = (int)(cB - cA);
+    t.G = Gd + (size_t)cA * P->R;
+    if (exact) {
+        t.K = S.K + kofs;
+        t.Y = S.Y + kofs;
+        t.npairs = (long long)P->n_rk * 4 * P->ns;
+        t.weight = 1.0;
+    } else {
+        t.K = S.K + kofs + mat;   // lambda_{j+1}, rho_{j+1} pair with row j
+        t.Y = S.Y + kofs + mat;
+        t.npairs = P->ns;
+        t.weight = P->T / P->n_slices;
+    }
+    if (!S.part && !t.packed) t.nsplit = 1;
+    t.part = S.part ? S.part + (size_t)cA * t.nsplit * P->R : nullptr;
+    if ((st = timed(P, PH_TRACE, ts, [&] { return k_trace(P, t, ts); })) != GRAPE_OK) return st;
+    if (t.nsplit > 1 &&
+        (st = timed(P, PH_TRACE, ts, [&] {
+             return P->prec == GRAPE_PREC_FP64 ? grape_launch_trace_finish_f64(t, ts)
+                                               : grape_launch_trace_finish_df(t, ts);
+         })) != GRAPE_OK)
+        return st;
+    return GRAPE_OK;
+}
+
+// The gradient with the forward and the adjoint sweep at the same time (see
+// concurrent_sweeps): the forward in the adjoint's chunks on s (then the
+// cost and the running penalty's rows), the adjoint on S.s3 (start value,
+// chunks last first), the trace of chunk c on S.s2 once both sweeps have
+// passed it; s then waits for both.
+grape_status run_gradient_concurrent(grape_problem *P, const double *ud, double *Fd, double *Gd,
+                                     cudaStream_t s, const GradScratch &S) {
+    grape_status st;
+    const size_t mat = full_set(P);
+    const size_t pst = packed_set(P);
+    const long long j0 = 0, j1 = P->n_slices;
+    const int nch = adjoint_chunks(P, j0, j1);
+    const size_t per_slice = (size_t)P->n_rk * 4 * pst;   // stored stage entries per slice
+    cudaStream_t sa = S.s3, ts = S.s2;
+    GRAPE_CUDA_TRY(cudaEventRecord(S.fork3, s));
+    GRAPE_CUDA_TRY(cudaStreamWaitEvent(sa, S.fork3, 0));
+    // adjoint start value: sigma (and the penalty's last term)
+    GRAPE_CUDA_TRY(cudaMemcpyAsync(S.mu, P->d_sigma, mat * sizeof(double2), cudaMemcpyDeviceToDevice, sa));
+    if (P->penalty)
+        GRAPE_CUDA_TRY(P->prec == GRAPE_PREC_FP64 ? grape_launch_add_diag_f64(S.mu, P->d_src, P->d, P->ns, sa)
+                                                  : grape_launch_add_diag_df(S.mu, P->d_src, P->d, P->ns, sa));
+    // forward sweep in chunks, each storing its slices' stage inputs
+    for (int ci = 0; ci < nch; ++ci) {
+        const long long cA = j0 + (j1 - j0) * ci / nch;
+        const long long cB = j0 + (j1 - j0) * (ci + 1) / nch;
+        PropArgs f = base_args(P, 0, ud);
+        f.sub_begin = cA * P->n_rk;
+        f.sub_end = cB * P->n_rk;
+        f.x_in = ci == 0 ? P->d_rho0 : S.x;
+        f.x_out = S.x;
+        f.stage_store = S.Y + (size_t)(cA - j0) * per_slice;
+        if ((st = launch_prop(P, f, s)) != GRAPE_OK) return st;
+        GRAPE_CUDA_TRY(cudaEventRecord(S.evF[ci], s));
+    }
+    if ((st = timed(P, PH_COST, s, [&] { return k_cost(P, S.x, Fd, s); })) != GRAPE_OK) return st;
+    if (P->penalty) {
+        if ((st = pen_rows(P, S.x, 0, 1, P->n_slices, s)) != GRAPE_OK) return st;
+        if ((st = pen_rows(P, S.Y, (long long)per_slice, j1 - j0, j0, s, 1)) != GRAPE_OK) return st;
+    }
+    // adjoint chunks (last slices first) and their traces
+    for (int ci = nch - 1; ci >= 0; --ci) {
+        const long long cA = j0 + (j1 - j0) * ci / nch;
+        const long long cB = j0 + (j1 - j0) * (ci + 1) / nch;
+        const size_t kofs = (size_t)(cA - j0) * per_slice;
+        PropArgs b = base_args(P, 1, ud);
+        b.sub_begin = cA * P->n_rk;
+        b.sub_end = cB * P->n_rk;
+        b.reverse = 1;
+        b.x_in = S.mu;
+        b.x_out = S.mu;
+        b.stage_store = S.K + kofs;
+        if ((st = launch_prop(P, b, sa)) != GRAPE_OK) return st;
+        if (P->R == 0) continue;
+        GRAPE_CUDA_TRY(cudaEventRecord(S.ev[ci], sa));
+        GRAPE_CUDA_TRY(cudaStreamWaitEvent(ts, S.ev[ci], 0));
+        GRAPE_CUDA_TRY(cudaStreamWaitEvent(ts, S.evF[ci], 0));
+        if ((st = trace_chunk(P, S, Gd, cA, cB, kofs, ts)) != GRAPE_OK) return st;
+    }
+    GRAPE_CUDA_TRY(cudaEventRecord(S.ev[grape_problem::kMaxChunks + 1], sa));
+    GRAPE_CUDA_TRY(cudaStreamWaitEvent(s, S.ev[grape_problem::kMaxChunks + 1], 0));
+    if (P->R > 0) {
+        GRAPE_CUDA_TRY(cudaEventRecord(S.ev[grape_problem::kMaxChunks], ts));
+        GRAPE_CUDA_TRY(cudaStreamWaitEvent(s, S.ev[grape_problem::kMaxChunks], 0));
+    }
+    if (P->penalty) return pen_finish(P, Fd, s);     // Phi = Phi_0 - beta dt sum_n Tr(A rho_n)
+    return GRAPE_OK;
+}
+
 // One gradient evaluation on stream s with device pointers only: forward
 // sweep (stage storage or checkpoints), cost, then per segment (last first)
 // the recomputed forward stage inputs, the adjoint sweep in chunks and the
 // trace kernels of the finished chunks.
 grape_status run_gradient(grape_problem *P, const double *ud, double *Fd, double *Gd,
                           cudaStream_t s, const GradScratch &S) {
+    if (S.s3 && S.s2 && S.evF && concurrent_sweeps(P, S.nseg))
+        return run_gradient_concurrent(P, ud, Fd, Gd, s, S);
     grape_status st;
     const bool exact = (P->mode == GRAPE_GRAD_EXACT);
     const long long nsub = (long long)P->n_slices * P->n_rk;
-    const double dt = P->T / P->n_slices;
     const size_t mat = full_set(P);                  // a state set as full matrices
     const size_t pst = exact ? packed_set(P) : mat;  // a stored stage set (packed in exact mode)
 
@@ -1330,30 +1464,7 @@ grape_status run_gradient(grape_problem *P, const double *ud, double *Fd, double
                 GRAPE_CUDA_TRY(cudaEventRecord(S.ev[ci], s));
                 GRAPE_CUDA_TRY(cudaStreamWaitEvent(S.s2, S.ev[ci], 0));
             }
-            TraceArgs t = P->trace;
-            t.n_rows = (int)(cB - cA);
-            t.G = Gd + (size_t)cA * P->R;
-            if (exact) {
-                t.K = S.K + kofs;
-                t.Y = S.Y + kofs;
-                t.npairs = (long long)P->n_rk * 4 * P->ns;
-                t.weight = 1.0;
-            } else {
-                t.K = S.K + kofs + mat;   // lambda_{j+1}, rho_{j+1} pair with row j
-                t.Y = S.Y + kofs + mat;
-                t.npairs = P->ns;
-                t.weight = dt;
-            }
-            if (!S.part && !t.packed) t.nsplit = 1;
-            t.part = S.part ? S.part + (size_t)cA * t.nsplit * P->R : nullptr;
-            if ((st = timed(P, PH_TRACE, ts, [&] { return k_trace(P, t, ts); })) != GRAPE_OK)
-                return st;
-            if (t.nsplit > 1 &&
-                (st = timed(P, PH_TRACE, ts, [&] {
-                     return P->prec == GRAPE_PREC_FP64 ? grape_launch_trace_finish_f64(t, ts)
-                                                       : grape_launch_trace_finish_df(t, ts);
-                 })) != GRAPE_OK)
-                return st;
+            if ((st = trace_chunk(P, S, Gd, cA, cB, kofs, ts)) != GRAPE_OK) return st;
         }
         if (P->R > 0 && S.s2) {   // the segment's stage storage is reused next: join s2 into s
             GRAPE_CUDA_TRY(cudaEventRecord(S.ev[grape_problem::kMaxChunks], S.s2));
@@ -1647,13 +1758,20 @@ grape_status grape_problem_create(const grape_problem_desc *desc, grape_problem_
         cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
         if (cudaStreamCreateWithPriority(&P->s1, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
             cudaStreamCreateWithPriority(&P->s2, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&P->s3, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
             cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->ev_fork3, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             return bail(fail(GRAPE_ECUDA, "cudaStreamCreate failed"));
         }
     }
     for (auto &e : P->ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(GRAPE_ECUDA, "cudaEventCreate failed"));
+        }
+    for (auto &e : P->evF)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             return bail(fail(GRAPE_ECUDA, "cudaEventCreate failed"));
@@ -1775,7 +1893,7 @@ grape_status grape_phase_times(grape_problem_t P, double ms[4], int32_t launches
 
 int32_t grape_gradient_launches(grape_problem_t P) {
     if (!P) return -1;
-    return gradient_launch_count(P, P->seg, P->nseg);
+    return gradient_launch_count(P, P->seg, P->nseg, concurrent_sweeps(P, P->nseg));
 }
 
 grape_status grape_forward(grape_problem_t P, const double *u, double *F, double *rhoT,
@@ -1958,7 +2076,12 @@ grape_status grape_gradient(grape_problem_t P, const double *u, double *F, doubl
     bool overlap = true;
     if (const char *env = std::getenv("GRAPE_TRACE_OVERLAP")) overlap = std::atoi(env) != 0;
     S.s2 = overlap ? P->s2 : nullptr;
-    // the sweeps run on the problem's high-priority stream, ordered after and
+    if (S.s2 && concurrent_sweeps(P, P->nseg)) {
+        S.s3 = P->s3;
+        S.fork3 = P->ev_fork3;
+        S.evF = P->evF;
+    }
+    // the sweeps run on the problem's high-priority streams, ordered after and
     // before the caller's stream; the traces on its low-priority stream
     GRAPE_CUDA_TRY(cudaEventRecord(P->ev_fork, s));
     GRAPE_CUDA_TRY(cudaStreamWaitEvent(P->s1, P->ev_fork, 0));
