@@ -1143,8 +1143,9 @@ long long seg_for_budget(const grape_problem *P, size_t budget) {
 // The adjoint sweep of a segment runs in chunks of slices; the trace kernel
 // of each finished chunk runs on the problem's second stream while the next
 // chunk propagates, on the SMs the propagation leaves idle.
-int adjoint_chunks(const grape_problem *P, long long j0, long long j1) {
-    int n = 8;
+int adjoint_chunks(const grape_problem *P, long long j0, long long j1, bool concurrent = false) {
+    // concurrent sweeps: finer chunks shorten the traces left after both sweeps
+    int n = concurrent ? 16 : 8;
     if (const char *env = std::getenv("GRAPE_ADJ_CHUNKS")) n = std::atoi(env);
     n = std::max(1, std::min(n, grape_problem::kMaxChunks));
     return (int)std::min<long long>(n, j1 - j0);
@@ -1173,12 +1174,12 @@ bool concurrent_sweeps(const grape_problem *P, int nseg) {
 int gradient_launch_count(const grape_problem *P, int seg, int nseg, bool concurrent = false) {
     if (nseg <= 0) return -1;
     int n = 2;                                    // forward sweep, cost
-    if (concurrent) n += adjoint_chunks(P, 0, P->n_slices) - 1;   // the forward in chunks
+    if (concurrent) n += adjoint_chunks(P, 0, P->n_slices, true) - 1;   // the forward in chunks
     if (P->penalty) n += 3;                       // adjoint start, final-state value, sum
     for (int gi = 0; gi < nseg; ++gi) {
         const long long j0 = (long long)gi * seg;
         const long long j1 = std::min<long long>(P->n_slices, j0 + seg);
-        const int nch = adjoint_chunks(P, j0, j1);
+        const int nch = adjoint_chunks(P, j0, j1, concurrent);
         n += (nseg > 1 ? 1 : 0) + nch;
         if (P->R > 0) n += nch * (P->trace.nsplit > 1 ? 2 : 1);
         if (P->penalty) n += 1;                   // boundary values of the segment
@@ -1327,7 +1328,7 @@ grape_status run_gradient_concurrent(grape_problem *P, const double *ud, double 
     const size_t mat = full_set(P);
     const size_t pst = packed_set(P);
     const long long j0 = 0, j1 = P->n_slices;
-    const int nch = adjoint_chunks(P, j0, j1);
+    const int nch = adjoint_chunks(P, j0, j1, true);
     const size_t per_slice = (size_t)P->n_rk * 4 * pst;   // stored stage entries per slice
     cudaStream_t sa = S.s3, ts = S.s2;
     GRAPE_CUDA_TRY(cudaEventRecord(S.fork3, s));
@@ -1355,24 +1356,36 @@ grape_status run_gradient_concurrent(grape_problem *P, const double *ud, double 
         if ((st = pen_rows(P, S.x, 0, 1, P->n_slices, s)) != GRAPE_OK) return st;
         if ((st = pen_rows(P, S.Y, (long long)per_slice, j1 - j0, j0, s, 1)) != GRAPE_OK) return st;
     }
-    // adjoint chunks (last slices first) and their traces
+    // adjoint chunks (last slices first)
     for (int ci = nch - 1; ci >= 0; --ci) {
         const long long cA = j0 + (j1 - j0) * ci / nch;
         const long long cB = j0 + (j1 - j0) * (ci + 1) / nch;
-        const size_t kofs = (size_t)(cA - j0) * per_slice;
         PropArgs b = base_args(P, 1, ud);
         b.sub_begin = cA * P->n_rk;
         b.sub_end = cB * P->n_rk;
         b.reverse = 1;
         b.x_in = S.mu;
         b.x_out = S.mu;
-        b.stage_store = S.K + kofs;
+        b.stage_store = S.K + (size_t)(cA - j0) * per_slice;
         if ((st = launch_prop(P, b, sa)) != GRAPE_OK) return st;
-        if (P->R == 0) continue;
         GRAPE_CUDA_TRY(cudaEventRecord(S.ev[ci], sa));
+    }
+    // the traces in the order the chunks become ready: the forward passes
+    // chunk c after c + 1 chunks, the adjoint after nch - c, so the middle
+    // chunks are ready first and the two ends last (one in-order stream)
+    int order[grape_problem::kMaxChunks];
+    for (int c = 0; c < nch; ++c) order[c] = c;
+    std::sort(order, order + nch, [nch](int a, int b) {
+        const int ra = std::max(a + 1, nch - a), rb = std::max(b + 1, nch - b);
+        return ra != rb ? ra < rb : a < b;
+    });
+    for (int k = 0; k < nch && P->R > 0; ++k) {
+        const int ci = order[k];
+        const long long cA = j0 + (j1 - j0) * ci / nch;
+        const long long cB = j0 + (j1 - j0) * (ci + 1) / nch;
         GRAPE_CUDA_TRY(cudaStreamWaitEvent(ts, S.ev[ci], 0));
         GRAPE_CUDA_TRY(cudaStreamWaitEvent(ts, S.evF[ci], 0));
-        if ((st = trace_chunk(P, S, Gd, cA, cB, kofs, ts)) != GRAPE_OK) return st;
+        if ((st = trace_chunk(P, S, Gd, cA, cB, (size_t)(cA - j0) * per_slice, ts)) != GRAPE_OK) return st;
     }
     GRAPE_CUDA_TRY(cudaEventRecord(S.ev[grape_problem::kMaxChunks + 1], sa));
     GRAPE_CUDA_TRY(cudaStreamWaitEvent(s, S.ev[grape_problem::kMaxChunks + 1], 0));
