@@ -662,6 +662,27 @@ std::vector<int> hermitian_table(int d, int ncl, int omax, int hb, int *maxwin, 
     return tab;
 }
 
+// The compile-time band/jump layout (the kernels' Shape) that both
+// directions' tables follow: 1 transmon x resonator (bands 0, +-1 real,
+// +-Q; three jump terms), 2 resonator drives only (bands 0, +-Q; one jump
+// term), 0 none (the kernels read the counts at run time).  Real jump tables
+// only; GRAPE_SHAPE=0 turns it off.  The arithmetic is the same either way.
+int shape_id(const grape_problem *P) {
+    if (!(P->variant & 1)) return 0;
+    if (const char *env = std::getenv("GRAPE_SHAPE"))
+        if (std::atoi(env) == 0) return 0;
+    auto is = [&](int nb, int nbr, int nt) {
+        for (int dir = 0; dir < 2; ++dir) {
+            const PropTables &t = P->tab[dir];
+            if (t.nb != nb || t.nbr != nbr || t.nt != nt || t.b0 != nb - 1) return false;
+        }
+        return true;
+    };
+    if (is(5, 2, 3)) return 1;
+    if (is(3, 0, 1)) return 2;
+    return 0;
+}
+
 // Hermitian cluster kernel with `ncl` CTAs of `threads` threads per state:
 // sets the geometry, or GRAPE_EINVAL when the tile does not fit.  Tables
 // are kept per width (a captured graph may still use an earlier one).
@@ -681,7 +702,17 @@ grape_status plan_h(grape_problem *P, int ncl, int threads) {
                         (size_t)cu * sizeof(int2) + 12 * sizeof(double) + tab.size() * sizeof(int) +
                         (size_t)rt_rows * (2 * ncl + 1) * sizeof(uint32_t) +
                         (size_t)cu * (2 * nb + nt + 1) * sizeof(short);
-    const int variant = (P->variant & 1) | 2;
+    const int sh = shape_id(P);
+    const int variant = (P->variant & 1) | 2 | (sh << 2) | ((sh && cu <= threads) ? 16 : 0);
+    {
+        const cudaError_t e = P->prec == GRAPE_PREC_FP64
+                                  ? grape_prepare_prop_f64(variant, (size_t)max_smem_optin(P), 16)
+                                  : grape_prepare_prop_df(variant, (size_t)max_smem_optin(P), 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GRAPE_ECUDA, std::string("hermitian kernel attributes: ") + cudaGetErrorString(e));
+        }
+    }
     // Options, each kept only when the tile still fits (the same values, so
     // the same bits, either way): the own-entry coefficients cached per slice
     // (16 B per owned entry) instead of recomputed every stage; the next
@@ -827,7 +858,7 @@ grape_status choose_geometry_grid(grape_problem *P) {
     int maxwin = 0, cu = 0, rt_rows = 0;
     const std::vector<int> tab = hermitian_table(d, nct, P->omax, hb, &maxwin, &cu, &rt_rows);
     if (maxwin >= 32767) return fail(GRAPE_EINVAL, "state window too large for the grid propagation kernel");
-    const int variant = P->variant & 1;
+    const int variant = (P->variant & 1) | (shape_id(P) << 2);
     int njt = 0;
     for (int dir = 0; dir < 2; ++dir) {
         int n = 0;

@@ -367,33 +367,61 @@ __device__ __forceinline__ typename Num::val diag_coef(int i, int j, int d, cons
     return c;
 }
 
+// Band and jump layout known at compile time (NB bands including the
+// offset-0 band, which is last; the first NBR are real; NT jump terms), so
+// the per-entry loops unroll and the neighbour indices can live in
+// registers; ShapeAny reads the counts from the tables at run time.  The
+// host picks a shape only when both directions' tables match it.
+template <int NB_, int NBR_, int NT_>
+struct Shape {
+    static constexpr int NB = NB_, NBR = NBR_, NT = NT_;
+};
+using ShapeAny = Shape<0, 0, 0>;
+using ShapeT = Shape<5, 2, 3>;   // transmon x resonator: bands 0, +-1 (real drive), +-Q; jumps a, b, b^dag b
+using ShapeR = Shape<3, 0, 1>;   // resonator drives only: bands 0, +-Q; jump a
+template <class SH> __device__ __forceinline__ int sh_nb(const PropTables &t) { return SH::NB ? SH::NB : t.nb; }
+template <class SH> __device__ __forceinline__ int sh_nt(const PropTables &t) { return SH::NB ? SH::NT : t.nt; }
+
 // The Hamiltonian bands: the first t.nbr are real for every control value
 // (real multiply-adds: the same bits as the complex ones with a zero
 // imaginary part, half the work), the offset-0 band is last and excluded
 // (it is part of the own-entry coefficient).  x1(b), x2(b): the neighbours
 // (i + o_b, j) and (i, j + o_b).  The A X terms and the X A^+ terms go to
 // two accumulators (two independent dependency chains), added at the end.
-template <class Num, class X1, class X2>
+template <class Num, class SH, class X1, class X2>
 __device__ __forceinline__ typename Num::acc band_terms(const PropTables &t, const typename Num::store_t *A,
                                                         int i, int j, int d, X1 &&x1, X2 &&x2) {
     typename Num::acc wa = Num::acc_zero(), wb = Num::acc_zero();
-    const int nbo = (t.b0 >= 0) ? t.nb - 1 : t.nb;
+    if constexpr (SH::NB > 0) {
+#pragma unroll
+        for (int b = 0; b < SH::NBR; ++b) {
+            Num::mac_real(wa, Num::load_re(A[b * d + i]), x1(b));
+            Num::mac_real(wb, Num::neg_real(Num::load_re(A[b * d + j])), x2(b));
+        }
+#pragma unroll
+        for (int b = SH::NBR; b < SH::NB - 1; ++b) {
+            Num::mac(wa, Num::load(A[b * d + i]), x1(b));
+            Num::mac_conj_neg(wb, Num::load(A[b * d + j]), x2(b));
+        }
+    } else {
+        const int nbo = (t.b0 >= 0) ? t.nb - 1 : t.nb;
 #pragma unroll 1
-    for (int b = 0; b < t.nbr; ++b) {
-        Num::mac_real(wa, Num::load_re(A[b * d + i]), x1(b));
-        Num::mac_real(wb, Num::neg_real(Num::load_re(A[b * d + j])), x2(b));
-    }
+        for (int b = 0; b < t.nbr; ++b) {
+            Num::mac_real(wa, Num::load_re(A[b * d + i]), x1(b));
+            Num::mac_real(wb, Num::neg_real(Num::load_re(A[b * d + j])), x2(b));
+        }
 #pragma unroll 2
-    for (int b = t.nbr; b < nbo; ++b) {
-        Num::mac(wa, Num::load(A[b * d + i]), x1(b));
-        Num::mac_conj_neg(wb, Num::load(A[b * d + j]), x2(b));
+        for (int b = t.nbr; b < nbo; ++b) {
+            Num::mac(wa, Num::load(A[b * d + i]), x1(b));
+            Num::mac_conj_neg(wb, Num::load(A[b * d + j]), x2(b));
+        }
     }
     return Num::acc_add(wa, wb);
 }
 
 // jc: null, or the entry's cached coefficients of the jump terms with an
 // offset (real tables only), jc[q' * jstride] for the q'-th such term
-template <class Num, bool REALJ>
+template <class Num, bool REALJ, class SH>
 __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::store_t *cur,
                                                            const short *nb_ad, int i, int j, int d,
                                                            const PropTables &t,
@@ -407,28 +435,41 @@ __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::s
     // every term is accumulated without a branch (adding 0 changes no bit).
     // The terms on the entry itself - the offset-0 band and the jump terms
     // with both offsets 0 - come as one coefficient D_ij (diag_coef).
-    typename Num::acc w = band_terms<Num>(t, A, i, j, d, [&](int b) { return Num::load(cur[nb_ad[2 * b]]); },
-                                          [&](int b) { return Num::load(cur[nb_ad[2 * b + 1]]); });
+    const int nb = sh_nb<SH>(t), nt = sh_nt<SH>(t);
+    typename Num::acc w = band_terms<Num, SH>(t, A, i, j, d, [&](int b) { return Num::load(cur[nb_ad[2 * b]]); },
+                                              [&](int b) { return Num::load(cur[nb_ad[2 * b + 1]]); });
     w = Num::acc_minus_i(w);
-    Num::mac(w, dij, Num::load(cur[nb_ad[2 * t.nb + t.nt]]));
+    Num::mac(w, dij, Num::load(cur[nb_ad[2 * nb + nt]]));
     if (REALJ && jc) {
         int qq = 0;
-#pragma unroll 1
-        for (int q = 0; q < t.nt; ++q) {
-            if ((t.jdiag >> q) & 1) continue;
-            Num::mac_real(w, jc[qq * jstride], Num::load(cur[nb_ad[2 * t.nb + q]]));
+        auto term = [&](int q) {
+            if ((t.jdiag >> q) & 1) return;
+            Num::mac_real(w, jc[qq * jstride], Num::load(cur[nb_ad[2 * nb + q]]));
             ++qq;
+        };
+        if constexpr (SH::NB > 0) {
+#pragma unroll
+            for (int q = 0; q < SH::NT; ++q) term(q);
+        } else {
+#pragma unroll 1
+            for (int q = 0; q < nt; ++q) term(q);
         }
         return Num::raw(w);
     }
     auto jumps = [&](auto rate) {
         constexpr bool RT = decltype(rate)::value;
-#pragma unroll 1
-        for (int q = 0; q < t.nt; ++q) {
-            if ((t.jdiag >> q) & 1) continue;
-            const int aJ = nb_ad[2 * t.nb + q];
+        auto term = [&](int q) {
+            if ((t.jdiag >> q) & 1) return;
+            const int aJ = nb_ad[2 * nb + q];
             if (REALJ) Num::mac_real(w, jump_real<Num, RT>(t, q, i, j, d, vL, vR, uj), Num::load(cur[aJ]));
             else Num::mac(w, jump_cplx<Num, RT>(t, q, i, j, d, vL, vR, uj), Num::load(cur[aJ]));
+        };
+        if constexpr (SH::NB > 0) {
+#pragma unroll
+            for (int q = 0; q < SH::NT; ++q) term(q);
+        } else {
+#pragma unroll 1
+            for (int q = 0; q < nt; ++q) term(q);
         }
     };
     if (!REALJ && t.jrate) jumps(std::true_type{});
@@ -570,7 +611,10 @@ __device__ __forceinline__ void hpush_async(const uint32_t *rowtab, int rstride,
 // to 2, later waits are skipped and the results are invalid (the host
 // reports GRAPE_ETIMEOUT).  A one-CTA cluster pushes only into itself and
 // needs only the CTA barrier.
-template <class Num, bool REALJ>
+// SH: the band and jump layout (ShapeAny: from the tables); ONE: every
+// thread owns at most one upper entry (cu <= threads), so the entry's
+// neighbour indices stay in registers for the whole launch.
+template <class Num, bool REALJ, class SH, bool ONE>
 __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const PropArgs p) {
     using S = typename Num::store_t;
     using V = typename Num::val;
@@ -602,7 +646,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     const int rstride = 2 * p.ncl + 1;
     uint32_t *rowtab = reinterpret_cast<uint32_t *>(tab + p.htab_len);
     short *nbad = reinterpret_cast<short *>(rowtab + p.rt_rows * rstride);
-    const int ns = 2 * p.tab.nb + p.tab.nt;     // neighbour slots; slot ns = own address
+    const int ns = SH::NB ? 2 * SH::NB + SH::NT : 2 * p.tab.nb + p.tab.nt;   // neighbour slots; slot ns = own address
     const int nstride = ns + 1;
     const S *x_in = static_cast<const S *>(p.x_in);
     S *x_out = static_cast<S *>(p.x_out);
@@ -751,6 +795,14 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     __syncthreads();
 
     const bool unit_g = (p.g[1] == 1.0 && p.g[2] == 1.0 && p.g[3] == 1.0);   // forward RK4
+    constexpr int NSC = SH::NB ? 2 * SH::NB + SH::NT + 1 : 1;
+    short nreg[NSC];                             // ONE: the entry's neighbour indices
+    if constexpr (ONE) {
+        const bool mine = u0 + (int)threadIdx.x < u1;
+        const short *na0 = nbad + (size_t)threadIdx.x * nstride;
+#pragma unroll
+        for (int k = 0; k < NSC; ++k) nreg[k] = mine ? na0[k] : (short)0;
+    }
     int tb = 0;
     uint32_t g = 0;                              // stages done in this launch
     bool dfresh = true;                          // D table to (re)build for this slice
@@ -786,7 +838,9 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
             for (int u = u0 + threadIdx.x; u < u1; u += nth) {
                 const int li = u - u0;
                 const int2 ij = rc[li];
-                const short *na = nbad + (size_t)li * nstride;
+                const short *na;
+                if constexpr (ONE) na = nreg;
+                else na = nbad + (size_t)li * nstride;
                 if (st) st[u] = cur[na[ns]];     // the stage input itself, packed
                 // own-entry coefficient: cached per slice (the entry is thread-private,
                 // so no barrier is needed) or recomputed when there is no room
@@ -797,7 +851,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                 } else {
                     dij = diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR, uj);
                 }
-                const V w = lindblad_h_at<Num, REALJ>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij, uj,
+                const V w = lindblad_h_at<Num, REALJ, SH>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij, uj,
                                                       jcache ? jc + li : nullptr, p.cu);
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
@@ -905,7 +959,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // [cu] (int2); 12 RK coefficients; jump coefficients [njt][cu] when
 // p.jcache; htab copy (ints); neighbour addresses [cu][ns + 1] (i16).  The
 // jump tables are read from global memory.
-template <class Num, bool REALJ>
+template <class Num, bool REALJ, class SH>
 __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const PropArgs p) {
     using S = typename Num::store_t;
     using V = typename Num::val;
@@ -933,7 +987,7 @@ __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const Pro
     R *jc = cg + 12;
     int *tab = reinterpret_cast<int *>(jc + (jcache ? njt * p.cu : 0));
     short *nbad = reinterpret_cast<short *>(tab + p.htab_len);
-    const int ns = 2 * p.tab.nb + p.tab.nt;
+    const int ns = SH::NB ? 2 * SH::NB + SH::NT : 2 * p.tab.nb + p.tab.nt;
     const int nstride = ns + 1;
     const int nct = p.ncl;                       // CTAs per state
     const int rank = blockIdx.x % nct;
@@ -1083,7 +1137,7 @@ __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const Pro
                 } else {
                     dij = diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR, uj);
                 }
-                const V w = lindblad_h_at<Num, REALJ>(win, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij, uj,
+                const V w = lindblad_h_at<Num, REALJ, SH>(win, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij, uj,
                                                       jcache ? jc + li : nullptr, p.cu);
                 const V x = Num::load(xs[li]);
                 const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
@@ -1749,8 +1803,32 @@ __global__ void __launch_bounds__(256) to_double_kernel(const void *src_v, doubl
 }
 
 // ------------------------------------------------------------------ launchers
-template <class Num, bool REALJ, bool HERM>
-cudaError_t launch_prop_t(const PropArgs &p, int threads, size_t smem, cudaStream_t stream) {
+// `variant`: bit 0 the jump tables are real; bit 1 Hermitian (upper-triangle)
+// kernel; bits 2-3 the band/jump shape (0 from the tables, 1 ShapeT, 2 ShapeR;
+// only with real jump tables); bit 4 one entry per thread (with a shape).
+using PropKernel = void (*)(const PropArgs);
+
+template <class Num>
+PropKernel prop_kernel_for(int variant) {
+    const bool realj = (variant & 1) != 0, herm = (variant & 2) != 0, one = (variant & 16) != 0;
+    const int shape = (variant >> 2) & 3;
+    if (!herm) return realj ? prop_kernel<Num, true> : prop_kernel<Num, false>;
+    if (realj && shape == 1) return one ? prop_h_kernel<Num, true, ShapeT, true> : prop_h_kernel<Num, true, ShapeT, false>;
+    if (realj && shape == 2) return one ? prop_h_kernel<Num, true, ShapeR, true> : prop_h_kernel<Num, true, ShapeR, false>;
+    return realj ? prop_h_kernel<Num, true, ShapeAny, false> : prop_h_kernel<Num, false, ShapeAny, false>;
+}
+
+template <class Num>
+PropKernel grid_kernel_for(int variant) {
+    const bool realj = (variant & 1) != 0;
+    const int shape = (variant >> 2) & 3;
+    if (realj && shape == 1) return prop_g_kernel<Num, true, ShapeT>;
+    if (realj && shape == 2) return prop_g_kernel<Num, true, ShapeR>;
+    return realj ? prop_g_kernel<Num, true, ShapeAny> : prop_g_kernel<Num, false, ShapeAny>;
+}
+
+template <class Num>
+cudaError_t launch_prop(const PropArgs &p, int threads, int variant, size_t smem, cudaStream_t stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(p.n_states * p.ncl));
     cfg.blockDim = dim3((unsigned)threads);
@@ -1763,8 +1841,7 @@ cudaError_t launch_prop_t(const PropArgs &p, int threads, size_t smem, cudaStrea
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (HERM) return cudaLaunchKernelEx(&cfg, prop_h_kernel<Num, REALJ>, p);
-    return cudaLaunchKernelEx(&cfg, prop_kernel<Num, REALJ>, p);
+    return cudaLaunchKernelEx(&cfg, prop_kernel_for<Num>(variant), p);
 }
 
 // smem_total: the per-block shared-memory budget; the dynamic limit is that
@@ -1782,14 +1859,13 @@ cudaError_t prepare_kernel(K kernel, size_t smem_total, int ncl) {
     return e;
 }
 
-template <class Num, bool REALJ, bool HERM>
-cudaError_t prepare_t(size_t smem_total, int ncl) {
-    if (HERM) return prepare_kernel(prop_h_kernel<Num, REALJ>, smem_total, ncl);
-    return prepare_kernel(prop_kernel<Num, REALJ>, smem_total, ncl);
+template <class Num>
+cudaError_t prepare(int variant, size_t smem, int ncl) {
+    return prepare_kernel(prop_kernel_for<Num>(variant), smem, ncl);
 }
 
-template <class Num, bool REALJ, bool HERM>
-cudaError_t clusters_t(int threads, size_t smem, int ncl, int n_blocks, int *clusters) {
+template <class Num>
+cudaError_t max_clusters(int threads, int variant, size_t smem, int ncl, int n_blocks, int *clusters) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)n_blocks);
     cfg.blockDim = dim3((unsigned)threads);
@@ -1801,12 +1877,11 @@ cudaError_t clusters_t(int threads, size_t smem, int ncl, int n_blocks, int *clu
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (HERM) return cudaOccupancyMaxActiveClusters(clusters, prop_h_kernel<Num, REALJ>, &cfg);
-    return cudaOccupancyMaxActiveClusters(clusters, prop_kernel<Num, REALJ>, &cfg);
+    return cudaOccupancyMaxActiveClusters(clusters, prop_kernel_for<Num>(variant), &cfg);
 }
 
-template <class Num, bool REALJ>
-cudaError_t launch_grid_t(const PropArgs &p, int nblocks, size_t smem, cudaStream_t stream) {
+template <class Num>
+cudaError_t launch_grid(const PropArgs &p, int nblocks, int variant, size_t smem, cudaStream_t stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)nblocks);
     cfg.blockDim = dim3(GRAPE_GRID_THREADS);
@@ -1817,55 +1892,22 @@ cudaError_t launch_grid_t(const PropArgs &p, int nblocks, size_t smem, cudaStrea
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, prop_g_kernel<Num, REALJ>, p);
-}
-
-template <class Num>
-cudaError_t launch_grid(const PropArgs &p, int nblocks, int variant, size_t smem, cudaStream_t s) {
-    return (variant & 1) ? launch_grid_t<Num, true>(p, nblocks, smem, s)
-                         : launch_grid_t<Num, false>(p, nblocks, smem, s);
+    return cudaLaunchKernelEx(&cfg, grid_kernel_for<Num>(variant), p);
 }
 
 // prepares the grid kernel and returns how many CTAs of it fit on the device at once
 template <class Num>
 cudaError_t prepare_grid(int variant, size_t smem_total, size_t smem, int *max_blocks) {
-    cudaError_t e = (variant & 1) ? prepare_kernel(prop_g_kernel<Num, true>, smem_total, 1)
-                                  : prepare_kernel(prop_g_kernel<Num, false>, smem_total, 1);
+    const PropKernel k = grid_kernel_for<Num>(variant);
+    cudaError_t e = prepare_kernel(k, smem_total, 1);
     if (e != cudaSuccess) return e;
     int per_sm = 0, dev = 0, sms = 0;
-    e = (variant & 1) ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prop_g_kernel<Num, true>,
-                                                                      GRAPE_GRID_THREADS, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prop_g_kernel<Num, false>,
-                                                                      GRAPE_GRID_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, GRAPE_GRID_THREADS, smem);
     if (e != cudaSuccess) return e;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     *max_blocks = per_sm * sms;
     return cudaSuccess;
-}
-
-// `variant` bit 0: the jump tables are real; bit 1: Hermitian (upper-triangle) kernel.
-#define GRAPE_VARIANT_DISPATCH(FN, ...)                                   \
-    switch (variant & 3) {                                                \
-    case 0: return FN<Num, false, false>(__VA_ARGS__);                    \
-    case 1: return FN<Num, true, false>(__VA_ARGS__);                     \
-    case 2: return FN<Num, false, true>(__VA_ARGS__);                     \
-    default: return FN<Num, true, true>(__VA_ARGS__);                     \
-    }
-
-template <class Num>
-cudaError_t launch_prop(const PropArgs &p, int threads, int variant, size_t smem, cudaStream_t s) {
-    GRAPE_VARIANT_DISPATCH(launch_prop_t, p, threads, smem, s)
-}
-
-template <class Num>
-cudaError_t prepare(int variant, size_t smem, int ncl) {
-    GRAPE_VARIANT_DISPATCH(prepare_t, smem, ncl)
-}
-
-template <class Num>
-cudaError_t max_clusters(int threads, int variant, size_t smem, int ncl, int n_blocks, int *clusters) {
-    GRAPE_VARIANT_DISPATCH(clusters_t, threads, smem, ncl, n_blocks, clusters)
 }
 
 template <class Num>
