@@ -421,7 +421,7 @@ __device__ __forceinline__ typename Num::acc band_terms(const PropTables &t, con
 
 // jc: null, or the entry's cached coefficients of the jump terms with an
 // offset (real tables only), jc[q' * jstride] for the q'-th such term
-template <class Num, bool REALJ, class SH>
+template <class Num, bool REALJ, class SH, bool JQ = false>
 __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::store_t *cur,
                                                            const short *nb_ad, int i, int j, int d,
                                                            const PropTables &t,
@@ -444,7 +444,9 @@ __device__ __forceinline__ typename Num::val lindblad_h_at(const typename Num::s
         int qq = 0;
         auto term = [&](int q) {
             if ((t.jdiag >> q) & 1) return;
-            Num::mac_real(w, jc[qq * jstride], Num::load(cur[nb_ad[2 * nb + q]]));
+            // JQ: coefficient q of a per-term array (registers); else the
+            // qq-th term with an offset in the per-entry cache
+            Num::mac_real(w, jc[(JQ ? q : qq) * jstride], Num::load(cur[nb_ad[2 * nb + q]]));
             ++qq;
         };
         if constexpr (SH::NB > 0) {
@@ -796,12 +798,33 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
 
     const bool unit_g = (p.g[1] == 1.0 && p.g[2] == 1.0 && p.g[3] == 1.0);   // forward RK4
     constexpr int NSC = SH::NB ? 2 * SH::NB + SH::NT + 1 : 1;
-    short nreg[NSC];                             // ONE: the entry's neighbour indices
+    constexpr int NJQ = SH::NB ? SH::NT : 1;
+    // ONE: the entry's neighbour indices, row and column, base value, RK
+    // accumulator, own-entry coefficient and jump coefficients in registers
+    short nreg[NSC];
+    int2 ijr = make_int2(0, 0);
+    V xr = Num::zero(), ar = Num::zero(), dr = Num::zero();
+    R jreg[NJQ];
+#pragma unroll
+    for (int q = 0; q < NJQ; ++q) jreg[q] = Num::real_const(0.0);
     if constexpr (ONE) {
         const bool mine = u0 + (int)threadIdx.x < u1;
         const short *na0 = nbad + (size_t)threadIdx.x * nstride;
 #pragma unroll
         for (int k = 0; k < NSC; ++k) nreg[k] = mine ? na0[k] : (short)0;
+        if (mine) {
+            ijr = rc[threadIdx.x];
+            xr = Num::load(xs[threadIdx.x]);
+            if (jcache) {
+                int qq = 0;
+#pragma unroll
+                for (int q = 0; q < NJQ; ++q) {
+                    if ((p.tab.jdiag >> q) & 1) continue;
+                    jreg[q] = jc[qq * p.cu + threadIdx.x];
+                    ++qq;
+                }
+            }
+        }
     }
     int tb = 0;
     uint32_t g = 0;                              // stages done in this launch
@@ -837,7 +860,7 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
 #pragma unroll 1
             for (int u = u0 + threadIdx.x; u < u1; u += nth) {
                 const int li = u - u0;
-                const int2 ij = rc[li];
+                const int2 ij = ONE ? ijr : rc[li];
                 const short *na;
                 if constexpr (ONE) na = nreg;
                 else na = nbad + (size_t)li * nstride;
@@ -845,23 +868,33 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                 // own-entry coefficient: cached per slice (the entry is thread-private,
                 // so no barrier is needed) or recomputed when there is no room
                 V dij;
-                if (p.fold) {
+                if constexpr (ONE) {
+                    if (s == 0 && dfresh) dr = diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR, uj);
+                    dij = dr;
+                } else if (p.fold) {
                     if (s == 0 && dfresh) Dt[li] = Num::store(diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR, uj));
                     dij = Num::load(Dt[li]);
                 } else {
                     dij = diag_coef<Num, REALJ>(ij.x, ij.y, d, p.tab, A, vL, vR, uj);
                 }
-                const V w = lindblad_h_at<Num, REALJ, SH>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij, uj,
+                V w;
+                if constexpr (ONE)
+                    w = lindblad_h_at<Num, REALJ, SH, true>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij, uj,
+                                                            jcache ? jreg : nullptr, 1);
+                else
+                    w = lindblad_h_at<Num, REALJ, SH>(cur, na, ij.x, ij.y, d, p.tab, A, vL, vR, dij, uj,
                                                       jcache ? jc + li : nullptr, p.cu);
-                const V x = Num::load(xs[li]);
-                const V acc = Num::axpy(as_, w, s == 0 ? x : Num::load(as[li]));
+                const V x = ONE ? xr : Num::load(xs[li]);
+                const V acc = Num::axpy(as_, w, s == 0 ? x : (ONE ? ar : Num::load(as[li])));
                 V z;
                 if (s < 3) {
-                    as[li] = Num::store(acc);
+                    if constexpr (ONE) ar = acc;
+                    else as[li] = Num::store(acc);
                     z = unit_g ? Num::axpy(cb[s + 1], w, x) : Num::lin2(cg[s + 1], x, cb[s + 1], w);
                 } else {
                     const V nx = with_source<Num>(p, n, ij.x, ij.y, acc);
-                    xs[li] = Num::store(nx);
+                    xs[li] = Num::store(nx);         // kept for the boundary and final stores
+                    if constexpr (ONE) xr = nx;
                     z = Num::scale(cg[0], nx);
                 }
                 if (p.defer) {
