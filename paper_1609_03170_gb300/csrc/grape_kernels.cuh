@@ -503,7 +503,8 @@ __device__ __forceinline__ void hpush_pre(const uint32_t *rowtab, int rstride, i
 // mbarrier of that window (complete_tx), so the writer never waits for the
 // store to complete; the reader waits on its own mbarrier until every byte
 // its window expects in the phase has arrived.  Pushes into the CTA's own
-// window are ordinary shared-memory stores (ordered by the CTA barrier).
+// window are ordinary shared-memory stores, published by every thread's
+// arrival (release) on the same mbarrier.
 __device__ __forceinline__ void st_async16(uint32_t addr, float4 v, uint32_t mbar) {
     asm volatile("st.async.weak.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
                  ::"r"(addr), "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
@@ -533,6 +534,13 @@ __device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
     asm volatile("{\n\t.reg .b64 st;\n\t"
                  "mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(mbar),
                  "r"(bytes)
+                 : "memory");
+}
+// a plain arrival (release: the arriving thread's earlier shared-memory
+// stores are visible to a thread whose wait on the phase succeeds)
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("{\n\t.reg .b64 st;\n\t"
+                 "mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(mbar)
                  : "memory");
 }
 // bounded wait for the phase of the given parity: false when it gave up
@@ -598,16 +606,18 @@ __device__ __forceinline__ void hpush_async(const uint32_t *rowtab, int rstride,
 // window (g + 1) mod 2.  Synchronisation per stage (cluster of ncl > 1):
 //  - wait on the window's mbarrier: every byte that peers push into it for
 //    this stage has landed (one thread announced the count when the phase
-//    began, 16 B per window slot a peer owns); own-CTA pushes are ordered by
-//    the CTA barrier that ends the previous stage;
+//    began, 16 B per window slot a peer owns) and every thread of the CTA
+//    arrived after its own pushes into it (a phase needs 1 + blockDim.x
+//    arrivals), so no CTA barrier separates the stages;
 //  - compute the owned entries (their next values wait in the z row);
 //  - wait on the cluster barrier that every thread arrived at after
 //    computing the previous stage: no peer still reads the window the
 //    pushes below overwrite.  Its latency is hidden behind the compute
 //    (tiles without room for the z row wait before computing and push each
 //    entry as it is computed: the same values);
-//  - push, arrive at the cluster barrier (relaxed: it orders nothing), CTA
-//    barrier.
+//  - push, arrive on the next window's mbarrier, arrive at the cluster
+//    barrier (relaxed: it orders nothing); a CTA barrier follows only the
+//    per-slice rebuild of the band table.
 // No release fence waits for the pushes or the stage stores.  Every
 // mbarrier wait is bounded: when one gives up, the error word gbar[2] is set
 // to 2, later waits are skipped and the results are invalid (the host
@@ -665,8 +675,10 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
     if (threadIdx.x == 0) {
         s_count = 0;
         s_err = 0;
-        mbar_init(mbar_sa, 1);
-        mbar_init(mbar_sa + 8, 1);
+        // per phase: the announcing arrival (expect_tx) and one arrival of
+        // every thread after its pushes into the window
+        mbar_init(mbar_sa, 1u + (uint32_t)blockDim.x);
+        mbar_init(mbar_sa + 8, 1u + (uint32_t)blockDim.x);
         mbar_init_fence();
     }
     for (int i = threadIdx.x; i < p.htab_len; i += nth) tab[i] = __ldg(&p.htab[i]);
@@ -793,7 +805,10 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
         if (ij.y > ij.x && ij.y - ij.x <= hb)
             hpush_async(rowtab, rstride, ij.y - rfirst, ij.x, 0u, 0u, conj_store<Num>(z));
     }
-    if (clu) cluster_arrive_relaxed();
+    if (clu) {
+        mbar_arrive(mbar_sa);
+        cluster_arrive_relaxed();
+    }
     __syncthreads();
 
     const bool unit_g = (p.g[1] == 1.0 && p.g[2] == 1.0 && p.g[3] == 1.0);   // forward RK4
@@ -922,12 +937,19 @@ __global__ void __launch_bounds__(GRAPE_PROP_THREADS, 1) prop_h_kernel(const Pro
                 const int jn = (int)(nn / p.n_rk);
                 if (jn != jcur) {
                     build_bands<Num>(bands + (tb ^ 1) * nbd, p, jn);
+                    __syncthreads();             // the new table before the next stage reads it
                     jcur = jn;
                     flip = true;
                 }
             }
-            if (clu) cluster_arrive_relaxed();
-            __syncthreads();
+            if (clu) {
+                // the own-window pushes reach the CTA's readers through the
+                // window's mbarrier (every thread arrives after its pushes)
+                mbar_arrive(mbar_sa + moff);
+                cluster_arrive_relaxed();
+            } else {
+                __syncthreads();
+            }
             ++g;
         }
         if (flip) tb ^= 1;
@@ -1553,11 +1575,6 @@ __global__ void __launch_bounds__(256) trace_packed_fast_kernel(const TraceArgs 
 #define GRAPE_TRACE_CONSUMERS 8
 #define GRAPE_TRACE_THREADS (32 * (GRAPE_TRACE_CONSUMERS + 1))
 
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-    asm volatile("{\n\t.reg .b64 st;\n\t"
-                 "mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(mbar)
-                 : "memory");
-}
 // bounded wait that also gives up once *stop is set (by another thread)
 __device__ __forceinline__ bool mbar_wait_or_stop(uint32_t mbar, uint32_t parity, long long cycles,
                                                   volatile int *stop) {
