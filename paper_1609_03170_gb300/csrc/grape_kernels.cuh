@@ -1124,11 +1124,13 @@ __global__ void __launch_bounds__(GRAPE_GRID_THREADS, 1) prop_g_kernel(const Pro
     const int nnb = nbr[0];
     int band_next = -1;                          // slice whose bands are rebuilt at the next stage
     auto wait_and_load = [&](unsigned round, const S *src) {
-        if (threadIdx.x == 0 && !s_err && p.spin_limit <= 0) {   // a limit of zero polls gives up at once
-            atomicExch(&p.gbar[2], 1u);
-            s_err = 1;
+        if (p.spin_limit <= 0) {                 // a limit of zero polls gives up at once
+            if (threadIdx.x == 0 && !s_err) {
+                atomicExch(&p.gbar[2], 1u);
+                s_err = 1;
+            }
+            __syncthreads();                     // s_err as thread 0 left it
         }
-        __syncthreads();                         // s_err as thread 0 left it
         if (threadIdx.x < nnb && !s_err) {       // one thread per neighbour, all at once
             const unsigned *f = &flags[nbr[1 + threadIdx.x]];
             long long it = 0;

@@ -374,3 +374,30 @@ def test_jaynes_cummings_fig2_workload(gp, d, mode):
     assert rel(r, r_ref) < TOL
     F2, G = P.gradient(w.u)
     assert abs(F2 - F_ref) < TOL * max(abs(F_ref), 1e-300) and rel(G, G_ref) < TOL
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("make", [lambda: workloads.transmon_resonator_d120(n_slices=6),
+                                  lambda: workloads.batch_problem(2, n_slices=6),
+                                  lambda: workloads.qubit_resonator_d20(n_slices=9)],
+                         ids=["transmon_shape", "resonator_shape_d92", "resonator_shape_d20"])
+@pytest.mark.parametrize("kernel", ["cluster", "grid"])
+def test_shape_specialised_kernels_equal_runtime_shape(gp, prec, make, kernel):
+    """The propagation kernels specialised on a model's band/jump layout
+    (compile-time loops, neighbour indices and entry state in registers)
+    run the same arithmetic in the same order as the kernels that read the
+    layout at run time (GRAPE_SHAPE=0): the same bits, on the cluster and on
+    the grid kernel."""
+    w = make()
+    kern = None if kernel == "cluster" else "grid"
+    with with_env(GRAPE_KERNEL=kern):
+        P1 = gp.GrapeProblem.from_workload(w, precision=prec)
+    with with_env(GRAPE_KERNEL=kern, GRAPE_SHAPE=0):
+        P0 = gp.GrapeProblem.from_workload(w, precision=prec)
+    F1, G1 = P1.gradient(w.u)
+    F0, G0 = P0.gradient(w.u)
+    P1.status()
+    P0.status()
+    assert np.all(np.isfinite(G1))
+    assert F1 == F0 and np.array_equal(G1, G0)
+    assert np.array_equal(P1.forward(w.u)[1], P0.forward(w.u)[1])
