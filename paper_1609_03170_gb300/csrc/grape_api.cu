@@ -1052,6 +1052,10 @@ void trace_layout(const grape_problem *P, TraceArgs *t) {
 grape_status trace_tiles(grape_problem *P, TraceArgs *t) {
     t->err = P->d_gbar + 2;
     t->tile = 0;
+    // bound of the staged kernel's copy waits: about a second of SM clocks;
+    // GRAPE_TRACE_SPIN=n overrides it (0 gives up at once: the error path)
+    t->spin = 1LL << 31;
+    if (const char *env = std::getenv("GRAPE_TRACE_SPIN")) t->spin = std::max(0LL, std::atoll(env));
     if (!t->packed) return GRAPE_OK;
     const int d = P->d;
     if (d > 65535) return fail(GRAPE_EINVAL, "d above 65535 (16-bit row and column indices)");
@@ -1143,7 +1147,8 @@ grape_status trace_tiles(grape_problem *P, TraceArgs *t) {
                                        w16[6] | w16[7] << 16);
         }
     }
-    // buffers: as many (2 to 4) as keep two CTAs per SM, else two at one CTA per SM
+    // buffers: as many (2 to 4) as fit 104 KB (two CTAs per SM), else two at
+    // one CTA per SM (a 108 KB budget, 4 buffers at d=120, measured 7 % slower)
     int nbuf = 0;
     for (int n = 4; n >= 2 && !nbuf; --n)
         if (trace_tile_smem(n, kcap) <= 104 * 1024) nbuf = n;

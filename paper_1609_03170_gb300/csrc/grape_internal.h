@@ -151,6 +151,7 @@ struct TraceArgs {
                                     // buffer indices (bit 15: conjugate of the mirror; 0xffff: none)
     const unsigned *tij;            // [NU]: i | j << 16 of packed entry u
     unsigned *err;                  // error word: 3 when a copy wait gave up
+    long long spin;                 // SM cycles a copy wait may take (0: give up at once)
 };
 
 // dynamic shared memory of the staged trace kernel: 8 mbarriers, the

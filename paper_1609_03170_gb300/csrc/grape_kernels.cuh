@@ -1624,7 +1624,8 @@ __global__ void __launch_bounds__(GRAPE_TRACE_THREADS, 2) trace_tile_kernel(cons
     const S *Yp = static_cast<const S *>(p.Y) + (row_base + state) * NU;
     const S *Kp = static_cast<const S *>(p.K) + (row_base + state) * NU;
     const S *cbs = static_cast<const S *>(p.cb_s);
-    const long long limit = 1LL << 31;
+    const long long limit = p.spin;                  // the pipeline's waits
+    const long long drain = 1LL << 31;               // waits for copies already issued
 
     if (tid == 0) {
         for (int b = 0; b < nbuf; ++b) {
@@ -1638,9 +1639,10 @@ __global__ void __launch_bounds__(GRAPE_TRACE_THREADS, 2) trace_tile_kernel(cons
         for (int c = 0; c < GRAPE_MAXCB; ++c) Zsm[c * 256 + tid] = Num::acc_zero();
     __syncthreads();
 
+    int issued = 0;                                  // producer: steps whose copies it issued
     if (warp == GRAPE_TRACE_CONSUMERS) {
         // ---- producer: one step per (block, pair), nbuf - 1 ahead of the slowest consumer
-        int buf = 0, use = 0, issued = 0;
+        int buf = 0, use = 0;
         bool stop = false;
         for (int st = 0; st < total && !stop; ++st) {
             const bool ok = use == 0 || mbar_wait_or_stop(empty0 + 8u * buf, (uint32_t)((use - 1) & 1), limit, &s_stop);
@@ -1674,11 +1676,6 @@ __global__ void __launch_bounds__(GRAPE_TRACE_THREADS, 2) trace_tile_kernel(cons
                 buf = 0;
                 ++use;
             }
-        }
-        if (stop && lane == 0) {
-            // no CTA leaves while a copy it issued may still write its shared memory
-            for (int st = max(0, issued - nbuf); st < issued; ++st)
-                mbar_wait(full0 + 8u * (st % nbuf), (uint32_t)((st / nbuf) & 1), limit);
         }
     } else {
         // ---- consumers
@@ -1761,7 +1758,15 @@ __global__ void __launch_bounds__(GRAPE_TRACE_THREADS, 2) trace_tile_kernel(cons
         }
     }
     __syncthreads();
-    if (s_stop) return;
+    if (s_stop) {
+        // a wait gave up somewhere: no CTA leaves while a copy it issued may
+        // still write its shared memory (the last nbuf steps' full phases)
+        if (warp == GRAPE_TRACE_CONSUMERS && lane == 0)
+            for (int st = max(0, issued - nbuf); st < issued; ++st)
+                mbar_wait(full0 + 8u * (st % nbuf), (uint32_t)((st / nbuf) & 1), drain);
+        __syncthreads();
+        return;
+    }
     A Z[GRAPE_MAXCB];
 #pragma unroll
     for (int c = 0; c < GRAPE_MAXCB; ++c) Z[c] = tid < 256 ? Zsm[c * 256 + tid] : Num::acc_zero();

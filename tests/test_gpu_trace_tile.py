@@ -79,3 +79,29 @@ def test_staged_trace_equals_global_trace(torch_cuda, name, make, precision):
     assert np.all(np.isfinite(G_t))
     assert F_t == F_f
     assert np.array_equal(G_t, G_f), float(np.abs(G_t - G_f).max())
+
+
+def test_copy_wait_timeout_returns_error_and_context_survives(torch_cuda):
+    """A copy-wait limit of zero makes the staged trace kernel's waits give
+    up at once (the producer still waits, with the normal limit, for the
+    copies it issued before its CTA leaves): grape_gradient reports
+    GRAPE_ETIMEOUT instead of returning a wrong gradient, and the device
+    stays usable for the next problem."""
+    from paper_1609_03170_gb300 import GrapeProblem, _lib
+    w = workloads.transmon_resonator_d120(n_slices=4)
+    old = os.environ.get("GRAPE_TRACE_SPIN")
+    os.environ["GRAPE_TRACE_SPIN"] = "0"
+    try:
+        P = GrapeProblem.from_workload(w)
+    finally:
+        if old is None:
+            os.environ.pop("GRAPE_TRACE_SPIN", None)
+        else:
+            os.environ["GRAPE_TRACE_SPIN"] = old
+    with pytest.raises(_lib.GrapeError) as e:
+        P.gradient(np.ascontiguousarray(w.u))
+    assert e.value.status == _lib.GRAPE_ETIMEOUT
+    P.status()                                   # flag cleared after the report
+    F1, G1 = GrapeProblem.from_workload(w).gradient(np.ascontiguousarray(w.u))
+    F2, G2 = GrapeProblem.from_workload(w).gradient(np.ascontiguousarray(w.u))
+    assert F1 == F2 and np.array_equal(G1, G2) and np.all(np.isfinite(G1))
