@@ -3,24 +3,29 @@
 // (grape_kernels_f64.cu) and double-float on the FP32 pipes
 // (grape_kernels_df.cu).
 //
-//  prop_kernel   RK4 propagation of one density matrix (forward, Sec. 3
-//                Eq. rkmaster) or of its adjoint (backward, Eq. lambda) per
-//                thread-block cluster.  The d x d matrix is split into
-//                contiguous chunks of its row-major flat index, one per CTA
-//                of the cluster.  Each CTA keeps the current stage input of
-//                its chunk plus a halo of omax*(d+1) entries on both sides in
-//                shared memory; new stage values are pushed into the
-//                neighbours' halos with distributed-shared-memory stores and
-//                one cluster barrier separates consecutive RK stages.  The
-//                slice's Hamiltonian bands A(u_j) are rebuilt in shared
-//                memory once per slice.  Stage inputs (forward y_s, adjoint
-//                kb_s) and slice-boundary states are streamed to HBM for the
-//                gradient.
-//  trace_kernel  per-slice gradient reduction of Eq. (dphidu): one CTA per
-//                slice, row dot-products of K and conj(Y) on the control
-//                bands, lane-private accumulation, warp-shuffle plus a
-//                fixed-order shared-memory tree (deterministic).
-//  cost_kernel   Phi = sum_s Re Tr(sigma_s rho_s(T)) (Eq. phi), fixed order.
+//  prop_h_kernel  RK4 propagation (forward, Sec. 3 Eq. rkmaster, or the exact
+//                 adjoint, Eq. lambda) of one density matrix per thread-block
+//                 cluster, upper triangle only (every stage value is
+//                 Hermitian); the state stays in the cluster's shared memory
+//                 as compact row windows, halo values are pushed with st.async
+//                 and counted on the receiving window's mbarrier.  The default
+//                 kernel; specialised on the band/jump layout (Shape) and on
+//                 one entry per thread.
+//  prop_kernel    the same over contiguous chunks of the full matrix (when the
+//                 Hermitian windows do not fit).
+//  prop_g_kernel  the Hermitian kernel's arithmetic over CTAs of the whole
+//                 device, for states beyond a cluster's shared memory: stage
+//                 values in global memory (L2), row windows loaded per stage,
+//                 neighbour-to-neighbour flags with bounded waits.
+//  trace_tile_kernel, trace_packed_fast_kernel, trace_packed_kernel
+//                 per-slice gradient traces of Eq. (dphidu) on the packed
+//                 stage storage (the first stages the operands in shared
+//                 memory through a warp-specialised TMA pipeline); fixed
+//                 (state, chunk) partials summed in order by
+//                 trace_finish_kernel, so no bit depends on the launch.
+//  trace_kernel   the first-order gradient's traces on full matrices.
+//  cost_kernel    Phi = sum_s Re Tr(sigma_s rho_s(T)) (Eq. phi), fixed order.
+//  penalty kernels, add_diag_kernel  the running-cost penalty (App. B).
 //  to_double_kernel  storage format -> complex128 (rho(T) output).
 #pragma once
 
