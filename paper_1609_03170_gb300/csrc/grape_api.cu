@@ -1053,7 +1053,8 @@ grape_status trace_tiles(grape_problem *P, TraceArgs *t) {
     t->err = P->d_gbar + 2;
     t->tile = 0;
     // bound of the staged kernel's copy waits: about a second of SM clocks;
-    // GRAPE_TRACE_SPIN=n overrides it (0 gives up at once: the error path)
+    // GRAPE_TRACE_SPIN=n overrides it (0: every wait gives up at once, the
+    // error path; the copies already issued are still waited for)
     t->spin = 1LL << 31;
     if (const char *env = std::getenv("GRAPE_TRACE_SPIN")) t->spin = std::max(0LL, std::atoll(env));
     if (!t->packed) return GRAPE_OK;

@@ -392,7 +392,8 @@ template <class SH> __device__ __forceinline__ int sh_nt(const PropTables &t) { 
 // imaginary part, half the work), the offset-0 band is last and excluded
 // (it is part of the own-entry coefficient).  x1(b), x2(b): the neighbours
 // (i + o_b, j) and (i, j + o_b).  The A X terms and the X A^+ terms go to
-// two accumulators (two independent dependency chains), added at the end.
+// two accumulators (two independent dependency chains), added at the end
+// (four, real and complex bands apart, measured 3 % slower).
 template <class Num, class SH, class X1, class X2>
 __device__ __forceinline__ typename Num::acc band_terms(const PropTables &t, const typename Num::store_t *A,
                                                         int i, int j, int d, X1 &&x1, X2 &&x2) {
@@ -1582,9 +1583,11 @@ __global__ void __launch_bounds__(256) trace_packed_fast_kernel(const TraceArgs 
 #define GRAPE_TRACE_CONSUMERS 8
 #define GRAPE_TRACE_THREADS (32 * (GRAPE_TRACE_CONSUMERS + 1))
 
-// bounded wait that also gives up once *stop is set (by another thread)
+// bounded wait that also gives up once *stop is set (by another thread); a
+// limit of zero gives up at once, whether or not the phase has completed
 __device__ __forceinline__ bool mbar_wait_or_stop(uint32_t mbar, uint32_t parity, long long cycles,
                                                   volatile int *stop) {
+    if (cycles <= 0) return false;
     const long long t0 = clock64();
     for (;;) {
         uint32_t done;
