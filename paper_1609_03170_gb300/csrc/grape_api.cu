@@ -723,6 +723,7 @@ grape_status plan_h(grape_problem *P, int ncl, int threads) {
     bool want_fold = true, want_defer = false, want_jc = (variant & 1) != 0;
     if (const char *env = std::getenv("GRAPE_FOLD")) want_fold = std::atoi(env) != 0;
     if (const char *env = std::getenv("GRAPE_DEFER")) want_defer = std::atoi(env) != 0;   // off: measured slower
+    if (variant & 16) want_defer = false;        // one entry per thread: the wait stays before the compute
     if (const char *env = std::getenv("GRAPE_JCACHE")) want_jc = want_jc && std::atoi(env) != 0;
     int njt = 0;
     for (int q = 0; q < P->tab[0].nt; ++q) njt += ((P->tab[0].jdiag >> q) & 1) ? 0 : 1;

@@ -615,15 +615,16 @@ __device__ __forceinline__ void hpush_async(const uint32_t *rowtab, int rstride,
 //    began, 16 B per window slot a peer owns) and every thread of the CTA
 //    arrived after its own pushes into it (a phase needs 1 + blockDim.x
 //    arrivals), so no CTA barrier separates the stages;
-//  - compute the owned entries (their next values wait in the z row);
 //  - wait on the cluster barrier that every thread arrived at after
 //    computing the previous stage: no peer still reads the window the
-//    pushes below overwrite.  Its latency is hidden behind the compute
-//    (tiles without room for the z row wait before computing and push each
-//    entry as it is computed: the same values);
-//  - push, arrive on the next window's mbarrier, arrive at the cluster
-//    barrier (relaxed: it orders nothing); a CTA barrier follows only the
-//    per-slice rebuild of the band table.
+//    pushes below overwrite;
+//  - compute the owned entries and push each as it is computed;
+//  - arrive on the next window's mbarrier, arrive at the cluster barrier
+//    (relaxed: it orders nothing); a CTA barrier follows only the per-slice
+//    rebuild of the band table.
+// With p.defer (tiles with several entries per thread) the next values wait
+// in the z row and the cluster wait comes after the compute, just before
+// the pushes (the same values; measured slower, off by default).
 // No release fence waits for the pushes or the stage stores.  Every
 // mbarrier wait is bounded: when one gives up, the error word gbar[2] is set
 // to 2, later waits are skipped and the results are invalid (the host

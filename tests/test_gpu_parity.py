@@ -401,3 +401,25 @@ def test_shape_specialised_kernels_equal_runtime_shape(gp, prec, make, kernel):
     assert np.all(np.isfinite(G1))
     assert F1 == F0 and np.array_equal(G1, G0)
     assert np.array_equal(P1.forward(w.u)[1], P0.forward(w.u)[1])
+
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_deferred_cluster_wait_equals_default(gp, prec):
+    """The Hermitian kernel with the cluster wait placed after the compute
+    (GRAPE_DEFER=1, tiles with several entries per thread: the next values
+    wait in a shared-memory row) only moves a barrier: the same bits as the
+    default placement."""
+    w = workloads.transmon_resonator_d120(n_slices=6)
+    with with_env(GRAPE_CLUSTER=4):
+        P1 = gp.GrapeProblem.from_workload(w, precision=prec)
+    with with_env(GRAPE_CLUSTER=4, GRAPE_DEFER=1):
+        P0 = gp.GrapeProblem.from_workload(w, precision=prec)
+    assert P1.geometry() == P0.geometry() and P1.geometry()[2] > 1
+    F1, G1 = P1.gradient(w.u)
+    F0, G0 = P0.gradient(w.u)
+    P1.status()
+    P0.status()
+    assert np.all(np.isfinite(G1))
+    assert F1 == F0 and np.array_equal(G1, G0)
+    assert np.array_equal(P1.forward(w.u)[1], P0.forward(w.u)[1])
