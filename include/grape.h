@@ -194,7 +194,10 @@ grape_status grape_problem_set_penalty(grape_problem_t problem, const double *di
  * see grape_batch_create).  Errors: GRAPE_EINVAL (values out of range, a
  * grid-kernel problem, or a tile whose state window does not fit in shared
  * memory or of which no cluster can be resident; the tile is unchanged),
- * GRAPE_ECUDA. */
+ * GRAPE_ECUDA.  The tile chosen at create is the widest useful cluster
+ * (shortest stage latency) with 512 threads per CTA or, when one CTA holds
+ * a whole state on the Hermitian kernel, the state's upper entries
+ * rounded up to whole warps (at least 64 threads). */
 grape_status grape_problem_set_tile(grape_problem_t problem, int32_t cluster, int32_t threads);
 
 /* Which propagation kernel the problem runs on: 0 = Hermitian cluster kernel
