@@ -6,7 +6,8 @@
 // geometry, the segment plan of the gradient (stage storage or checkpoints
 // plus recomputation) and the launch sequence of grape_forward and
 // grape_gradient.  All arithmetic of the propagation and of the gradient
-// runs in the kernels of grape_kernels.cu.
+// runs in the kernels of grape_kernels.cuh (instantiated per number type by
+// grape_kernels_df.cu and grape_kernels_f64.cu).
 #include "grape.h"
 #include "grape_internal.h"
 #include "grape_num.cuh"
