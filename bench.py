@@ -171,13 +171,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_sha():
+def kernel_source_sha(csrc=None):
     """sha256 over the kernel sources with comments, trailing blanks and
     empty lines removed (the profile summaries record it): any change of the
     code invalidates a recorded traffic figure, an edit of a comment does not."""
+    csrc = csrc or os.path.join(ROOT, "paper_1609_03170_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("grape_kernels.cuh", "grape_num.cuh", "grape_internal.h"):
-        text = open(os.path.join(ROOT, "paper_1609_03170_gb300", "csrc", f)).read()
+        text = open(os.path.join(csrc, f)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
         h.update("\n".join(ln for ln in lines if ln).encode())

@@ -67,3 +67,24 @@ def test_reference_arm_prints_the_contract_line():
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_kernel_fingerprint_ignores_comments_and_sees_code(tmp_path):
+    """The traffic figure of a committed ncu summary is used only while the
+    kernel code it was taken on is unchanged: the fingerprint must not move
+    when only comments or blank lines change, and must move with the code."""
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    src = os.path.join(ROOT, "paper_1609_03170_gb300", "csrc")
+    for f in ("grape_kernels.cuh", "grape_num.cuh", "grape_internal.h"):
+        shutil.copy(os.path.join(src, f), tmp_path / f)
+    base = bench.kernel_source_sha(str(tmp_path))
+    assert base == bench.kernel_source_sha()
+    k = tmp_path / "grape_kernels.cuh"
+    text = k.read_text()
+    k.write_text("// a new comment line\n\n" + text.replace("\n", "   \n", 3) + "/* block\n comment */\n")
+    assert bench.kernel_source_sha(str(tmp_path)) == base
+    k.write_text(text.replace("mbar_init(mbar_sa, 1u + (uint32_t)blockDim.x);",
+                              "mbar_init(mbar_sa, 2u + (uint32_t)blockDim.x);", 1))
+    assert bench.kernel_source_sha(str(tmp_path)) != base
