@@ -142,7 +142,7 @@ def test_tile_does_not_change_bits(gp, prec, herm):
         P = gp.GrapeProblem.from_workload(w, precision=prec)
     F0, G0 = P.gradient(w.u)
     r0 = P.forward(w.u)[1]
-    for c, t in ((8, 128), (16, 64), (16, 256), (8, 512)):
+    for c, t in ((8, 128), (16, 64), (16, 256), (8, 512), (16, 480)):
         P.set_tile(c, t)
         assert P.geometry()[:2] == (c, t)
         F, G = P.gradient(w.u)
@@ -168,12 +168,14 @@ def test_cached_and_recomputed_own_coefficients_agree(gp, prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_single_cta_tiles_match_oracle(gp, prec):
-    """d=20 with one CTA per state and 64 or 96 threads (several entries per
-    thread, a ragged last pass) against the C oracle."""
+    """d=20 with one CTA per state: the tile chosen at create (threads for
+    the 210 upper entries rounded up to whole warps) and 64 or 96 threads
+    (several entries per thread, a ragged last pass) against the C oracle."""
     w = workloads.qubit_resonator_d20(n_slices=40)
     F_ref, G_ref, r_ref, _ = sparse.run_workload(w, threads=2)
     P = gp.GrapeProblem.from_workload(w, precision=prec)
-    for c, t in ((1, 64), (1, 96), (2, 160)):
+    assert tuple(P.geometry()) == (1, 224, 1)
+    for c, t in ((1, 224), (1, 64), (1, 96), (2, 160)):
         P.set_tile(c, t)
         F, r = P.forward(w.u)
         assert rel(r, r_ref) < TOL
