@@ -55,7 +55,7 @@ def test_two_gloo_ranks_take_the_max_and_only_rank0_reports():
 
 def test_reference_arm_prints_the_contract_line():
     """`bench.py --impl reference` times the FP64 oracle on the host and prints
-    one JSON line with the keys the driver reads."""
+    one JSON line with the keys of the bench line contract."""
     import json
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"],
                        cwd=ROOT, capture_output=True, text=True, timeout=600,
